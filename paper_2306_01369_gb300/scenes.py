@@ -1,0 +1,315 @@
+"""Seeded synthetic scenes for the granular contact step.
+
+This module only *generates inputs*: particle positions, radii, velocities and
+masses, rigid-body descriptions and per-step tool twists.  It holds none of the
+method's arithmetic (no binning, contact, solver or integration code), so both
+the CUDA path and the FP64 oracle can consume its arrays without sharing code.
+
+Random numbers come from splitmix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) turned into 53-bit uniform
+doubles, then stored as float32.  Scene shapes follow the paper's workloads: a
+particle column collapsing onto a plane (the column benchmark of Sec. II-D), a
+particle bed dug by a kinematic scoop whose geometry is a signed distance
+function (the Excavation task of Sec. III-C), and many independent copies of the
+latter run side by side (the paper's "multiple independent simulations",
+Sec. III-A).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Body kinds (same numbering as the C header's gg_body_kind).
+PLANE = 0          # half-space below the body's local z = 0 plane
+BOX = 1            # solid box, shape[0:3] = half extents
+BOX_MINUS_BOX = 2  # box A (shape[0:3]) minus box B (half extents shape[3:6], centre shape[6:9])
+OPEN_BOX = 3       # container: inside of a box with no lid, shape[0:3] = half extents
+
+DENSITY = 2500.0   # kg/m^3, used when a scene gives no density
+
+
+def splitmix64(seed: int, count: int) -> np.ndarray:
+    """`count` successive splitmix64 outputs for a generator started at `seed`."""
+    with np.errstate(over="ignore"):
+        k = np.arange(1, count + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + k * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, count: int) -> np.ndarray:
+    """53-bit uniform doubles in [0, 1)."""
+    return (splitmix64(seed, count) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+@dataclass
+class Body:
+    kind: int
+    shape: tuple = (0.0,) * 12
+    pos: tuple = (0.0, 0.0, 0.0)
+    quat: tuple = (1.0, 0.0, 0.0, 0.0)   # (w, x, y, z)
+    lin_vel: tuple = (0.0, 0.0, 0.0)
+    ang_vel: tuple = (0.0, 0.0, 0.0)
+    is_free: int = 0
+    mass: float = 0.0
+    inertia: tuple = (0.0, 0.0, 0.0)     # principal moments in the body frame
+
+    def shape12(self):
+        s = list(self.shape) + [0.0] * (12 - len(self.shape))
+        return tuple(float(v) for v in s[:12])
+
+
+@dataclass
+class Params:
+    dt: float = 1e-4
+    gravity: tuple = (0.0, 0.0, -9.81)
+    mu: float = 0.5
+    alpha: float = 0.2
+    pja_iters: int = 20
+    cell_size: float = 0.0      # 0 -> 2.002 * r_max
+    hash_size: int = 0          # 0 -> 2 n (per environment)
+    max_contacts: int = 16      # particle-particle capacity per particle
+    max_body_contacts: int = 4  # particle-body capacity per particle
+
+
+@dataclass
+class Scene:
+    name: str
+    pos_r: np.ndarray                 # float32 (n, 4): x, y, z, radius
+    vel: np.ndarray                   # float32 (n, 3)
+    mass: np.ndarray                  # float32 (n,)
+    bodies: list                      # list[Body] (all environments, concatenated)
+    params: Params
+    n_steps: int
+    twist: dict = field(default_factory=dict)   # global body index -> float32 (n_steps, 6)
+    env_offsets: np.ndarray | None = None       # uint32 (E+1,) particle offsets, batched scenes
+    body_offsets: np.ndarray | None = None      # uint32 (E+1,) body offsets, batched scenes
+    info: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.pos_r.shape[0])
+
+
+def sphere_mass(r: np.ndarray, density: float = DENSITY) -> np.ndarray:
+    r = r.astype(np.float64)
+    return (density * (4.0 / 3.0) * math.pi * r ** 3).astype(np.float32)
+
+
+def jittered_lattice(dims, n, r0, jitter, seed, origin=(0.0, 0.0, 0.0), pitch=None):
+    """First `n` sites of a dims=(nx, ny, nz) lattice, z-major (layers fill bottom up).
+
+    Radius r_i = r0 * (1 + U(-jitter, jitter)); pitch defaults to 2 r_max * 1.02;
+    each site is offset per axis by U(-(pitch/2 - r_i), +(pitch/2 - r_i)), so no
+    two spheres overlap initially and every sphere stays inside its site.
+    Returns float32 (n, 4) = (x, y, z, r) with the lattice's lower corner at origin.
+    """
+    nx, ny, nz = dims
+    assert nx * ny * nz >= n
+    r_max = r0 * (1.0 + jitter)
+    if pitch is None:
+        pitch = 2.0 * r_max * 1.02
+    u = uniform(seed, 4 * n).reshape(n, 4)
+    r = r0 * (1.0 + jitter * (2.0 * u[:, 0] - 1.0))
+    idx = np.arange(n)
+    ix = idx % nx
+    iy = (idx // nx) % ny
+    iz = idx // (nx * ny)
+    site = np.stack([ix, iy, iz], axis=1).astype(np.float64) + 0.5
+    slack = (0.5 * pitch - r)[:, None]
+    off = slack * (2.0 * u[:, 1:4] - 1.0)
+    p = np.asarray(origin, np.float64)[None, :] + site * pitch + off
+    out = np.empty((n, 4), np.float32)
+    out[:, :3] = p
+    out[:, 3] = r
+    return out, pitch
+
+
+def _quat_from_rotvec(rv):
+    rv = np.asarray(rv, np.float64)
+    th = float(np.linalg.norm(rv))
+    if th == 0.0:
+        return (1.0, 0.0, 0.0, 0.0)
+    a = rv / th
+    s = math.sin(0.5 * th)
+    return (math.cos(0.5 * th), a[0] * s, a[1] * s, a[2] * s)
+
+
+def scoop_body(scale: float = 1.0, pos=(0.0, 0.0, 0.0), rotvec=(0.0, 0.0, 0.0)) -> Body:
+    """Excavation tool: box A (0.06, 0.05, 0.04) m minus box B (0.054, 0.044, 0.04) m
+    raised 0.01 m, i.e. 6 mm walls and floor with an open top, scaled by `scale`."""
+    a = (0.06 * scale, 0.05 * scale, 0.04 * scale)
+    b = (0.054 * scale, 0.044 * scale, 0.04 * scale)
+    c = (0.0, 0.0, 0.01 * scale)
+    return Body(kind=BOX_MINUS_BOX, shape=a + b + c, pos=tuple(float(v) for v in pos),
+                quat=_quat_from_rotvec(rotvec))
+
+
+def waypoint_twists(seed, n_steps, dt, start, dig_depth, span, n_way=6, pos_jit=0.05, rot_range=0.3):
+    """Per-step world-frame twists (vx, vy, vz, wx, wy, wz) of a tool following
+    `n_way` seeded waypoints along a dig path, piecewise constant per segment.
+
+    Waypoint k sits at start + (span * k/(n_way-1), 0, -dig_depth * sin(pi k/(n_way-1)))
+    plus U(-pos_jit, pos_jit) per axis, with a rotation vector drawn from
+    U(-rot_range, rot_range) per axis.  The tool moves on each segment with the
+    constant linear velocity that joins the two waypoint positions and the
+    constant angular velocity (rotvec_{k+1} - rotvec_k) / T_segment.
+    Returns (twist float32 (n_steps, 6), rotvec of waypoint 0, position of waypoint 0).
+    """
+    u = uniform(seed, 6 * n_way).reshape(n_way, 6)
+    k = np.arange(n_way, dtype=np.float64) / (n_way - 1)
+    pts = np.stack([start[0] + span * k,
+                    np.full(n_way, start[1]),
+                    start[2] - dig_depth * np.sin(math.pi * k)], axis=1)
+    pts = pts + pos_jit * (2.0 * u[:, 0:3] - 1.0)
+    rv = rot_range * (2.0 * u[:, 3:6] - 1.0)
+    seg = max(1, n_steps // (n_way - 1))
+    tw = np.zeros((n_steps, 6), np.float64)
+    for s in range(n_steps):
+        kseg = min(s // seg, n_way - 2)
+        T = seg * dt
+        tw[s, 0:3] = (pts[kseg + 1] - pts[kseg]) / T
+        tw[s, 3:6] = (rv[kseg + 1] - rv[kseg]) / T
+    return tw.astype(np.float32), rv[0], pts[0]
+
+
+# --------------------------------------------------------------------------- #
+# Workloads shaped like the paper's tasks
+# --------------------------------------------------------------------------- #
+
+def settle_box(n=4096, seed=1000, n_steps=200):
+    """4,096 spheres, r = 5 mm +-10 %, on a jittered 17x17x15 lattice inside an open
+    0.2 m box (floor + 4 walls); dt = 1e-4 s, 20 PJA iterations, mu = 0.5."""
+    r0, jit = 5e-3, 0.10
+    pitch = 2.0 * r0 * (1 + jit) * 1.02
+    dims = (17, 17, 15)
+    ox = 0.5 * (0.2 - dims[0] * pitch)
+    pr, _ = jittered_lattice(dims, n, r0, jit, seed, origin=(ox, ox, 0.0), pitch=pitch)
+    box = Body(kind=OPEN_BOX, shape=(0.1, 0.1, 0.0), pos=(0.1, 0.1, 0.0))
+    return Scene("settle_box_4096", pr, np.zeros((n, 3), np.float32), sphere_mass(pr[:, 3]), [box],
+                 Params(dt=1e-4, mu=0.5, pja_iters=20), n_steps)
+
+
+def column_collapse(n=262144, seed=1001, n_steps=2000, dims=None):
+    """Granular column: n spheres, r = 2 mm +-10 %, on a jittered lattice 40x40 sites
+    wide (1:1:4 aspect, 4.49 mm pitch) released onto a ground plane; mu = 0.6,
+    dt = 5e-5 s, 20 PJA iterations."""
+    r0, jit = 2e-3, 0.10
+    if dims is None:
+        side = 40 if n >= 40 * 40 * 4 else max(2, int(round((n / 4.0) ** (1.0 / 3.0))))
+        dims = (side, side, -(-n // (side * side)))
+    pitch = 2.0 * r0 * (1 + jit) * 1.02
+    half = 0.5 * dims[0] * pitch
+    pr, _ = jittered_lattice(dims, n, r0, jit, seed, origin=(-half, -half, 0.0), pitch=pitch)
+    ground = Body(kind=PLANE, pos=(0.0, 0.0, 0.0))
+    return Scene(f"column_collapse_{n}", pr, np.zeros((n, 3), np.float32), sphere_mass(pr[:, 3]),
+                 [ground], Params(dt=5e-5, mu=0.6, pja_iters=20), n_steps,
+                 info={"dims": dims, "pitch": pitch})
+
+
+def _bed_env(n, r0, jit, seed, side=None, layers=None, n_steps=500, dt=1e-4, scoop_scale=1.0,
+             tool_seed=None, margin=0.005):
+    """A bed of n spheres in an open container, plus a kinematic scoop on a seeded
+    dig trajectory.  Returns (pos_r, bodies, twist_of_scoop, info)."""
+    if layers is None and side is None:
+        layers = 16
+    if side is None:
+        side = int(math.ceil(math.sqrt(n / layers)))
+    if layers is None:
+        layers = -(-n // (side * side))
+    pitch = 2.0 * r0 * (1 + jit) * 1.02
+    foot = side * pitch
+    half = 0.5 * foot + margin
+    pr, _ = jittered_lattice((side, side, layers), n, r0, jit, seed,
+                             origin=(-0.5 * foot, -0.5 * foot, 0.0), pitch=pitch)
+    height = layers * pitch
+    container = Body(kind=OPEN_BOX, shape=(half, half, 0.0), pos=(0.0, 0.0, 0.0))
+    # the scoop starts above one side of the bed and digs across it
+    ts = seed * 7 + 3 if tool_seed is None else tool_seed
+    span = 0.6 * foot
+    start = (-0.3 * foot, 0.0, height + 0.05 * scoop_scale)
+    tw, rv0, p0 = waypoint_twists(ts, n_steps, dt, start, dig_depth=0.5 * height + 0.05 * scoop_scale,
+                                  span=span, pos_jit=0.05 * scoop_scale)
+    scoop = scoop_body(scoop_scale, pos=p0, rotvec=rv0)
+    return pr, [container, scoop], tw, {"side": side, "layers": layers, "pitch": pitch, "height": height}
+
+
+def excavation(n=1048576, seed=1002, n_steps=1000, with_cubes=True):
+    """Bed of n spheres (r = 2 mm +-15 %) 128x128 sites wide in a 0.61 m container,
+    one kinematic box-minus-box scoop on 6 seeded waypoints, two free 3 cm cubes;
+    dt = 1e-4 s, 30 PJA iterations, mu = 0.5."""
+    r0, jit = 2e-3, 0.15
+    side = 128 if n >= 128 * 128 else int(math.ceil(math.sqrt(n / 16)))
+    pr, bodies, tw, info = _bed_env(n, r0, jit, seed, side=side, n_steps=n_steps, dt=1e-4,
+                                    margin=0.5 * (0.61 - 128 * 2 * r0 * (1 + jit) * 1.02) if side == 128 else 0.005)
+    if with_cubes:
+        s = 0.03
+        m = DENSITY * s ** 3
+        inertia = m * s * s / 6.0
+        zc = info["height"] + 0.5 * s + 0.002
+        for x in (0.15 * side * info["pitch"], 0.3 * side * info["pitch"]):
+            bodies.append(Body(kind=BOX, shape=(0.5 * s, 0.5 * s, 0.5 * s), pos=(x, 0.05, zc), is_free=1,
+                               mass=m, inertia=(inertia,) * 3))
+    return Scene(f"excavation_{n}", pr, np.zeros((n, 3), np.float32), sphere_mass(pr[:, 3]), bodies,
+                 Params(dt=1e-4, mu=0.5, pja_iters=30, max_body_contacts=4), n_steps, twist={1: tw},
+                 info=info)
+
+
+def scoop_bed(n=32768, seed=1004, n_steps=200, dims=None):
+    """Differentiable workload: n spheres (32x32x32 lattice, r = 2 mm +-10 %) in a
+    container plus a scoop on a seeded trajectory; dt = 1e-4 s, 20 PJA iterations."""
+    r0, jit = 2e-3, 0.10
+    if dims is None:
+        side = int(round(n ** (1.0 / 3.0)))
+        dims = (side, side, -(-n // (side * side)))
+    pr, bodies, tw, info = _bed_env(n, r0, jit, seed, side=dims[0], layers=dims[2], n_steps=n_steps,
+                                    dt=1e-4, scoop_scale=0.5)
+    return Scene(f"scoop_bed_{n}", pr, np.zeros((n, 3), np.float32), sphere_mass(pr[:, 3]), bodies,
+                 Params(dt=1e-4, mu=0.5, pja_iters=20), n_steps, twist={1: tw}, info=info)
+
+
+def batched_beds(n_envs=256, seed=1003, n_steps=500, n_min=8192, n_max=65536):
+    """n_envs independent beds with n_e = round(exp(U(ln n_min, ln n_max))) spheres,
+    radius r_e ~ U(2, 4) mm (+-10 %), 16 layers, each with its own container and a
+    scoop (scaled by r_e / 2 mm) on its own seeded trajectory; dt = 1e-4 s,
+    20 PJA iterations, mu = 0.5.  Environments are spaced 10 m apart in x so that
+    they never touch; they stay independent in any case because each has its own
+    hash-bucket range."""
+    u = uniform(seed, 2 * n_envs).reshape(n_envs, 2)
+    ne = np.rint(np.exp(math.log(n_min) + u[:, 0] * (math.log(n_max) - math.log(n_min)))).astype(np.int64)
+    re = 2e-3 + 2e-3 * u[:, 1]
+    pos, bodies, twist = [], [], {}
+    offs, boffs = [0], [0]
+    for e in range(n_envs):
+        pr, bl, tw, _ = _bed_env(int(ne[e]), float(re[e]), 0.10, seed * 65536 + e, layers=16,
+                                 n_steps=n_steps, dt=1e-4, scoop_scale=float(re[e]) / 2e-3)
+        dx = 10.0 * e
+        pr[:, 0] += np.float32(dx)
+        for b in bl:
+            b.pos = (b.pos[0] + dx, b.pos[1], b.pos[2])
+        twist[len(bodies) + 1] = tw
+        bodies.extend(bl)
+        pos.append(pr)
+        offs.append(offs[-1] + pr.shape[0])
+        boffs.append(len(bodies))
+    pr = np.concatenate(pos, 0)
+    n = pr.shape[0]
+    return Scene(f"batched_{n_envs}env_{n}", pr, np.zeros((n, 3), np.float32), sphere_mass(pr[:, 3]),
+                 bodies, Params(dt=1e-4, mu=0.5, pja_iters=20), n_steps, twist=twist,
+                 env_offsets=np.asarray(offs, np.uint32), body_offsets=np.asarray(boffs, np.uint32),
+                 info={"n_e": ne.tolist(), "r_e": re.tolist()})
+
+
+def random_cloud(n, seed, box=0.05, r0=2e-3, jitter=0.1, vel_scale=0.0, overlap=1.0):
+    """n spheres uniformly scattered in [0, box]^3 (overlaps allowed), for contact
+    tests.  `overlap` < 1 shrinks the box relative to the given size."""
+    u = uniform(seed, 7 * n).reshape(n, 7)
+    pr = np.empty((n, 4), np.float32)
+    pr[:, :3] = (u[:, 0:3] * box * overlap).astype(np.float32)
+    pr[:, 3] = (r0 * (1.0 + jitter * (2.0 * u[:, 3] - 1.0))).astype(np.float32)
+    vel = (vel_scale * (2.0 * u[:, 4:7] - 1.0)).astype(np.float32)
+    return pr, vel
