@@ -1,0 +1,216 @@
+/*
+ * gg.h -- C ABI of libgg.so, a GB300 (sm_103a) implementation of the per-time-step
+ * granular contact pipeline of GranularGym (arxiv 2306.01369):
+ *
+ *   bin spheres with the spatial hash of Eq. 6 and a sort        (Sec. II-B, Alg. 2's role)
+ *   build particle-particle contacts over the 27 neighbour cells (Sec. II-B, II-C)
+ *   build particle-body contacts against signed distance functions (Sec. II-C, Eq. 7)
+ *   solve the frictional contact NCP (Eq. 1-3) with projected Jacobi (Alg. 1, Baumgarte)
+ *   reduce contact impulses into a wrench per rigid body        (Sec. III-C, force readback)
+ *   integrate with symplectic Euler                             (Eq. 4-5)
+ *
+ * Problem statement (Sec. II): n spheres with positions x and velocities v (3 x n),
+ * and rigid bodies with pose X in SE(3) and twist in se(3) that are driven by time
+ * (kinematic).  Free rigid bodies that take contact reactions go beyond the paper
+ * (its Sec. V names two-way coupling as future work).
+ *
+ * Conventions
+ *  - All arithmetic on the device is FP32.  Arrays are row-major, little-endian.
+ *  - Particle arrays passed in or read back are in the caller's particle order
+ *    ("id" order).  Internally the library stores particles in sorted-bucket order.
+ *  - Host pointers are borrowed for the duration of the call only; the library
+ *    copies what it needs.  Device pointers (flag *_on_device != 0) must be
+ *    cudaMalloc'ed memory of the current device; they too are read only during the
+ *    call (or, for async calls, by work enqueued on the given stream).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *  - Every call returns a gg_status; no C++ exception crosses the ABI.  Device-side
+ *    errors (capacity overflow, non-finite state) are latched in a device status
+ *    word and reported by the next call that synchronises (gg_sync, gg_readback).
+ *  - A gg_sim is not thread-safe; use one host thread per simulation.
+ */
+#ifndef GG_H
+#define GG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GG_ABI_VERSION 1u
+
+/* Only the functions declared here are exported from libgg.so. */
+#if defined(__GNUC__)
+#define GG_API __attribute__((visibility("default")))
+#else
+#define GG_API
+#endif
+
+typedef struct gg_sim gg_sim;
+
+typedef enum {
+  GG_OK = 0,
+  GG_ERR_INVALID_ARG = 1,       /* bad pointer, size, parameter or field */
+  GG_ERR_OOM = 2,               /* device or host allocation failed */
+  GG_ERR_CUDA = 3,              /* a CUDA runtime call failed (see gg_last_error) */
+  GG_ERR_CONTACT_OVERFLOW = 4,  /* a particle had more contacts than its capacity */
+  GG_ERR_DEVICE_TIMEOUT = 5,    /* a bounded device-side wait gave up */
+  GG_ERR_NONFINITE = 6,         /* a position or velocity became NaN or infinite */
+  GG_ERR_UNSUPPORTED = 7,       /* valid request the library does not implement */
+  GG_ERR_NO_DEVICE = 8          /* no usable CUDA device */
+} gg_status;
+
+/* Rigid-body geometry, as closed-form SDFs (Sec. II-C).  Body frame: origin at pos. */
+typedef enum {
+  GG_BODY_PLANE = 0,          /* half-space z_body <= 0; surface z_body = 0, normal +z_body */
+  GG_BODY_BOX = 1,            /* solid box; shape[0..2] = half extents */
+  GG_BODY_BOX_MINUS_BOX = 2,  /* box A (half extents shape[0..2]) minus box B (half extents
+                                 shape[3..5], centre shape[6..8]): an excavation scoop */
+  GG_BODY_OPEN_BOX = 3        /* container: inside of a box with no lid, walls at x = +-shape[0],
+                                 y = +-shape[1], floor at z = -shape[2]; walls are unbounded in +z */
+} gg_body_kind;
+
+typedef struct {
+  uint32_t struct_size;      /* sizeof(gg_params): ABI versioning, must be set */
+  float dt;                  /* time step Delta t (Alg. 1, Eq. 4-5), > 0 */
+  float gravity[3];          /* external acceleration F_ext / m (Eq. 1) */
+  float mu;                  /* Coulomb friction coefficient (Eq. 3), >= 0 */
+  float alpha;               /* Baumgarte factor: normal bias alpha psi / dt (Sec. II-A), >= 0 */
+  uint32_t pja_iters;        /* projected-Jacobi iterations n of Alg. 1, >= 1 */
+  float cell_size;           /* grid cell edge c (Eq. 6 uses c = 2r); 0 -> float(2.002 r_max)
+                                per environment; otherwise must be >= 2 r_max of every environment */
+  uint32_t hash_factor;      /* hash table size n_h = hash_factor * n_env (Sec. II-B proposes 2);
+                                0 -> 2; ignored when hash_size != 0 */
+  uint32_t hash_size;        /* explicit n_h for every environment (tests); 0 -> hash_factor * n_env */
+  uint32_t max_contacts;     /* particle-particle contact capacity per particle, 1..32; 0 -> 16 */
+  uint32_t max_body_contacts;/* particle-body contact capacity per particle, 1..8; 0 -> 4 */
+  uint32_t max_bodies;       /* bodies per environment, 1..64; 0 -> 8 */
+  float density;             /* mass = density 4/3 pi r^3 when no masses are given; 0 -> 2500 */
+  uint32_t tuning;           /* 0: pick launch shapes by timing (results do not depend on it);
+                                k >= 1: fixed launch-shape set k (see gg_tuning_count) */
+  uint32_t wrench_history;   /* per-step body wrenches kept for readback; 0 -> 1 */
+} gg_params;
+
+typedef struct {
+  uint32_t kind;             /* gg_body_kind */
+  uint32_t is_free;          /* 0: kinematic, follows its twist (paper); 1: free rigid body */
+  float shape[12];           /* see gg_body_kind */
+  float pos[3];              /* world position of the body origin (translation of 0_X_b) */
+  float quat[4];             /* orientation (w, x, y, z), body -> world; normalised by the library */
+  float lin_vel[3];          /* world-frame twist: velocity of the origin ... */
+  float ang_vel[3];          /* ... and angular velocity (rad/s) */
+  float mass;                /* free bodies: mass (> 0) */
+  float inertia[3];          /* free bodies: principal moments of inertia, body frame (> 0) */
+} gg_body;
+
+/* Fields for gg_readback.  Sizes: gg_field_bytes().  n = particles, H = hash table
+ * entries (all environments), K = max_contacts, Kb = max_body_contacts,
+ * B = environments x max_bodies. */
+typedef enum {
+  GG_FIELD_POS = 0,            /* float[n][4]: x, y, z, radius */
+  GG_FIELD_VEL = 1,            /* float[n][3] */
+  GG_FIELD_BODY_STATE = 2,     /* float[B][16]: pos[3], quat[4], lin_vel[3], ang_vel[3], 0, 0, 0 */
+  GG_FIELD_BODY_WRENCH = 3,    /* float[wrench_history][B][6]: force, torque on each body over the
+                                  last wrench_history steps, oldest first (Sec. III-C force readback) */
+  GG_FIELD_CELL_KEY = 4,       /* uint32[n]: hash bucket of each particle at the last binning
+                                  (environment base + Eq. 6 value) */
+  GG_FIELD_SORT_PERM = 5,      /* uint32[n]: particle ids in ascending (bucket, id) order */
+  GG_FIELD_CELL_START = 6,     /* uint32[H + 1]: first sorted slot of each bucket, then n */
+  GG_FIELD_CONTACTS = 7,       /* uint32[n][2 + K + Kb]: particle-particle count, particle-body
+                                  count, partner ids (ascending), body indices (ascending, local to
+                                  the environment); unused entries 0xFFFFFFFF */
+  GG_FIELD_CONTACT_GEOM = 8,   /* float[n][K][4]: unit normal from partner into particle, psi */
+  GG_FIELD_CONTACT_IMPULSE = 9,/* float[n][K][3]: accumulated impulse on the particle, last solve */
+  GG_FIELD_BODY_CONTACT_GEOM = 10, /* float[n][Kb][8]: normal (body into particle), psi, contact point, 0 */
+  GG_FIELD_BODY_CONTACT_IMPULSE = 11, /* float[n][Kb][3] */
+  GG_FIELD_STATS = 12,         /* gg_stats */
+  GG_FIELD_STATE = 13          /* opaque checkpoint for gg_set_state (bit-exact resume) */
+} gg_field;
+
+typedef struct {
+  uint64_t steps;          /* time steps taken since creation (or the restored checkpoint) */
+  uint32_t n_pp;           /* directed particle-particle contacts at the last step (pairs x 2) */
+  uint32_t n_body;         /* particle-body contacts at the last step */
+  uint32_t max_pp;         /* largest particle-particle count of one particle, last step */
+  uint32_t max_body;       /* largest particle-body count of one particle, last step */
+  uint32_t status_flags;   /* latched device flags: 1 pp overflow, 2 body overflow, 4 non-finite */
+  float max_psi;           /* largest penetration depth at the last step */
+} gg_stats;
+
+GG_API uint32_t gg_abi_version(void);
+GG_API const char *gg_status_string(gg_status s);
+
+/*
+ * Create a single-environment simulation of n spheres.
+ * pos_radius: float[n][4] (x, y, z, radius > 0); vel: float[n][3] (NULL -> 0);
+ * mass: float[n] (> 0; NULL -> density 4/3 pi r^3).  All device memory the step
+ * needs is allocated here, at capacity; gg_step allocates nothing.
+ * On success *out owns the simulation (free with gg_destroy).
+ */
+GG_API gg_status gg_create(const gg_params *params, uint32_t n, const float *pos_radius, const float *vel,
+                    const float *mass, int inputs_on_device, gg_sim **out);
+
+/*
+ * Create n_envs independent environments stepped together (batched mode; the
+ * paper's "multiple independent simulations", Sec. III-A).  env_offsets:
+ * uint32[n_envs + 1], env e owns particles [env_offsets[e], env_offsets[e+1]),
+ * env_offsets[0] = 0, non-decreasing.  Each environment gets its own hash range
+ * and bodies; results are bit-identical to stepping each environment alone.
+ */
+GG_API gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32_t *env_offsets,
+                          const float *pos_radius, const float *vel, const float *mass,
+                          int inputs_on_device, gg_sim **out);
+
+/* Replace the bodies of environment env (n_bodies <= max_bodies; host array).
+ * Synchronous with respect to previously enqueued steps. */
+GG_API gg_status gg_set_bodies(gg_sim *sim, uint32_t env, uint32_t n_bodies, const gg_body *bodies);
+
+/*
+ * Prescribe the twist of kinematic body `body` of environment env for the next
+ * n_steps steps: twist = float[n_steps][6] (world-frame lin_vel, ang_vel), step k
+ * counted from the current step.  Past the table the body keeps its own twist.
+ * Allocates device memory (outside gg_step).
+ */
+GG_API gg_status gg_set_trajectory(gg_sim *sim, uint32_t env, uint32_t body, uint32_t n_steps,
+                            const float *twist, int twist_on_device);
+
+/* Overwrite particle positions/radii (float[n][4]) and velocities (float[n][3]; NULL
+ * keeps them), asynchronously on `stream`.  Masses are kept. */
+GG_API gg_status gg_set_particles(gg_sim *sim, const float *pos_radius, const float *vel, int on_device,
+                           void *stream);
+
+/* Enqueue n_steps time steps on `stream` (replays of one captured CUDA graph per
+ * step).  Returns without waiting; see gg_sync for device-side errors. */
+GG_API gg_status gg_step(gg_sim *sim, uint32_t n_steps, void *stream);
+
+/* Wait for `stream` and report the latched device status (GG_OK or the first error). */
+GG_API gg_status gg_sync(gg_sim *sim, void *stream);
+
+/* Size in bytes of a readback field. */
+GG_API size_t gg_field_bytes(const gg_sim *sim, gg_field field);
+
+/*
+ * Copy `field` into dst (bytes must equal gg_field_bytes).  dst on the device:
+ * asynchronous on `stream`; on the host: waits for `stream`.  Returns the latched
+ * device status when it waited (the copy is made either way).
+ */
+GG_API gg_status gg_readback(gg_sim *sim, gg_field field, void *dst, size_t bytes, int dst_on_device,
+                      void *stream);
+
+/* Restore a GG_FIELD_STATE checkpoint taken from a simulation with the same sizes. */
+GG_API gg_status gg_set_state(gg_sim *sim, const void *state, size_t bytes, int on_device, void *stream);
+
+/* Number of fixed launch-shape sets accepted by gg_params.tuning, and the set chosen. */
+GG_API uint32_t gg_tuning_count(void);
+GG_API uint32_t gg_tuning_selected(const gg_sim *sim);
+
+/* Last error message of this simulation (never NULL). */
+GG_API const char *gg_last_error(const gg_sim *sim);
+
+GG_API void gg_destroy(gg_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GG_H */

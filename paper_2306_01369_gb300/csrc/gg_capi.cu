@@ -1,0 +1,649 @@
+// gg_capi.cu -- host implementation of the C ABI declared in include/gg.h.
+//
+// All device memory is allocated by gg_create / gg_create_batch (and by
+// gg_set_trajectory for its table, and lazily by the first readback that needs a
+// staging buffer); gg_step allocates nothing.  A time step is captured once into
+// a CUDA graph and replayed on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/gg.h"
+#include "gg_device.cuh"
+#include "gg_internal.h"
+
+using gg::DevBody;
+using gg::DevCtrl;
+using gg::DevEnv;
+using gg::StepArgs;
+
+namespace {
+
+// Launch-shape sets accepted by gg_params.tuning (index k-1).
+const gg::LaunchShape kShapes[] = {{0, 256}, {0, 128}, {0, 512}, {0, 64}};
+constexpr uint32_t kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+constexpr uint32_t kStateMagic = 0x31534747u;  // "GGS1"
+
+struct StateHeader {
+  uint32_t magic, n, n_envs, maxb;
+  uint64_t steps;
+  uint32_t pad[2];
+};
+
+}  // namespace
+
+struct gg_sim {
+  int device = 0;
+  gg_params p{};
+  uint32_t n = 0, n_envs = 0, maxb = 0, K = 0, Kb = 0, H = 1;
+  uint32_t nh_total = 0, nh_pad = 0, n_chunks = 0;
+  std::vector<DevEnv> envs;
+  std::vector<uint32_t> nbodies;
+  std::vector<float *> traj;  // per body slot
+  std::vector<void *> allocs;
+  StepArgs a{};
+  gg::LaunchShape ls{};
+  uint32_t tuning_sel = 1;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_ready = false;
+  uint64_t steps = 0;
+  void *staging = nullptr;
+  size_t staging_bytes = 0;
+  float *vel3 = nullptr;  // n*3 staging for velocity upload / readback
+  std::string err;
+};
+
+namespace {
+
+gg_status fail(gg_sim *s, gg_status st, const std::string &msg) {
+  if (s) s->err = msg;
+  return st;
+}
+
+gg_status cuda_fail(gg_sim *s, cudaError_t e, const char *what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  (void)cudaGetLastError();
+  return fail(s, GG_ERR_CUDA, m);
+}
+
+#define GG_CUDA(sim, call)                                         \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_fail((sim), e_, #call);     \
+  } while (0)
+
+template <typename T>
+gg_status dalloc(gg_sim *s, T **ptr, size_t count) {
+  void *p = nullptr;
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(s, GG_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  s->allocs.push_back(p);
+  *ptr = static_cast<T *>(p);
+  return GG_OK;
+}
+
+gg_status status_from_flags(gg_sim *s, uint32_t f) {
+  if (f & gg::kFlagNonFinite) return fail(s, GG_ERR_NONFINITE, "a particle position or velocity became non-finite");
+  if (f & (gg::kFlagPPOverflow | gg::kFlagBodyOverflow))
+    return fail(s, GG_ERR_CONTACT_OVERFLOW, "a particle exceeded its contact capacity (flags " + std::to_string(f) + ")");
+  return GG_OK;
+}
+
+gg_status read_ctrl(gg_sim *s, DevCtrl *out, cudaStream_t st) {
+  GG_CUDA(s, cudaMemcpyAsync(out, s->a.ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, st));
+  GG_CUDA(s, cudaStreamSynchronize(st));
+  return GG_OK;
+}
+
+void free_graph(gg_sim *s) {
+  if (s->exec) cudaGraphExecDestroy(s->exec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  s->exec = nullptr;
+  s->graph = nullptr;
+  s->graph_ready = false;
+}
+
+gg_status ensure_staging(gg_sim *s, size_t bytes) {
+  if (s->staging_bytes >= bytes) return GG_OK;
+  if (s->staging) cudaFree(s->staging);
+  s->staging = nullptr;
+  s->staging_bytes = 0;
+  cudaError_t e = cudaMalloc(&s->staging, bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(s, GG_ERR_OOM, "staging allocation failed");
+  }
+  s->staging_bytes = bytes;
+  return GG_OK;
+}
+
+bool finite_pos(float v) { return std::isfinite(v); }
+
+gg_status capture(gg_sim *s) {
+  free_graph(s);
+  GG_CUDA(s, cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = gg::enqueue_step(s->a, s->ls, s->cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(s, e, "enqueue_step during capture");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(s, e2, "cudaStreamEndCapture");
+  s->graph = g;
+  GG_CUDA(s, cudaGraphInstantiate(&s->exec, g, 0));
+  s->graph_ready = true;
+  return GG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint32_t gg_abi_version(void) { return GG_ABI_VERSION; }
+
+const char *gg_status_string(gg_status s) {
+  switch (s) {
+  case GG_OK: return "ok";
+  case GG_ERR_INVALID_ARG: return "invalid argument";
+  case GG_ERR_OOM: return "out of memory";
+  case GG_ERR_CUDA: return "CUDA error";
+  case GG_ERR_CONTACT_OVERFLOW: return "contact capacity overflow";
+  case GG_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+  case GG_ERR_NONFINITE: return "non-finite state";
+  case GG_ERR_UNSUPPORTED: return "unsupported";
+  case GG_ERR_NO_DEVICE: return "no CUDA device";
+  }
+  return "unknown status";
+}
+
+const char *gg_last_error(const gg_sim *sim) { return sim ? sim->err.c_str() : "null simulation"; }
+
+uint32_t gg_tuning_count(void) { return kNumShapes; }
+
+uint32_t gg_tuning_selected(const gg_sim *sim) { return sim ? sim->tuning_sel : 0; }
+
+void gg_destroy(gg_sim *sim) {
+  if (!sim) return;
+  cudaSetDevice(sim->device);
+  cudaDeviceSynchronize();
+  free_graph(sim);
+  if (sim->cap) cudaStreamDestroy(sim->cap);
+  for (void *p : sim->allocs) cudaFree(p);
+  for (float *t : sim->traj)
+    if (t) cudaFree(t);
+  if (sim->staging) cudaFree(sim->staging);
+  delete sim;
+}
+
+gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32_t *env_offsets,
+                          const float *pos_radius, const float *vel, const float *mass, int inputs_on_device,
+                          gg_sim **out) {
+  if (!out) return GG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!params || params->struct_size != sizeof(gg_params)) return GG_ERR_INVALID_ARG;
+  if (n_envs == 0 || !env_offsets) return GG_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    (void)cudaGetLastError();
+    return GG_ERR_NO_DEVICE;
+  }
+  gg_sim *s = new (std::nothrow) gg_sim();
+  if (!s) return GG_ERR_OOM;
+  gg_status rc = GG_OK;
+  auto bail = [&](gg_status st) {
+    gg_destroy(s);
+    return st;
+  };
+  cudaGetDevice(&s->device);
+  const gg_params &P = *params;
+  s->p = P;
+  std::vector<uint32_t> offs(env_offsets, env_offsets + n_envs + 1);
+  if (offs[0] != 0) return bail(GG_ERR_INVALID_ARG);
+  for (uint32_t e = 0; e < n_envs; ++e)
+    if (offs[e + 1] < offs[e]) return bail(GG_ERR_INVALID_ARG);
+  const uint32_t n = offs[n_envs];
+  if (n && !pos_radius) return bail(GG_ERR_INVALID_ARG);
+  if (!(P.dt > 0.f) || !std::isfinite(P.dt) || !(P.mu >= 0.f) || !(P.alpha >= 0.f) || P.pja_iters == 0 ||
+      P.pja_iters > 100000 || !(P.cell_size >= 0.f) || !(P.density >= 0.f) ||
+      !std::isfinite(P.gravity[0]) || !std::isfinite(P.gravity[1]) || !std::isfinite(P.gravity[2]))
+    return bail(GG_ERR_INVALID_ARG);
+  s->K = P.max_contacts ? P.max_contacts : 16;
+  s->Kb = P.max_body_contacts ? P.max_body_contacts : 4;
+  s->maxb = P.max_bodies ? P.max_bodies : 8;
+  s->H = P.wrench_history ? P.wrench_history : 1;
+  if (s->K > (uint32_t)gg::kMaxK || s->Kb > (uint32_t)gg::kMaxKb || s->maxb > 64 || s->H > (1u << 20))
+    return bail(GG_ERR_INVALID_ARG);
+  if (P.tuning > kNumShapes) return bail(GG_ERR_INVALID_ARG);
+  s->n = n;
+  s->n_envs = n_envs;
+
+  // host copies of the inputs
+  std::vector<float> hp((size_t)n * 4), hv((size_t)n * 3, 0.f), hm;
+  auto fetch = [&](const float *src, float *dst, size_t count) -> gg_status {
+    if (!count) return GG_OK;
+    if (inputs_on_device) {
+      cudaError_t e = cudaMemcpy(dst, src, count * sizeof(float), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(s, e, "reading input arrays");
+    } else {
+      std::memcpy(dst, src, count * sizeof(float));
+    }
+    return GG_OK;
+  };
+  if ((rc = fetch(pos_radius, hp.data(), (size_t)n * 4)) != GG_OK) return bail(rc);
+  if (vel && (rc = fetch(vel, hv.data(), (size_t)n * 3)) != GG_OK) return bail(rc);
+  if (mass) {
+    hm.resize(n);
+    if ((rc = fetch(mass, hm.data(), n)) != GG_OK) return bail(rc);
+  }
+  const double rho = P.density > 0.f ? P.density : 2500.0;
+  std::vector<float4> h_pos(n), h_vel(n);
+  std::vector<uint32_t> h_env(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    const float *q = &hp[(size_t)4 * i];
+    if (!finite_pos(q[0]) || !finite_pos(q[1]) || !finite_pos(q[2]) || !(q[3] > 0.f) || !std::isfinite(q[3]))
+      return bail(fail(s, GG_ERR_INVALID_ARG, "particle " + std::to_string(i) + ": bad position or radius"));
+    const float m = mass ? hm[i] : (float)(rho * (4.0 / 3.0) * 3.14159265358979323846 * (double)q[3] * q[3] * q[3]);
+    if (!(m > 0.f) || !std::isfinite(m))
+      return bail(fail(s, GG_ERR_INVALID_ARG, "particle " + std::to_string(i) + ": bad mass"));
+    h_pos[i] = make_float4(q[0], q[1], q[2], q[3]);
+    h_vel[i] = make_float4(hv[3 * i], hv[3 * i + 1], hv[3 * i + 2], 1.0f / m);
+  }
+  // environments: cell size, hash range, wrench chunks
+  s->envs.resize(n_envs);
+  uint64_t hb = 0;
+  uint32_t chunks = 0;
+  for (uint32_t e = 0; e < n_envs; ++e) {
+    DevEnv &E = s->envs[e];
+    E.off = offs[e];
+    E.n = offs[e + 1] - offs[e];
+    float rmax = 0.f;
+    for (uint32_t i = E.off; i < E.off + E.n; ++i) {
+      rmax = std::max(rmax, h_pos[i].w);
+      h_env[i] = e;
+    }
+    float c = P.cell_size > 0.f ? P.cell_size : (float)(2.002 * (double)rmax);
+    if (E.n && !(c >= 2.0f * rmax))
+      return bail(fail(s, GG_ERR_INVALID_ARG, "cell_size must be >= 2 r_max of every environment"));
+    if (!(c > 0.f)) c = 1.0f;
+    E.inv_cell = (float)(1.0 / (double)c);
+    uint64_t nh = P.hash_size ? P.hash_size : (uint64_t)(P.hash_factor ? P.hash_factor : 2) * E.n;
+    if (nh == 0) nh = 1;
+    E.hbase = (uint32_t)hb;
+    E.nh = (uint32_t)nh;
+    hb += nh;
+    if (hb > 0xF0000000ull) return bail(fail(s, GG_ERR_INVALID_ARG, "hash tables exceed 2^32 buckets"));
+    E.nbodies = 0;
+    E.chunk0 = chunks;
+    E.nchunks = (E.n + gg::kWrenchChunk - 1) / gg::kWrenchChunk;
+    chunks += E.nchunks;
+  }
+  s->nh_total = (uint32_t)hb;
+  s->nh_pad = (uint32_t)(((hb + gg::kScanTile - 1) / gg::kScanTile) * gg::kScanTile);
+  if (s->nh_pad == 0) s->nh_pad = gg::kScanTile;
+  s->n_chunks = chunks;
+  const uint32_t nbt = n_envs * s->maxb;
+  s->nbodies.assign(n_envs, 0);
+  s->traj.assign(nbt, nullptr);
+
+  // device buffers, all at capacity
+  StepArgs &a = s->a;
+  a.n = n;
+  a.n_envs = n_envs;
+  a.nh_total = s->nh_total;
+  a.nh_pad = s->nh_pad;
+  a.maxb = s->maxb;
+  a.K = s->K;
+  a.Kb = s->Kb;
+  a.n_chunks = chunks;
+  a.wrench_hist = s->H;
+  a.dt = P.dt;
+  a.mu = P.mu;
+  a.ab = P.alpha / P.dt;
+  for (int k = 0; k < 3; ++k) a.g[k] = P.gravity[k];
+  const size_t nK = (size_t)n * s->K, nKb = (size_t)n * s->Kb;
+  if ((rc = dalloc(s, &a.pos_id, n)) || (rc = dalloc(s, &a.vel_id, n)) || (rc = dalloc(s, &a.env_of, n)) ||
+      (rc = dalloc(s, &a.key_id, n)) || (rc = dalloc(s, &a.cnt, s->nh_pad)) ||
+      (rc = dalloc(s, &a.start, (size_t)s->nh_pad + 4)) || (rc = dalloc(s, &a.bsum, s->nh_pad / gg::kScanTile)) ||
+      (rc = dalloc(s, &a.sid_tmp, n)) || (rc = dalloc(s, &a.sid, n)) || (rc = dalloc(s, &a.slot_of, n)) ||
+      (rc = dalloc(s, &a.spos, n)) || (rc = dalloc(s, &a.sbase, n)) || (rc = dalloc(s, &a.U[0], n)) ||
+      (rc = dalloc(s, &a.U[1], n)) || (rc = dalloc(s, &a.ccount, n)) || (rc = dalloc(s, &a.cj, nK)) ||
+      (rc = dalloc(s, &a.cn, nK)) || (rc = dalloc(s, &a.clam, 3 * nK)) || (rc = dalloc(s, &a.bj, nKb)) ||
+      (rc = dalloc(s, &a.bn, nKb)) || (rc = dalloc(s, &a.bxc, nKb)) || (rc = dalloc(s, &a.blam, 3 * nKb)) ||
+      (rc = dalloc(s, &a.envs, n_envs)) || (rc = dalloc(s, &a.bodies, nbt)) ||
+      (rc = dalloc(s, &a.chunk_env, chunks)) || (rc = dalloc(s, &a.wpart, (size_t)std::max(chunks, 1u) * s->maxb * 6)) ||
+      (rc = dalloc(s, &a.wrench, (size_t)s->H * nbt * 6)) || (rc = dalloc(s, &a.ctrl, 1)) ||
+      (rc = dalloc(s, &s->vel3, (size_t)n * 3)))
+    return bail(rc);
+  std::vector<uint32_t> h_chunk_env(std::max(chunks, 1u), 0);
+  for (uint32_t e = 0; e < n_envs; ++e)
+    for (uint32_t c = 0; c < s->envs[e].nchunks; ++c) h_chunk_env[s->envs[e].chunk0 + c] = e;
+  cudaError_t e;
+#define GG_UP(dst, src, bytes)                                                        \
+  if ((e = cudaMemcpy((dst), (src), (bytes), cudaMemcpyHostToDevice)) != cudaSuccess) \
+    return bail(cuda_fail(s, e, "upload"));
+  if (n) {
+    GG_UP(a.pos_id, h_pos.data(), sizeof(float4) * n);
+    GG_UP(a.vel_id, h_vel.data(), sizeof(float4) * n);
+    GG_UP(a.env_of, h_env.data(), sizeof(uint32_t) * n);
+  }
+  GG_UP(a.envs, s->envs.data(), sizeof(DevEnv) * n_envs);
+  GG_UP(a.chunk_env, h_chunk_env.data(), sizeof(uint32_t) * h_chunk_env.size());
+#undef GG_UP
+  if ((e = cudaMemset(a.cnt, 0, sizeof(uint32_t) * s->nh_pad)) != cudaSuccess ||
+      (e = cudaMemset(a.start, 0, sizeof(uint32_t) * ((size_t)s->nh_pad + 4))) != cudaSuccess ||
+      (e = cudaMemset(a.bodies, 0, sizeof(DevBody) * nbt)) != cudaSuccess ||
+      (e = cudaMemset(a.wrench, 0, sizeof(float) * s->H * nbt * 6)) != cudaSuccess ||
+      (e = cudaMemset(a.ccount, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
+      (e = cudaMemset(a.sid, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
+      (e = cudaMemset(a.key_id, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
+      (e = cudaMemset(a.ctrl, 0, sizeof(DevCtrl))) != cudaSuccess)
+    return bail(cuda_fail(s, e, "initialising buffers"));
+  if ((e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(cuda_fail(s, e, "cudaStreamCreate"));
+  s->tuning_sel = P.tuning ? P.tuning : 1;
+  s->ls = kShapes[s->tuning_sel - 1];
+  s->ls.iters = P.pja_iters;
+  *out = s;
+  return GG_OK;
+}
+
+gg_status gg_create(const gg_params *params, uint32_t n, const float *pos_radius, const float *vel, const float *mass,
+                    int inputs_on_device, gg_sim **out) {
+  uint32_t offs[2] = {0, n};
+  return gg_create_batch(params, 1, offs, pos_radius, vel, mass, inputs_on_device, out);
+}
+
+gg_status gg_set_bodies(gg_sim *s, uint32_t env, uint32_t n_bodies, const gg_body *bodies) {
+  if (!s) return GG_ERR_INVALID_ARG;
+  if (env >= s->n_envs || n_bodies > s->maxb || (n_bodies && !bodies))
+    return fail(s, GG_ERR_INVALID_ARG, "gg_set_bodies: bad environment, count or pointer");
+  std::vector<DevBody> hb(s->maxb);
+  std::memset(hb.data(), 0, sizeof(DevBody) * s->maxb);
+  for (uint32_t b = 0; b < n_bodies; ++b) {
+    const gg_body &in = bodies[b];
+    DevBody &o = hb[b];
+    if (in.kind > GG_BODY_OPEN_BOX) return fail(s, GG_ERR_INVALID_ARG, "unknown body kind");
+    if (in.is_free) return fail(s, GG_ERR_UNSUPPORTED, "free rigid bodies are not supported by this build");
+    double qn = std::sqrt((double)in.quat[0] * in.quat[0] + (double)in.quat[1] * in.quat[1] +
+                          (double)in.quat[2] * in.quat[2] + (double)in.quat[3] * in.quat[3]);
+    if (!(qn > 0.0) || !std::isfinite(qn)) return fail(s, GG_ERR_INVALID_ARG, "body quaternion must be non-zero");
+    o.kind = in.kind;
+    o.is_free = in.is_free;
+    for (int k = 0; k < 12; ++k) o.shape[k] = in.shape[k];
+    for (int k = 0; k < 3; ++k) {
+      o.p[k] = in.pos[k];
+      o.own_v[k] = o.v[k] = in.lin_vel[k];
+      o.own_w[k] = o.w[k] = in.ang_vel[k];
+      o.inertia[k] = in.inertia[k];
+    }
+    // keep the caller's float quaternion when it is already unit length to FP32 precision
+    const bool unit = std::fabs(qn - 1.0) < 1e-6;
+    for (int k = 0; k < 4; ++k) o.q[k] = unit ? in.quat[k] : (float)(in.quat[k] / qn);
+    o.mass = in.mass;
+    o.env = env;
+    o.active = 1;
+  }
+  GG_CUDA(s, cudaDeviceSynchronize());
+  for (uint32_t b = 0; b < s->maxb; ++b) {
+    float *&t = s->traj[env * s->maxb + b];
+    if (t) cudaFree(t);
+    t = nullptr;
+  }
+  GG_CUDA(s, cudaMemcpy(s->a.bodies + (size_t)env * s->maxb, hb.data(), sizeof(DevBody) * s->maxb,
+                        cudaMemcpyHostToDevice));
+  s->nbodies[env] = n_bodies;
+  s->envs[env].nbodies = n_bodies;
+  GG_CUDA(s, cudaMemcpy(&s->a.envs[env].nbodies, &n_bodies, sizeof(uint32_t), cudaMemcpyHostToDevice));
+  return GG_OK;
+}
+
+gg_status gg_set_trajectory(gg_sim *s, uint32_t env, uint32_t body, uint32_t n_steps, const float *twist,
+                            int twist_on_device) {
+  if (!s) return GG_ERR_INVALID_ARG;
+  if (env >= s->n_envs || body >= s->nbodies[env] || (n_steps && !twist))
+    return fail(s, GG_ERR_INVALID_ARG, "gg_set_trajectory: bad environment, body or pointer");
+  GG_CUDA(s, cudaDeviceSynchronize());
+  const uint32_t gb = env * s->maxb + body;
+  float *&t = s->traj[gb];
+  if (t) cudaFree(t);
+  t = nullptr;
+  if (n_steps) {
+    cudaError_t e = cudaMalloc(&t, sizeof(float) * 6 * n_steps);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      t = nullptr;
+      return fail(s, GG_ERR_OOM, "trajectory allocation failed");
+    }
+    GG_CUDA(s, cudaMemcpy(t, twist, sizeof(float) * 6 * n_steps,
+                          twist_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+  }
+  DevCtrl c;
+  GG_CUDA(s, cudaMemcpy(&c, s->a.ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost));
+  DevBody *db = s->a.bodies + gb;
+  const float *tp = t;
+  GG_CUDA(s, cudaMemcpy(&db->traj, &tp, sizeof(tp), cudaMemcpyHostToDevice));
+  GG_CUDA(s, cudaMemcpy(&db->traj_len, &n_steps, sizeof(uint32_t), cudaMemcpyHostToDevice));
+  GG_CUDA(s, cudaMemcpy(&db->traj_start, &c.step, sizeof(uint32_t), cudaMemcpyHostToDevice));
+  return GG_OK;
+}
+
+gg_status gg_set_particles(gg_sim *s, const float *pos_radius, const float *vel, int on_device, void *stream) {
+  if (!s || !pos_radius) return s ? fail(s, GG_ERR_INVALID_ARG, "gg_set_particles: null positions") : GG_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (!s->n) return GG_OK;
+  GG_CUDA(s, cudaMemcpyAsync(s->a.pos_id, pos_radius, sizeof(float4) * s->n, kind, st));
+  if (vel) {
+    const float *src = vel;
+    if (!on_device) {
+      GG_CUDA(s, cudaMemcpyAsync(s->vel3, vel, sizeof(float) * 3 * s->n, cudaMemcpyHostToDevice, st));
+      src = s->vel3;
+    }
+    GG_CUDA(s, gg::enqueue_vel3_to_vel4(s->a.vel_id, src, s->n, st));
+  }
+  return GG_OK;
+}
+
+gg_status gg_step(gg_sim *s, uint32_t n_steps, void *stream) {
+  if (!s) return GG_ERR_INVALID_ARG;
+  if (!s->graph_ready) {
+    gg_status rc = capture(s);
+    if (rc != GG_OK) return rc;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (uint32_t k = 0; k < n_steps; ++k) GG_CUDA(s, cudaGraphLaunch(s->exec, st));
+  s->steps += n_steps;
+  return GG_OK;
+}
+
+gg_status gg_sync(gg_sim *s, void *stream) {
+  if (!s) return GG_ERR_INVALID_ARG;
+  DevCtrl c;
+  gg_status rc = read_ctrl(s, &c, static_cast<cudaStream_t>(stream));
+  if (rc != GG_OK) return rc;
+  return status_from_flags(s, c.status);
+}
+
+size_t gg_field_bytes(const gg_sim *s, gg_field f) {
+  if (!s) return 0;
+  const size_t n = s->n, nbt = (size_t)s->n_envs * s->maxb;
+  switch (f) {
+  case GG_FIELD_POS: return n * 16;
+  case GG_FIELD_VEL: return n * 12;
+  case GG_FIELD_BODY_STATE: return nbt * 16 * 4;
+  case GG_FIELD_BODY_WRENCH: return (size_t)s->H * nbt * 6 * 4;
+  case GG_FIELD_CELL_KEY: return n * 4;
+  case GG_FIELD_SORT_PERM: return n * 4;
+  case GG_FIELD_CELL_START: return ((size_t)s->nh_total + 1) * 4;
+  case GG_FIELD_CONTACTS: return n * (2 + s->K + s->Kb) * 4;
+  case GG_FIELD_CONTACT_GEOM: return n * s->K * 16;
+  case GG_FIELD_CONTACT_IMPULSE: return n * s->K * 12;
+  case GG_FIELD_BODY_CONTACT_GEOM: return n * s->Kb * 32;
+  case GG_FIELD_BODY_CONTACT_IMPULSE: return n * s->Kb * 12;
+  case GG_FIELD_STATS: return sizeof(gg_stats);
+  case GG_FIELD_STATE: return sizeof(StateHeader) + n * 32 + nbt * 16 * 4;
+  }
+  return 0;
+}
+
+gg_status gg_readback(gg_sim *s, gg_field f, void *dst, size_t bytes, int dst_on_device, void *stream) {
+  if (!s) return GG_ERR_INVALID_ARG;
+  const size_t need = gg_field_bytes(s, f);
+  if (need == 0 || bytes != need || !dst) return fail(s, GG_ERR_INVALID_ARG, "gg_readback: bad field, size or pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const cudaMemcpyKind d2x = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t n = s->n, nbt = (size_t)s->n_envs * s->maxb;
+  // device-side producer: write straight into dst when it is device memory, else into staging
+  auto target = [&](size_t b, void **t) -> gg_status {
+    if (dst_on_device) {
+      *t = dst;
+      return GG_OK;
+    }
+    gg_status rc = ensure_staging(s, b);
+    *t = s->staging;
+    return rc;
+  };
+  gg_status rc = GG_OK;
+  void *t = nullptr;
+  switch (f) {
+  case GG_FIELD_POS:
+    if (n) GG_CUDA(s, cudaMemcpyAsync(dst, s->a.pos_id, need, d2x, st));
+    break;
+  case GG_FIELD_VEL:
+    if ((rc = target(need, &t)) != GG_OK) return rc;
+    GG_CUDA(s, gg::enqueue_vel4_to_vel3(s->a.vel_id, static_cast<float *>(t), s->n, st));
+    if (!dst_on_device && n) GG_CUDA(s, cudaMemcpyAsync(dst, t, need, cudaMemcpyDeviceToHost, st));
+    break;
+  case GG_FIELD_BODY_STATE:
+    if ((rc = target(need, &t)) != GG_OK) return rc;
+    GG_CUDA(s, gg::enqueue_body_state(s->a.bodies, (uint32_t)nbt, static_cast<float *>(t), st));
+    if (!dst_on_device) GG_CUDA(s, cudaMemcpyAsync(dst, t, need, cudaMemcpyDeviceToHost, st));
+    break;
+  case GG_FIELD_BODY_WRENCH: {
+    const size_t row = nbt * 6 * sizeof(float);
+    const uint64_t H = s->H;
+    const uint64_t oldest = s->steps >= H ? s->steps % H : 0;
+    char *d = static_cast<char *>(dst);
+    const char *src = reinterpret_cast<const char *>(s->a.wrench);
+    if (oldest) {  // ring has wrapped: rows [oldest, H) then [0, oldest)
+      GG_CUDA(s, cudaMemcpyAsync(d, src + oldest * row, (H - oldest) * row, d2x, st));
+      GG_CUDA(s, cudaMemcpyAsync(d + (H - oldest) * row, src, oldest * row, d2x, st));
+    } else {
+      GG_CUDA(s, cudaMemcpyAsync(d, src, H * row, d2x, st));
+    }
+    break;
+  }
+  case GG_FIELD_CELL_KEY:
+    if (n) GG_CUDA(s, cudaMemcpyAsync(dst, s->a.key_id, need, d2x, st));
+    break;
+  case GG_FIELD_SORT_PERM:
+    if (n) GG_CUDA(s, cudaMemcpyAsync(dst, s->a.sid, need, d2x, st));
+    break;
+  case GG_FIELD_CELL_START:
+    GG_CUDA(s, cudaMemcpyAsync(dst, s->a.start, need, d2x, st));
+    break;
+  case GG_FIELD_CONTACTS:
+  case GG_FIELD_CONTACT_GEOM:
+  case GG_FIELD_CONTACT_IMPULSE:
+  case GG_FIELD_BODY_CONTACT_GEOM:
+  case GG_FIELD_BODY_CONTACT_IMPULSE: {
+    if ((rc = target(need, &t)) != GG_OK) return rc;
+    uint32_t *rows = f == GG_FIELD_CONTACTS ? static_cast<uint32_t *>(t) : nullptr;
+    float *geom = f == GG_FIELD_CONTACT_GEOM ? static_cast<float *>(t) : nullptr;
+    float *lam = f == GG_FIELD_CONTACT_IMPULSE ? static_cast<float *>(t) : nullptr;
+    float *bgeom = f == GG_FIELD_BODY_CONTACT_GEOM ? static_cast<float *>(t) : nullptr;
+    float *blam = f == GG_FIELD_BODY_CONTACT_IMPULSE ? static_cast<float *>(t) : nullptr;
+    GG_CUDA(s, gg::enqueue_export_contacts(s->a, rows, geom, lam, bgeom, blam, st));
+    if (!dst_on_device && n) GG_CUDA(s, cudaMemcpyAsync(dst, t, need, cudaMemcpyDeviceToHost, st));
+    break;
+  }
+  case GG_FIELD_STATS: {
+    if (dst_on_device) return fail(s, GG_ERR_UNSUPPORTED, "GG_FIELD_STATS is host-only");
+    DevCtrl c;
+    if ((rc = read_ctrl(s, &c, st)) != GG_OK) return rc;
+    gg_stats out{};
+    out.steps = s->steps;
+    out.n_pp = c.n_pp;
+    out.n_body = c.n_body;
+    out.max_pp = c.max_pp;
+    out.max_body = c.max_body;
+    out.status_flags = c.status;
+    uint32_t bits = c.max_psi_bits;
+    std::memcpy(&out.max_psi, &bits, 4);
+    std::memcpy(dst, &out, sizeof(out));
+    return status_from_flags(s, c.status);
+  }
+  case GG_FIELD_STATE: {
+    if ((rc = target(need, &t)) != GG_OK) return rc;
+    StateHeader h{kStateMagic, s->n, s->n_envs, s->maxb, s->steps, {0, 0}};
+    char *d = static_cast<char *>(t);
+    GG_CUDA(s, cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+    GG_CUDA(s, cudaStreamSynchronize(st));  // h lives on this stack frame
+    if (n) {
+      GG_CUDA(s, cudaMemcpyAsync(d + sizeof(h), s->a.pos_id, n * 16, cudaMemcpyDeviceToDevice, st));
+      GG_CUDA(s, cudaMemcpyAsync(d + sizeof(h) + n * 16, s->a.vel_id, n * 16, cudaMemcpyDeviceToDevice, st));
+    }
+    GG_CUDA(s, gg::enqueue_body_state(s->a.bodies, (uint32_t)nbt, reinterpret_cast<float *>(d + sizeof(h) + n * 32), st));
+    if (!dst_on_device) GG_CUDA(s, cudaMemcpyAsync(dst, t, need, cudaMemcpyDeviceToHost, st));
+    break;
+  }
+  default:
+    return fail(s, GG_ERR_INVALID_ARG, "unknown field");
+  }
+  if (dst_on_device) return GG_OK;
+  DevCtrl c;
+  if ((rc = read_ctrl(s, &c, st)) != GG_OK) return rc;
+  return status_from_flags(s, c.status);
+}
+
+gg_status gg_set_state(gg_sim *s, const void *state, size_t bytes, int on_device, void *stream) {
+  if (!s || !state) return s ? fail(s, GG_ERR_INVALID_ARG, "gg_set_state: null state") : GG_ERR_INVALID_ARG;
+  if (bytes != gg_field_bytes(s, GG_FIELD_STATE)) return fail(s, GG_ERR_INVALID_ARG, "gg_set_state: size mismatch");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GG_CUDA(s, cudaStreamSynchronize(st));
+  GG_CUDA(s, cudaDeviceSynchronize());
+  std::vector<char> h(bytes);
+  GG_CUDA(s, cudaMemcpy(h.data(), state, bytes, on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+  StateHeader hd;
+  std::memcpy(&hd, h.data(), sizeof(hd));
+  if (hd.magic != kStateMagic || hd.n != s->n || hd.n_envs != s->n_envs || hd.maxb != s->maxb)
+    return fail(s, GG_ERR_INVALID_ARG, "gg_set_state: checkpoint from a different simulation");
+  const size_t n = s->n, nbt = (size_t)s->n_envs * s->maxb;
+  if (n) {
+    GG_CUDA(s, cudaMemcpy(s->a.pos_id, h.data() + sizeof(hd), n * 16, cudaMemcpyHostToDevice));
+    GG_CUDA(s, cudaMemcpy(s->a.vel_id, h.data() + sizeof(hd) + n * 16, n * 16, cudaMemcpyHostToDevice));
+  }
+  std::vector<DevBody> bd(nbt);
+  GG_CUDA(s, cudaMemcpy(bd.data(), s->a.bodies, sizeof(DevBody) * nbt, cudaMemcpyDeviceToHost));
+  const float *bs = reinterpret_cast<const float *>(h.data() + sizeof(hd) + n * 32);
+  for (size_t b = 0; b < nbt; ++b) {
+    const float *q = bs + 16 * b;
+    for (int k = 0; k < 3; ++k) bd[b].p[k] = q[k];
+    for (int k = 0; k < 4; ++k) bd[b].q[k] = q[3 + k];
+    for (int k = 0; k < 3; ++k) bd[b].own_v[k] = q[7 + k];
+    for (int k = 0; k < 3; ++k) bd[b].own_w[k] = q[10 + k];
+  }
+  GG_CUDA(s, cudaMemcpy(s->a.bodies, bd.data(), sizeof(DevBody) * nbt, cudaMemcpyHostToDevice));
+  DevCtrl c;
+  GG_CUDA(s, cudaMemcpy(&c, s->a.ctrl, sizeof(c), cudaMemcpyDeviceToHost));
+  c.step = (uint32_t)hd.steps;
+  GG_CUDA(s, cudaMemcpy(s->a.ctrl, &c, sizeof(c), cudaMemcpyHostToDevice));
+  s->steps = hd.steps;
+  return GG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,268 @@
+// gg_device.cuh -- device-side layout and FP32 helpers of the granular contact step.
+//
+// Integer decisions (cell index, hash bucket, contact yes/no, active SDF branch)
+// use explicitly rounded FP32 intrinsics (__fmul_rn, __fadd_rn, __fsub_rn,
+// __fsqrt_rn) so that nvcc cannot contract them into FMAs: the result is then a
+// function of the FP32 inputs alone, fixed by the evaluation order written here.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gg {
+
+constexpr uint32_t kHashP1 = 73856093u;  // Eq. 6 primes
+constexpr uint32_t kHashP2 = 19349663u;
+constexpr uint32_t kHashP3 = 83492791u;
+constexpr uint32_t kHashQ = 100u;        // Eq. 6 offset q
+
+constexpr uint32_t kFlagPPOverflow = 1u;
+constexpr uint32_t kFlagBodyOverflow = 2u;
+constexpr uint32_t kFlagNonFinite = 4u;
+
+constexpr int kMaxK = 32;   // particle-particle capacity limit
+constexpr int kMaxKb = 8;   // particle-body capacity limit
+constexpr int kScanItems = 16;          // counts per thread in the bucket scan
+constexpr int kScanThreads = 256;
+constexpr int kScanTile = kScanItems * kScanThreads;
+constexpr int kWrenchChunk = 8192;      // slots per wrench partial
+
+struct DevEnv {
+  uint32_t off, n;        // particle range [off, off + n)
+  uint32_t hbase, nh;     // bucket range [hbase, hbase + nh)
+  float inv_cell;         // float(1 / c)
+  uint32_t nbodies;       // active bodies (slots [e * maxb, e * maxb + nbodies))
+  uint32_t chunk0, nchunks;  // wrench partial chunks of this environment
+};
+
+struct DevBody {
+  uint32_t kind, is_free;
+  float shape[12];
+  float p[3];       // pose at the start of the current step
+  float q[4];       // (w, x, y, z)
+  float R[9];       // rotation of q, row-major, body -> world, FP32 fixed order
+  float v[3], w[3]; // twist used during the current step
+  float own_v[3], own_w[3];  // the body's own twist (kinematic), or its state (free)
+  float mass, inertia[3];
+  const float *traj;  // float[traj_len][6] or null
+  uint32_t traj_len;
+  uint32_t traj_start;  // step index at which traj[0] applies
+  uint32_t env, active;
+};
+
+struct DevCtrl {
+  uint32_t step;      // steps taken (low 32 bits)
+  uint32_t status;    // latched flags
+  uint32_t n_pp, n_body, max_pp, max_body;
+  uint32_t max_psi_bits;  // max psi as the bits of a non-negative float
+  uint32_t pad;
+};
+
+// Everything a step's kernels read or write; passed by value to each kernel.
+struct StepArgs {
+  uint32_t n, n_envs, nh_total, nh_pad, maxb, K, Kb, n_chunks, wrench_hist;
+  float dt, mu, ab;       // ab = alpha / dt
+  float g[3];
+  // id order
+  float4 *pos_id;   // x, y, z, r
+  float4 *vel_id;   // vx, vy, vz, 1/m
+  uint32_t *env_of;
+  uint32_t *key_id;
+  // buckets
+  uint32_t *cnt;    // nh_pad entries, zero between steps
+  uint32_t *start;  // nh_pad + 1
+  uint32_t *bsum;   // scan block sums
+  // slot order
+  uint32_t *sid_tmp, *sid, *slot_of;
+  float4 *spos;     // x, y, z, r
+  float4 *sbase;    // v + dt g, 1/m
+  float4 *U[2];     // velocity estimate, w = n_contacts / m
+  uint32_t *ccount; // pp | body << 8
+  uint32_t *cj;     // [K][n] partner slot
+  float4 *cn;       // [K][n] normal (partner -> particle), psi
+  float *clam;      // [3][K][n]
+  uint32_t *bj;     // [Kb][n] global body index
+  float4 *bn;       // [Kb][n] normal (body -> particle), psi
+  float4 *bxc;      // [Kb][n] contact point
+  float *blam;      // [3][Kb][n]
+  // environments and bodies
+  DevEnv *envs;
+  DevBody *bodies;
+  uint32_t *chunk_env;    // environment of each wrench chunk
+  float *wpart;           // [n_chunks][maxb][6]
+  float *wrench;          // [wrench_hist][n_envs * maxb][6]
+  DevCtrl *ctrl;
+};
+
+// ---------------------------------------------------------------------------
+// FP32 decisions
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int32_t cell_of(float x, float inv_cell) {
+  float t = __fmul_rn(x, inv_cell);
+  t = __fadd_rn(t, 0.5f);
+  return (int32_t)floorf(t);
+}
+
+__device__ __forceinline__ uint32_t hash_cell(int32_t k0, int32_t k1, int32_t k2, uint32_t nh) {
+  uint32_t a = ((uint32_t)k0 - kHashQ) * kHashP1;
+  uint32_t b = ((uint32_t)k1 - kHashQ) * kHashP2;
+  uint32_t c = ((uint32_t)k2 - kHashQ) * kHashP3;
+  return (a ^ b ^ c) % nh;
+}
+
+// squared distance ((dx dx + dy dy) + dz dz) and the sum of radii squared
+__device__ __forceinline__ bool sphere_hit(float4 a, float4 b, float *d2out, float3 *dout) {
+  float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
+  float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+  float rs = __fadd_rn(a.w, b.w);
+  *d2out = d2;
+  *dout = make_float3(dx, dy, dz);
+  return d2 <= __fmul_rn(rs, rs);
+}
+
+__device__ __forceinline__ void quat_to_R(const float *q, float *R) {
+  float w = q[0], x = q[1], y = q[2], z = q[3];
+  float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+  float xy = __fmul_rn(x, y), xz = __fmul_rn(x, z), yz = __fmul_rn(y, z);
+  float wx = __fmul_rn(w, x), wy = __fmul_rn(w, y), wz = __fmul_rn(w, z);
+  R[0] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(yy, zz)));
+  R[1] = __fmul_rn(2.0f, __fsub_rn(xy, wz));
+  R[2] = __fmul_rn(2.0f, __fadd_rn(xz, wy));
+  R[3] = __fmul_rn(2.0f, __fadd_rn(xy, wz));
+  R[4] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, zz)));
+  R[5] = __fmul_rn(2.0f, __fsub_rn(yz, wx));
+  R[6] = __fmul_rn(2.0f, __fsub_rn(xz, wy));
+  R[7] = __fmul_rn(2.0f, __fadd_rn(yz, wx));
+  R[8] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, yy)));
+}
+
+// y = R^T (x - p), each component summed R[0k]d0 + R[1k]d1 first, then + R[2k]d2
+__device__ __forceinline__ float3 world_to_body(const DevBody &b, float3 x) {
+  float d0 = __fsub_rn(x.x, b.p[0]), d1 = __fsub_rn(x.y, b.p[1]), d2 = __fsub_rn(x.z, b.p[2]);
+  float y[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    y[k] = __fadd_rn(__fadd_rn(__fmul_rn(b.R[k], d0), __fmul_rn(b.R[3 + k], d1)), __fmul_rn(b.R[6 + k], d2));
+  return make_float3(y[0], y[1], y[2]);
+}
+
+// Box SDF: branch 0..2 inside (nearest face axis), 3 outside.
+__device__ __forceinline__ float box_sdf(float3 y, const float *h, int *branch) {
+  float q0 = __fsub_rn(fabsf(y.x), h[0]);
+  float q1 = __fsub_rn(fabsf(y.y), h[1]);
+  float q2 = __fsub_rn(fabsf(y.z), h[2]);
+  float m0 = fmaxf(q0, 0.0f), m1 = fmaxf(q1, 0.0f), m2 = fmaxf(q2, 0.0f);
+  float s = __fadd_rn(__fadd_rn(__fmul_rn(m0, m0), __fmul_rn(m1, m1)), __fmul_rn(m2, m2));
+  float o = __fsqrt_rn(s);
+  float mx = fmaxf(fmaxf(q0, q1), q2);
+  float f = __fadd_rn(o, fminf(mx, 0.0f));
+  *branch = (mx > 0.0f) ? 3 : ((q0 >= q1 && q0 >= q2) ? 0 : ((q1 >= q2) ? 1 : 2));
+  return f;
+}
+
+__device__ __forceinline__ float body_sdf(const DevBody &b, float3 y, int *branch) {
+  switch (b.kind) {
+  case 0:  // plane
+    *branch = 0;
+    return y.z;
+  case 1:  // box
+    return box_sdf(y, b.shape, branch);
+  case 2: {  // box minus box
+    int ba, bb;
+    float fa = box_sdf(y, b.shape, &ba);
+    float3 z = make_float3(__fsub_rn(y.x, b.shape[6]), __fsub_rn(y.y, b.shape[7]), __fsub_rn(y.z, b.shape[8]));
+    float nfb = -box_sdf(z, b.shape + 3, &bb);
+    if (fa >= nfb) {
+      *branch = ba;
+      return fa;
+    }
+    *branch = 4 + bb;
+    return nfb;
+  }
+  case 3: {  // open box (container)
+    float w[5] = {__fsub_rn(b.shape[0], y.x), __fadd_rn(y.x, b.shape[0]), __fsub_rn(b.shape[1], y.y),
+                  __fadd_rn(y.y, b.shape[1]), __fadd_rn(y.z, b.shape[2])};
+    float f = w[0];
+    int br = 0;
+#pragma unroll
+    for (int k = 1; k < 5; ++k)
+      if (w[k] < f) {
+        f = w[k];
+        br = k;
+      }
+    *branch = br;
+    return f;
+  }
+  }
+  *branch = -1;
+  return __int_as_float(0x7f800000);  // +inf: never in contact
+}
+
+// Unit gradient (body frame) of the branch chosen by body_sdf.
+__device__ __forceinline__ float3 box_grad(float3 y, const float *h, int branch) {
+  if (branch == 3) {
+    float m0 = fmaxf(fabsf(y.x) - h[0], 0.0f), m1 = fmaxf(fabsf(y.y) - h[1], 0.0f),
+          m2 = fmaxf(fabsf(y.z) - h[2], 0.0f);
+    float inv = rsqrtf(m0 * m0 + m1 * m1 + m2 * m2);
+    return make_float3(copysignf(m0 * inv, y.x), copysignf(m1 * inv, y.y), copysignf(m2 * inv, y.z));
+  }
+  float3 g = make_float3(0.f, 0.f, 0.f);
+  if (branch == 0) g.x = (y.x < 0.f) ? -1.f : 1.f;
+  if (branch == 1) g.y = (y.y < 0.f) ? -1.f : 1.f;
+  if (branch == 2) g.z = (y.z < 0.f) ? -1.f : 1.f;
+  return g;
+}
+
+__device__ __forceinline__ float3 body_grad(const DevBody &b, float3 y, int branch) {
+  switch (b.kind) {
+  case 0:
+    return make_float3(0.f, 0.f, 1.f);
+  case 1:
+    return box_grad(y, b.shape, branch);
+  case 2:
+    if (branch < 4) return box_grad(y, b.shape, branch);
+    {
+      float3 z = make_float3(y.x - b.shape[6], y.y - b.shape[7], y.z - b.shape[8]);
+      float3 g = box_grad(z, b.shape + 3, branch - 4);
+      return make_float3(-g.x, -g.y, -g.z);
+    }
+  case 3: {
+    float3 g = make_float3(0.f, 0.f, 0.f);
+    if (branch == 0) g.x = -1.f;
+    if (branch == 1) g.x = 1.f;
+    if (branch == 2) g.y = -1.f;
+    if (branch == 3) g.y = 1.f;
+    if (branch == 4) g.z = 1.f;
+    return g;
+  }
+  }
+  return make_float3(0.f, 0.f, 1.f);
+}
+
+__device__ __forceinline__ float3 rot_apply(const float *R, float3 g) {
+  return make_float3(R[0] * g.x + R[1] * g.y + R[2] * g.z, R[3] * g.x + R[4] * g.y + R[5] * g.z,
+                     R[6] * g.x + R[7] * g.y + R[8] * g.z);
+}
+
+// One projected-Jacobi contact update (Alg. 1 with the accumulated-impulse clamp).
+// lam: accumulated impulse on the particle; u: relative velocity particle - partner;
+// n: unit normal partner -> particle; bias: alpha psi / dt; w: effective mass.
+__device__ __forceinline__ float3 pja_project(float3 lam, float3 u, float3 n, float bias, float w, float mu) {
+  float sx = lam.x - w * (u.x - bias * n.x);
+  float sy = lam.y - w * (u.y - bias * n.y);
+  float sz = lam.z - w * (u.z - bias * n.z);
+  float ln = sx * n.x + sy * n.y + sz * n.z;
+  float lnp = fmaxf(ln, 0.0f);
+  float tx = sx - ln * n.x, ty = sy - ln * n.y, tz = sz - ln * n.z;
+  float t2 = tx * tx + ty * ty + tz * tz;
+  float lim = mu * lnp;
+  if (t2 > lim * lim) {
+    float sc = lim * rsqrtf(t2);
+    tx *= sc;
+    ty *= sc;
+    tz *= sc;
+  }
+  return make_float3(lnp * n.x + tx, lnp * n.y + ty, lnp * n.z + tz);
+}
+
+}  // namespace gg

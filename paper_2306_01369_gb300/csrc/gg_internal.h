@@ -1,0 +1,22 @@
+// gg_internal.h -- launchers shared by the C ABI and the kernels (not installed).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "gg_device.cuh"
+
+namespace gg {
+
+// Launch shape of the step; any choice gives bit-identical results.
+struct LaunchShape {
+  uint32_t iters;      // projected-Jacobi iterations
+  int pja_block;       // threads per block of k_pja
+};
+
+cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st);
+cudaError_t enqueue_export_contacts(const StepArgs &a, uint32_t *rows, float *geom, float *lam, float *bgeom,
+                                    float *blam, cudaStream_t st);
+cudaError_t enqueue_vel3_to_vel4(float4 *vel_id, const float *vel3, uint32_t n, cudaStream_t st);
+cudaError_t enqueue_vel4_to_vel3(const float4 *vel_id, float *vel3, uint32_t n, cudaStream_t st);
+cudaError_t enqueue_body_state(const DevBody *bodies, uint32_t nbt, float *out, cudaStream_t st);
+
+}  // namespace gg

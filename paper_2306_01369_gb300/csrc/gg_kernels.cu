@@ -1,0 +1,660 @@
+// gg_kernels.cu -- sm_103a kernels of the granular contact step.
+//
+// One time step = the launches below, in this order (captured once into a CUDA
+// graph and replayed):
+//   k_key            bucket of every particle (Eq. 6), bucket histogram, body prep
+//   k_scan_*         exclusive scan of the histogram -> bucket start table
+//   k_scatter        counting-sort scatter (returns the histogram to zero)
+//   k_reorder        stable order inside each bucket (ascending id) + gather of
+//                    positions / velocities into sorted slots
+//   k_contacts       27-cell bucket walk, sphere test, SDF tests (Sec. II-B, II-C)
+//   k_pja  x I       projected-Jacobi sweeps (Alg. 1), one launch per iteration
+//   k_integrate      symplectic Euler (Eq. 4-5), back to particle-id order
+//   k_wrench_partial per-body impulse sums over fixed slot chunks (deterministic)
+//   k_wrench_final   wrench readback ring, kinematic body poses, step counter
+// Detection and impulse computation are separate launches, the split the paper
+// finds fastest (Sec. II-D).
+#include "gg_device.cuh"
+#include "gg_internal.h"
+
+namespace gg {
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Fixed-order sum of 6 floats over the block, result valid in thread 0.
+template <int NT>
+__device__ __forceinline__ void block_sum6(float v[6]) {
+  __shared__ float sm[NT / 32][6];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sm[wid][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float s = sm[0][k];
+      for (int w = 1; w < NT / 32; ++w) s += sm[w][k];
+      v[k] = s;
+    }
+  }
+}
+
+__device__ __forceinline__ void flag(DevCtrl *c, uint32_t f) { atomicOr(&c->status, f); }
+
+// ---------------------------------------------------------------------------
+// 1. bucket keys + histogram; body pose/twist for this step
+// ---------------------------------------------------------------------------
+
+__device__ void prep_body(const StepArgs &a, uint32_t gb) {
+  DevBody &B = a.bodies[gb];
+  if (!B.active) return;
+  quat_to_R(B.q, B.R);
+  const uint32_t step = a.ctrl->step;
+  if (B.is_free) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      B.v[k] = B.own_v[k] + a.dt * a.g[k];
+      B.w[k] = B.own_w[k];
+    }
+    return;
+  }
+  const float *tw = nullptr;
+  if (B.traj && step >= B.traj_start && step - B.traj_start < B.traj_len) tw = B.traj + 6u * (step - B.traj_start);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    B.v[k] = tw ? tw[k] : B.own_v[k];
+    B.w[k] = tw ? tw[3 + k] : B.own_w[k];
+  }
+}
+
+__global__ void k_key(StepArgs a) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n) {
+    float4 p = a.pos_id[i];
+    const DevEnv &E = a.envs[a.env_of[i]];
+    int32_t k0 = cell_of(p.x, E.inv_cell), k1 = cell_of(p.y, E.inv_cell), k2 = cell_of(p.z, E.inv_cell);
+    uint32_t key = E.hbase + hash_cell(k0, k1, k2, E.nh);
+    a.key_id[i] = key;
+    atomicAdd(&a.cnt[key], 1u);
+  }
+  if (i < a.n_envs * a.maxb) prep_body(a, i);
+  if (i == 0) {
+    a.ctrl->n_pp = 0;
+    a.ctrl->n_body = 0;
+    a.ctrl->max_pp = 0;
+    a.ctrl->max_body = 0;
+    a.ctrl->max_psi_bits = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2. exclusive scan of the bucket histogram (reduce, scan block sums, down-sweep)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(StepArgs a) {
+  const uint4 *c4 = reinterpret_cast<const uint4 *>(a.cnt + (size_t)blockIdx.x * kScanTile +
+                                                     (size_t)threadIdx.x * kScanItems);
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems / 4; ++k) {
+    uint4 v = c4[k];
+    s += v.x + v.y + v.z + v.w;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ uint32_t ws[kScanThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) t += ws[w];
+    a.bsum[blockIdx.x] = t;
+  }
+}
+
+// Single block: exclusive scan of the block sums in place; start[nh_pad] = total.
+__global__ void __launch_bounds__(1024) k_scan_top(StepArgs a, uint32_t nblk) {
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < nblk; base += 1024) {
+    uint32_t idx = base + threadIdx.x;
+    uint32_t v = idx < nblk ? a.bsum[idx] : 0u;
+    // block scan of 1024 values
+    __shared__ uint32_t ws[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t inc = warp_incl_scan(v);
+    if (lane == 31) ws[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t s = ws[lane];
+      uint32_t si = warp_incl_scan(s);
+      ws[lane] = si - s;
+    }
+    __syncthreads();
+    uint32_t excl = carry + ws[wid] + inc - v;
+    if (idx < nblk) a.bsum[idx] = excl;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a.start[a.nh_pad] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(StepArgs a) {
+  const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
+  const uint4 *c4 = reinterpret_cast<const uint4 *>(a.cnt + base);
+  uint32_t v[kScanItems];
+#pragma unroll
+  for (int k = 0; k < kScanItems / 4; ++k) {
+    uint4 q = c4[k];
+    v[4 * k] = q.x;
+    v[4 * k + 1] = q.y;
+    v[4 * k + 2] = q.z;
+    v[4 * k + 3] = q.w;
+  }
+  uint32_t tsum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) tsum += v[k];
+  __shared__ uint32_t ws[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t inc = warp_incl_scan(tsum);
+  if (lane == 31) ws[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t s = lane < kScanThreads / 32 ? ws[lane] : 0u;
+    uint32_t si = warp_incl_scan(s);
+    if (lane < kScanThreads / 32) ws[lane] = si - s;
+  }
+  __syncthreads();
+  uint32_t run = a.bsum[blockIdx.x] + ws[wid] + inc - tsum;
+  uint4 *s4 = reinterpret_cast<uint4 *>(a.start + base);
+#pragma unroll
+  for (int k = 0; k < kScanItems / 4; ++k) {
+    uint4 o;
+    o.x = run;
+    run += v[4 * k];
+    o.y = run;
+    run += v[4 * k + 1];
+    o.z = run;
+    run += v[4 * k + 2];
+    o.w = run;
+    run += v[4 * k + 3];
+    s4[k] = o;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. scatter into buckets; 4. stable order inside buckets + gather
+// ---------------------------------------------------------------------------
+
+__global__ void k_scatter(StepArgs a) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const uint32_t key = a.key_id[i];
+  const uint32_t r = atomicSub(&a.cnt[key], 1u) - 1u;  // leaves the histogram at zero
+  a.sid_tmp[a.start[key] + r] = i;
+}
+
+__global__ void k_reorder(StepArgs a) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.n) return;
+  const uint32_t id = a.sid_tmp[s];
+  const uint32_t key = a.key_id[id];
+  const uint32_t b0 = a.start[key], b1 = a.start[key + 1];
+  uint32_t rank = 0;
+  for (uint32_t t = b0; t < b1; ++t) rank += (a.sid_tmp[t] < id) ? 1u : 0u;
+  const uint32_t dst = b0 + rank;
+  a.sid[dst] = id;
+  a.slot_of[id] = dst;
+  a.spos[dst] = a.pos_id[id];
+  float4 v = a.vel_id[id];
+  a.sbase[dst] = make_float4(v.x + a.dt * a.g[0], v.y + a.dt * a.g[1], v.z + a.dt * a.g[2], v.w);
+}
+
+// ---------------------------------------------------------------------------
+// 5. contacts: particle-particle (27 buckets) and particle-body (SDF)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_contacts(StepArgs a) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t npp = 0, nbc = 0;
+  float psi_max = 0.f;
+  if (i < a.n) {
+    const float4 pi = a.spos[i];
+    const uint32_t idi = a.sid[i];
+    const uint32_t e = a.env_of[idi];
+    const DevEnv E = a.envs[e];
+    const int32_t k0 = cell_of(pi.x, E.inv_cell), k1 = cell_of(pi.y, E.inv_cell), k2 = cell_of(pi.z, E.inv_cell);
+    uint32_t fid[kMaxK], fsl[kMaxK];
+    const uint32_t K = a.K;
+    bool ovf = false;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const uint32_t h = E.hbase + hash_cell(k0 + dx, k1 + dy, k2 + dz, E.nh);
+          const uint32_t t1 = a.start[h + 1];
+          for (uint32_t t = a.start[h]; t < t1; ++t) {
+            if (t == i) continue;
+            float d2;
+            float3 d;
+            if (!sphere_hit(pi, a.spos[t], &d2, &d)) continue;
+            const uint32_t jid = a.sid[t];
+            // insert by ascending id; a bucket reached twice yields the same id: skip it
+            uint32_t p = 0;
+            while (p < npp && fid[p] < jid) ++p;
+            if (p < npp && fid[p] == jid) continue;
+            if (npp == K) {
+              ovf = true;
+              if (p == K) continue;
+            } else {
+              ++npp;
+            }
+            for (uint32_t q = npp - 1; q > p; --q) {
+              fid[q] = fid[q - 1];
+              fsl[q] = fsl[q - 1];
+            }
+            fid[p] = jid;
+            fsl[p] = t;
+          }
+        }
+    const size_t n = a.n;
+    for (uint32_t c = 0; c < npp; ++c) {
+      const uint32_t j = fsl[c];
+      float d2;
+      float3 d;
+      const float4 pj = a.spos[j];
+      sphere_hit(pi, pj, &d2, &d);
+      const float dist = __fsqrt_rn(d2);
+      float3 nn;
+      if (dist > 0.f) {
+        nn = make_float3(__fdiv_rn(d.x, dist), __fdiv_rn(d.y, dist), __fdiv_rn(d.z, dist));
+      } else {
+        nn = make_float3(0.f, 0.f, idi > fid[c] ? 1.f : -1.f);
+      }
+      const float psi = __fsub_rn(__fadd_rn(pi.w, pj.w), dist);
+      psi_max = fmaxf(psi_max, psi);
+      const size_t o = (size_t)c * n + i;
+      a.cj[o] = j;
+      a.cn[o] = make_float4(nn.x, nn.y, nn.z, psi);
+      a.clam[o] = 0.f;
+      a.clam[o + (size_t)K * n] = 0.f;
+      a.clam[o + 2 * (size_t)K * n] = 0.f;
+    }
+    // particle-body contacts, bodies in ascending index
+    const float3 xi = make_float3(pi.x, pi.y, pi.z);
+    for (uint32_t b = 0; b < E.nbodies; ++b) {
+      const uint32_t gb = e * a.maxb + b;
+      const DevBody &B = a.bodies[gb];
+      const float3 y = world_to_body(B, xi);
+      int br;
+      const float f = body_sdf(B, y, &br);
+      if (!(f <= pi.w)) continue;
+      if (nbc == a.Kb) {
+        flag(a.ctrl, kFlagBodyOverflow);
+        continue;
+      }
+      const float3 g = body_grad(B, y, br);
+      const float3 nn = rot_apply(B.R, g);
+      const float psi = pi.w - f;
+      psi_max = fmaxf(psi_max, psi);
+      const size_t o = (size_t)nbc * n + i;
+      a.bj[o] = gb;
+      a.bn[o] = make_float4(nn.x, nn.y, nn.z, psi);
+      a.bxc[o] = make_float4(xi.x - f * nn.x, xi.y - f * nn.y, xi.z - f * nn.z, 0.f);
+      a.blam[o] = 0.f;
+      a.blam[o + (size_t)a.Kb * n] = 0.f;
+      a.blam[o + 2 * (size_t)a.Kb * n] = 0.f;
+      ++nbc;
+    }
+    if (ovf) flag(a.ctrl, kFlagPPOverflow);
+    a.ccount[i] = npp | (nbc << 8);
+    const float4 sb = a.sbase[i];
+    a.U[0][i] = make_float4(sb.x, sb.y, sb.z, (float)(npp + nbc) * sb.w);
+  }
+  // per-step statistics (integer atomics: order-independent)
+  uint32_t s_pp = npp, s_b = nbc, m_pp = npp, m_b = nbc;
+  float m_psi = psi_max;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s_pp += __shfl_xor_sync(0xffffffffu, s_pp, o);
+    s_b += __shfl_xor_sync(0xffffffffu, s_b, o);
+    m_pp = max(m_pp, __shfl_xor_sync(0xffffffffu, m_pp, o));
+    m_b = max(m_b, __shfl_xor_sync(0xffffffffu, m_b, o));
+    m_psi = fmaxf(m_psi, __shfl_xor_sync(0xffffffffu, m_psi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (s_pp) atomicAdd(&a.ctrl->n_pp, s_pp);
+    if (s_b) atomicAdd(&a.ctrl->n_body, s_b);
+    if (m_pp) atomicMax(&a.ctrl->max_pp, m_pp);
+    if (m_b) atomicMax(&a.ctrl->max_body, m_b);
+    if (m_psi > 0.f) atomicMax(&a.ctrl->max_psi_bits, __float_as_uint(m_psi));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 6. one projected-Jacobi sweep: U[s] -> U[s^1]
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_pja(StepArgs a, int s) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const float4 *__restrict__ Uin = a.U[s];
+  const size_t n = a.n;
+  const uint32_t cc = a.ccount[i];
+  const uint32_t npp = cc & 0xffu, nbc = (cc >> 8) & 0xffu;
+  const float4 ui = Uin[i];
+  const float4 base = a.sbase[i];
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  const size_t KN = (size_t)a.K * n;
+  for (uint32_t c = 0; c < npp; ++c) {
+    const size_t o = (size_t)c * n + i;
+    const uint32_t j = a.cj[o];
+    const float4 nn = a.cn[o];
+    const float4 uj = Uin[j];
+    const float3 lam = make_float3(a.clam[o], a.clam[o + KN], a.clam[o + 2 * KN]);
+    const float w = 1.0f / (ui.w + uj.w);
+    const float3 u = make_float3(ui.x - uj.x, ui.y - uj.y, ui.z - uj.z);
+    const float3 l = pja_project(lam, u, make_float3(nn.x, nn.y, nn.z), a.ab * nn.w, w, a.mu);
+    a.clam[o] = l.x;
+    a.clam[o + KN] = l.y;
+    a.clam[o + 2 * KN] = l.z;
+    sx += l.x;
+    sy += l.y;
+    sz += l.z;
+  }
+  const size_t KbN = (size_t)a.Kb * n;
+  for (uint32_t c = 0; c < nbc; ++c) {
+    const size_t o = (size_t)c * n + i;
+    const DevBody &B = a.bodies[a.bj[o]];
+    const float4 nn = a.bn[o];
+    const float4 xc = a.bxc[o];
+    const float3 lam = make_float3(a.blam[o], a.blam[o + KbN], a.blam[o + 2 * KbN]);
+    const float rx = xc.x - B.p[0], ry = xc.y - B.p[1], rz = xc.z - B.p[2];
+    const float ubx = B.v[0] + (B.w[1] * rz - B.w[2] * ry);
+    const float uby = B.v[1] + (B.w[2] * rx - B.w[0] * rz);
+    const float ubz = B.v[2] + (B.w[0] * ry - B.w[1] * rx);
+    const float w = 1.0f / ui.w;
+    const float3 u = make_float3(ui.x - ubx, ui.y - uby, ui.z - ubz);
+    const float3 l = pja_project(lam, u, make_float3(nn.x, nn.y, nn.z), a.ab * nn.w, w, a.mu);
+    a.blam[o] = l.x;
+    a.blam[o + KbN] = l.y;
+    a.blam[o + 2 * KbN] = l.z;
+    sx += l.x;
+    sy += l.y;
+    sz += l.z;
+  }
+  a.U[s ^ 1][i] = make_float4(base.x + base.w * sx, base.y + base.w * sy, base.z + base.w * sz, ui.w);
+}
+
+// ---------------------------------------------------------------------------
+// 7. symplectic Euler back into particle-id order
+// ---------------------------------------------------------------------------
+
+__global__ void k_integrate(StepArgs a, int s) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const float4 u = a.U[s][i];
+  const float4 p = a.spos[i];
+  const float4 b = a.sbase[i];
+  const uint32_t id = a.sid[i];
+  const float x = p.x + a.dt * u.x, y = p.y + a.dt * u.y, z = p.z + a.dt * u.z;
+  if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(u.x) && isfinite(u.y) && isfinite(u.z)))
+    flag(a.ctrl, kFlagNonFinite);
+  a.pos_id[id] = make_float4(x, y, z, p.w);
+  a.vel_id[id] = make_float4(u.x, u.y, u.z, b.w);
+}
+
+// ---------------------------------------------------------------------------
+// 8. wrench: per (chunk, body) fixed-order sums, then per body over chunks
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_wrench_partial(StepArgs a) {
+  const uint32_t c = blockIdx.x, lb = blockIdx.y;
+  const uint32_t e = a.chunk_env[c];
+  const DevEnv &E = a.envs[e];
+  if (lb >= E.nbodies) return;
+  const uint32_t gb = e * a.maxb + lb;
+  const DevBody &B = a.bodies[gb];
+  const uint32_t s0 = E.off + (c - E.chunk0) * kWrenchChunk;
+  const uint32_t s1 = min(s0 + kWrenchChunk, E.off + E.n);
+  const size_t n = a.n, KbN = (size_t)a.Kb * n;
+  const float inv_dt = 1.0f / a.dt;
+  float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (uint32_t s = s0 + threadIdx.x; s < s1; s += 256) {
+    const uint32_t nbc = (a.ccount[s] >> 8) & 0xffu;
+    for (uint32_t k = 0; k < nbc; ++k) {
+      const size_t o = (size_t)k * n + s;
+      if (a.bj[o] != gb) continue;
+      const float fx = -a.blam[o] * inv_dt, fy = -a.blam[o + KbN] * inv_dt, fz = -a.blam[o + 2 * KbN] * inv_dt;
+      const float4 xc = a.bxc[o];
+      const float rx = xc.x - B.p[0], ry = xc.y - B.p[1], rz = xc.z - B.p[2];
+      v[0] += fx;
+      v[1] += fy;
+      v[2] += fz;
+      v[3] += ry * fz - rz * fy;
+      v[4] += rz * fx - rx * fz;
+      v[5] += rx * fy - ry * fx;
+    }
+  }
+  block_sum6<256>(v);
+  if (threadIdx.x == 0) {
+    float *dst = a.wpart + ((size_t)c * a.maxb + lb) * 6;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) dst[k] = v[k];
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_wrench_final(StepArgs a) {
+  const uint32_t step = a.ctrl->step;
+  const uint32_t nbt = a.n_envs * a.maxb;
+  for (uint32_t gb = threadIdx.x; gb < nbt; gb += blockDim.x) {
+    DevBody &B = a.bodies[gb];
+    float *dst = a.wrench + ((size_t)(step % a.wrench_hist) * nbt + gb) * 6;
+    if (!B.active) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) dst[k] = 0.f;
+      continue;
+    }
+    const uint32_t e = gb / a.maxb, lb = gb % a.maxb;
+    const DevEnv &E = a.envs[e];
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (uint32_t c = E.chunk0; c < E.chunk0 + E.nchunks; ++c) {
+      const float *src = a.wpart + ((size_t)c * a.maxb + lb) * 6;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) v[k] += src[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) dst[k] = v[k];
+    // pose update with this step's twist: p += dt v, q <- exp(dt w / 2) q
+#pragma unroll
+    for (int k = 0; k < 3; ++k) B.p[k] += a.dt * B.v[k];
+    const float tx = a.dt * B.w[0], ty = a.dt * B.w[1], tz = a.dt * B.w[2];
+    const float ang = sqrtf(tx * tx + ty * ty + tz * tz);
+    if (ang > 0.f) {
+      float sh, ch;
+      sincosf(0.5f * ang, &sh, &ch);
+      const float sc = sh / ang;
+      const float dw = ch, dx = tx * sc, dy = ty * sc, dz = tz * sc;
+      const float qw = B.q[0], qx = B.q[1], qy = B.q[2], qz = B.q[3];
+      float rw = dw * qw - dx * qx - dy * qy - dz * qz;
+      float rx = dw * qx + dx * qw + dy * qz - dz * qy;
+      float ry = dw * qy - dx * qz + dy * qw + dz * qx;
+      float rz = dw * qz + dx * qy - dy * qx + dz * qw;
+      const float inv = rsqrtf(rw * rw + rx * rx + ry * ry + rz * rz);
+      B.q[0] = rw * inv;
+      B.q[1] = rx * inv;
+      B.q[2] = ry * inv;
+      B.q[3] = rz * inv;
+    }
+    if (B.is_free) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        B.own_v[k] = B.v[k];
+        B.own_w[k] = B.w[k];
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) a.ctrl->step = step + 1;
+}
+
+// ---------------------------------------------------------------------------
+// readback helpers (outside the step)
+// ---------------------------------------------------------------------------
+
+__global__ void k_export_contacts(StepArgs a, uint32_t *rows, float *geom, float *lam, float *bgeom, float *blam) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.n) return;
+  const uint32_t id = a.sid[s];
+  const uint32_t K = a.K, Kb = a.Kb, W = 2 + K + Kb;
+  const size_t n = a.n;
+  const uint32_t cc = a.ccount[s];
+  const uint32_t npp = cc & 0xffu, nbc = (cc >> 8) & 0xffu;
+  if (rows) {
+    uint32_t *r = rows + (size_t)id * W;
+    r[0] = npp;
+    r[1] = nbc;
+    for (uint32_t c = 0; c < K; ++c) r[2 + c] = c < npp ? a.sid[a.cj[(size_t)c * n + s]] : 0xffffffffu;
+    for (uint32_t c = 0; c < Kb; ++c) r[2 + K + c] = c < nbc ? a.bj[(size_t)c * n + s] % a.maxb : 0xffffffffu;
+  }
+  for (uint32_t c = 0; c < K; ++c) {
+    const size_t o = (size_t)c * n + s;
+    const bool on = c < npp;
+    if (geom) {
+      float4 g = on ? a.cn[o] : make_float4(0.f, 0.f, 0.f, 0.f);
+      float *d = geom + ((size_t)id * K + c) * 4;
+      d[0] = g.x;
+      d[1] = g.y;
+      d[2] = g.z;
+      d[3] = g.w;
+    }
+    if (lam) {
+      float *d = lam + ((size_t)id * K + c) * 3;
+      d[0] = on ? a.clam[o] : 0.f;
+      d[1] = on ? a.clam[o + (size_t)K * n] : 0.f;
+      d[2] = on ? a.clam[o + 2 * (size_t)K * n] : 0.f;
+    }
+  }
+  for (uint32_t c = 0; c < Kb; ++c) {
+    const size_t o = (size_t)c * n + s;
+    const bool on = c < nbc;
+    if (bgeom) {
+      float4 g = on ? a.bn[o] : make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 x = on ? a.bxc[o] : make_float4(0.f, 0.f, 0.f, 0.f);
+      float *d = bgeom + ((size_t)id * Kb + c) * 8;
+      d[0] = g.x;
+      d[1] = g.y;
+      d[2] = g.z;
+      d[3] = g.w;
+      d[4] = x.x;
+      d[5] = x.y;
+      d[6] = x.z;
+      d[7] = 0.f;
+    }
+    if (blam) {
+      float *d = blam + ((size_t)id * Kb + c) * 3;
+      d[0] = on ? a.blam[o] : 0.f;
+      d[1] = on ? a.blam[o + (size_t)Kb * n] : 0.f;
+      d[2] = on ? a.blam[o + 2 * (size_t)Kb * n] : 0.f;
+    }
+  }
+}
+
+// float[n][4] / float[n][3] conversions for user-facing particle arrays
+__global__ void k_vel3_to_vel4(float4 *vel_id, const float *vel3, uint32_t n) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 v = vel_id[i];
+  vel_id[i] = make_float4(vel3[3 * i], vel3[3 * i + 1], vel3[3 * i + 2], v.w);
+}
+
+__global__ void k_vel4_to_vel3(const float4 *vel_id, float *vel3, uint32_t n) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 v = vel_id[i];
+  vel3[3 * i] = v.x;
+  vel3[3 * i + 1] = v.y;
+  vel3[3 * i + 2] = v.z;
+}
+
+__global__ void k_body_state(const DevBody *bodies, uint32_t nbt, float *out) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbt) return;
+  const DevBody &B = bodies[b];
+  float *d = out + (size_t)b * 16;
+  for (int k = 0; k < 3; ++k) d[k] = B.p[k];
+  for (int k = 0; k < 4; ++k) d[3 + k] = B.q[k];
+  for (int k = 0; k < 3; ++k) d[7 + k] = B.own_v[k];
+  for (int k = 0; k < 3; ++k) d[10 + k] = B.own_w[k];
+  d[13] = d[14] = d[15] = 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+static inline unsigned grid_for(uint32_t n, int bs) { return (n + bs - 1) / bs > 0 ? (n + bs - 1) / bs : 1; }
+
+cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st) {
+  const uint32_t nbt = a.n_envs * a.maxb;
+  const uint32_t nk = a.n > nbt ? a.n : nbt;
+  k_key<<<grid_for(nk, 256), 256, 0, st>>>(a);
+  const uint32_t nblk = a.nh_pad / kScanTile;
+  k_scan_reduce<<<nblk, kScanThreads, 0, st>>>(a);
+  k_scan_top<<<1, 1024, 0, st>>>(a, nblk);
+  k_scan_down<<<nblk, kScanThreads, 0, st>>>(a);
+  if (a.n) {
+    k_scatter<<<grid_for(a.n, 256), 256, 0, st>>>(a);
+    k_reorder<<<grid_for(a.n, 256), 256, 0, st>>>(a);
+    k_contacts<<<grid_for(a.n, 256), 256, 0, st>>>(a);
+    for (uint32_t it = 0; it < ls.iters; ++it) k_pja<<<grid_for(a.n, ls.pja_block), ls.pja_block, 0, st>>>(a, it & 1);
+    k_integrate<<<grid_for(a.n, 256), 256, 0, st>>>(a, ls.iters & 1);
+  }
+  if (a.n_chunks) {
+    dim3 g(a.n_chunks, a.maxb);
+    k_wrench_partial<<<g, 256, 0, st>>>(a);
+  }
+  k_wrench_final<<<1, 1024, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_export_contacts(const StepArgs &a, uint32_t *rows, float *geom, float *lam, float *bgeom,
+                                    float *blam, cudaStream_t st) {
+  if (a.n) k_export_contacts<<<grid_for(a.n, 256), 256, 0, st>>>(a, rows, geom, lam, bgeom, blam);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_vel3_to_vel4(float4 *vel_id, const float *vel3, uint32_t n, cudaStream_t st) {
+  if (n) k_vel3_to_vel4<<<grid_for(n, 256), 256, 0, st>>>(vel_id, vel3, n);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_vel4_to_vel3(const float4 *vel_id, float *vel3, uint32_t n, cudaStream_t st) {
+  if (n) k_vel4_to_vel3<<<grid_for(n, 256), 256, 0, st>>>(vel_id, vel3, n);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_body_state(const DevBody *bodies, uint32_t nbt, float *out, cudaStream_t st) {
+  if (nbt) k_body_state<<<grid_for(nbt, 128), 128, 0, st>>>(bodies, nbt, out);
+  return cudaGetLastError();
+}
+
+}  // namespace gg

@@ -1,0 +1,70 @@
+"""C ABI checks that need no GPU: the library builds, loads, and exports every
+function include/gg.h declares (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2306_01369_gb300 import _build, gg
+    _build.build()
+    return gg.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "gg.h")).read()
+    return sorted(set(re.findall(r"^GG_API[^;]*?\b(gg_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_api():
+    names = _declared()
+    for n in ("gg_create", "gg_create_batch", "gg_set_bodies", "gg_step", "gg_readback", "gg_destroy"):
+        assert n in names
+    assert len(names) >= 16
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+    from paper_2306_01369_gb300 import gg
+    assert set(_declared()) == set(gg.SIGNATURES), "binding and header disagree"
+
+
+def test_library_exports_nothing_else():
+    from paper_2306_01369_gb300 import gg
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", gg.LIB_PATH], capture_output=True, text=True).stdout
+    syms = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert syms == set(_declared())
+
+
+def test_host_only_calls(lib):
+    assert lib.gg_abi_version() == 1
+    assert lib.gg_status_string(0) == b"ok"
+    assert lib.gg_status_string(4) == b"contact capacity overflow"
+    assert lib.gg_tuning_count() >= 2
+    assert lib.gg_last_error(None) == b"null simulation"
+    lib.gg_destroy(None)   # no-op
+
+
+def test_struct_sizes_match_header():
+    """The ctypes mirrors must have the C layout: 16 4-byte fields + arrays."""
+    from paper_2306_01369_gb300 import gg
+    assert ctypes.sizeof(gg.GGParams) == 4 * 17
+    assert ctypes.sizeof(gg.GGBody) == 4 * (2 + 12 + 3 + 4 + 3 + 3 + 1 + 3)
+    assert ctypes.sizeof(gg.GGStats) == 8 + 4 * 6
+
+
+def test_create_rejects_bad_params_before_touching_a_device(lib):
+    """Invalid parameter structs are rejected by argument checks (no CUDA call needed)."""
+    from paper_2306_01369_gb300 import gg
+    p = gg.GGParams()
+    p.struct_size = 3   # wrong version
+    h = ctypes.c_void_p()
+    assert lib.gg_create(ctypes.byref(p), 0, None, None, None, 0, ctypes.byref(h)) == gg.ERR_INVALID_ARG
+    assert lib.gg_create(None, 0, None, None, None, 0, ctypes.byref(h)) == gg.ERR_INVALID_ARG

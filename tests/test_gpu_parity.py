@@ -1,0 +1,352 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Integer work -- bucket keys, sort permutation, bucket table, contact sets and
+their order -- must match bit for bit, in lockstep: the GPU's FP32 state after k
+steps is handed to the oracle's binning and contact stages.  Dynamics are
+compared with tolerances: after one step every velocity within 1e-5 of the
+scene's velocity scale, and after ten steps every position within 1e-3 r_i.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_helpers import (F32, assert_contacts_equal, bodies_from_gpu, need_gpu, oracle_from_gpu, vel_err)
+from paper_2306_01369_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return need_gpu()
+
+
+@pytest.fixture(scope="module")
+def gg(torch):
+    from paper_2306_01369_gb300 import gg
+    return gg
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def squeezed_box(n=4096, factor=0.96, seed=1000, vel_scale=0.05):
+    sc = S.settle_box(n=n, seed=seed)
+    sc.pos_r[:, :3] = (sc.pos_r[:, :3] - np.float32(0.1)) * np.float32(factor) + np.float32(0.1)
+    sc.pos_r[:, 2] += np.float32(0.006)
+    rng = np.random.default_rng(seed)
+    sc.vel = (vel_scale * rng.uniform(-1, 1, (n, 3))).astype(F32)
+    return sc
+
+
+# --------------------------------------------------------------------------- #
+# bit-exact integer stages
+# --------------------------------------------------------------------------- #
+
+@pytest.mark.parametrize("n,hash_size", [(4096, 0), (3001, 0), (2000, 97)])
+def test_binning_sort_table_bit_exact(gg, orc, n, hash_size):
+    sc = squeezed_box(n)
+    sc.params.hash_size = hash_size
+    sim = gg.Sim.from_scene(sc)
+    sim.step(1)
+    sim.sync()
+    nh = hash_size or 2 * n
+    cs = orc.default_cell_size(float(sc.pos_r[:, 3].max()))
+    keys = orc.cell_keys(sc.pos_r[:, :3].astype(np.float64), cs, nh)
+    assert np.array_equal(sim.cell_keys(), keys)
+    perm = orc.sort_perm(keys)
+    assert np.array_equal(sim.sort_perm(), perm)
+    start = np.zeros(nh + 1, np.uint32)
+    np.add.at(start, keys.astype(np.int64) + 1, 1)
+    start = np.cumsum(start).astype(np.uint32)
+    assert np.array_equal(sim.cell_start(), start)
+
+
+@pytest.mark.parametrize("steps_before", [0, 3, 40])
+def test_contacts_bit_exact_lockstep(gg, orc, steps_before):
+    sc = squeezed_box(4096)
+    sim = gg.Sim.from_scene(sc)
+    sim.step(steps_before)
+    o = oracle_from_gpu(sim, sc, steps_before)
+    want = o.contacts()
+    sim.step(1)
+    sim.sync()
+    got = sim.contacts()
+    assert want["stats"]["n_pp"] > 5000 and want["stats"]["n_body"] > 100
+    assert_contacts_equal(got, want)
+    # brute force agrees too (the bucket walk misses nothing)
+    brute = o.contacts(brute=True)
+    assert np.array_equal(brute["pp_j"], want["pp_j"])
+
+
+def test_contacts_bit_exact_random_cloud_tiny_table(gg, orc):
+    """Many hash collisions (n_h = 5) force duplicate buckets in the 27-cell walk."""
+    pr, vel = S.random_cloud(1500, seed=21, box=0.05, overlap=0.5)
+    p = S.Params(dt=1e-4, gravity=(0, 0, 0), mu=0.5, pja_iters=5, hash_size=5, max_contacts=32)
+    sim = gg.Sim(pr, vel, S.sphere_mass(pr[:, 3]), p)
+    sim.step(1)
+    sim.sync()
+    want = orc.contacts(pr[:, :3], pr[:, 3], [], p)
+    assert want["stats"]["max_pp"] <= 32
+    assert_contacts_equal(sim.contacts(), want)
+
+
+# --------------------------------------------------------------------------- #
+# dynamics
+# --------------------------------------------------------------------------- #
+
+def test_one_step_dynamics(gg, orc):
+    sc = squeezed_box(4096)
+    sim = gg.Sim.from_scene(sc)
+    o = orc.Sim(sc.pos_r, sc.vel, sc.mass, sc.bodies, sc.params)
+    sim.step(1)
+    o.step(1)
+    err = vel_err(sim.vel(), o.v, sc.params.dt)
+    assert err < 1e-5, err
+    dx = np.abs(sim.pos()[:, :3].astype(np.float64) - o.x).max()
+    assert dx < 1e-5 * max(float(np.abs(o.x).max()), 0.2), dx
+
+
+@pytest.mark.parametrize("steps_before", [5, 60])
+def test_one_step_dynamics_lockstep(gg, orc, steps_before):
+    sc = squeezed_box(4096)
+    sim = gg.Sim.from_scene(sc)
+    sim.step(steps_before)
+    o = oracle_from_gpu(sim, sc, steps_before)
+    sim.step(1)
+    o.step(1)
+    assert vel_err(sim.vel(), o.v, sc.params.dt) < 1e-5
+
+
+def test_contact_geometry_and_impulses(gg, orc):
+    sc = squeezed_box(2048)
+    sim = gg.Sim.from_scene(sc)
+    sim.step(4)
+    o = oracle_from_gpu(sim, sc, 4)
+    want = o.contacts()
+    npp, nbc = int(want["pp_off"][-1]), int(want["bc_off"][-1])
+    lam = np.zeros((npp, 3))
+    blam = np.zeros((nbc, 3))
+    o.step(1, pp_lam=lam, bc_lam=blam)
+    sim.step(1)
+    got = sim.contacts()
+    assert_contacts_equal(got, want)
+    assert np.abs(got["pp_geom"][:, :3] - want["pp_geom"][:, :3]).max() < 1e-5
+    assert np.abs(got["pp_geom"][:, 3] - want["pp_geom"][:, 3]).max() < 1e-7 * 1   # psi in metres
+    assert np.abs(got["bc_geom"][:, :3] - want["bc_geom"][:, :3]).max() < 1e-5
+    assert np.abs(got["bc_geom"][:, 3] - want["bc_geom"][:, 3]).max() < 1e-7
+    scale = max(np.abs(lam).max(), np.abs(blam).max())
+    assert np.abs(got["pp_lam"] - lam).max() < 1e-4 * scale
+    assert np.abs(got["bc_lam"] - blam).max() < 1e-4 * scale
+
+
+def test_ten_steps_within_radius_fraction(gg, orc):
+    sc = squeezed_box(4096)
+    sim = gg.Sim.from_scene(sc)
+    o = orc.Sim(sc.pos_r, sc.vel, sc.mass, sc.bodies, sc.params, n_threads=4)
+    sim.step(10)
+    o.step(10)
+    d = np.linalg.norm(sim.pos()[:, :3].astype(np.float64) - o.x, axis=1)
+    assert np.all(d <= 1e-3 * sc.pos_r[:, 3]), float((d / sc.pos_r[:, 3]).max())
+
+
+def test_momentum_and_antisymmetric_impulses(gg, orc):
+    pr, vel = S.random_cloud(3000, seed=9, box=0.06, overlap=0.5, vel_scale=0.3)
+    m = S.sphere_mass(pr[:, 3])
+    p = S.Params(dt=1e-4, gravity=(0, 0, 0), mu=0.4, pja_iters=20, max_contacts=32)
+    sim = gg.Sim(pr, vel, m, p)
+    sim.step(1)
+    c = sim.contacts()
+    off, jj, lam = c["pp_off"], c["pp_j"], c["pp_lam"]
+    assert off[-1] > 1000
+    # lambda_ji == -lambda_ij bit for bit
+    pos = {}
+    for i in range(len(off) - 1):
+        for k in range(off[i], off[i + 1]):
+            pos[(i, int(jj[k]))] = k
+    for (i, j), k in pos.items():
+        assert np.array_equal(lam[pos[(j, i)]], -lam[k])
+    sim.step(4)
+    v = sim.vel().astype(np.float64)
+    P0 = (m[:, None].astype(np.float64) * vel).sum(0)
+    P1 = (m[:, None].astype(np.float64) * v).sum(0)
+    scale = (m[:, None] * np.abs(vel)).sum()
+    assert np.abs(P1 - P0).max() < 2e-6 * scale
+
+
+def test_resting_sphere_baumgarte_decay(gg):
+    r = F32(0.005)
+    psi0 = 1e-6
+    pr = np.array([[0.0, 0.0, F32(float(r) - psi0), r]], F32)
+    p = S.Params(dt=1e-4, mu=0.5, alpha=0.2, pja_iters=20)
+    sim = gg.Sim(pr, np.zeros((1, 3), F32), np.array([0.01], F32), p)
+    sim.set_bodies([S.Body(kind=S.PLANE)])
+    psi = float(r) - float(pr[0, 2])
+    for k in range(1, 6):
+        sim.step(1)
+        got = float(r) - float(sim.pos()[0, 2])
+        want = (1 - 0.2) ** k * psi
+        assert abs(got - want) < 4 * 2 ** -24 * 0.005 * k, (k, got, want)
+
+
+@pytest.mark.parametrize("dtheta_deg", [-2.0, 2.0])
+def test_incline_threshold(gg, dtheta_deg):
+    mu = 0.5
+    theta = math.atan(mu) + math.radians(dtheta_deg)
+    quat = (math.cos(theta / 2), math.sin(theta / 2), 0.0, 0.0)
+    r = 0.005
+    nrm = np.array([0.0, -math.sin(theta), math.cos(theta)])
+    x0 = (r - 1e-8) * nrm
+    pr = np.array([[x0[0], x0[1], x0[2], r]], F32)
+    sim = gg.Sim(pr, np.zeros((1, 3), F32), np.array([0.02], F32), S.Params(dt=1e-4, mu=mu, alpha=0.0, pja_iters=20))
+    sim.set_bodies([S.Body(kind=S.PLANE, quat=quat)])
+    sim.step(1)
+    v = sim.vel()[0].astype(np.float64)
+    vt = v - np.dot(v, nrm) * nrm
+    want = 1e-4 * 9.81 * max(0.0, math.sin(theta) - mu * math.cos(theta))
+    assert abs(np.linalg.norm(vt) - want) < 1e-5 * 9.81e-4 + 1e-6 * want
+
+
+def test_wrench_matches_oracle_with_kinematic_scoop(gg, orc):
+    sc = S.scoop_bed(n=4096, n_steps=60, dims=(16, 16, 16))
+    sim = gg.Sim.from_scene(sc, wrench_history=8)
+    sim.step(50)
+    o = oracle_from_gpu(sim, sc, 50)
+    want = o.contacts()
+    sim.step(1)
+    o.step(1)
+    got = sim.contacts()
+    assert_contacts_equal(got, want)
+    w = sim.wrench()[-1, :len(sc.bodies)].astype(np.float64)
+    scale = np.abs(o.wrench[:len(sc.bodies)]).max()
+    assert scale > 0
+    assert np.abs(w - o.wrench[:len(sc.bodies)]).max() < 2e-4 * scale
+    assert vel_err(sim.vel(), o.v, sc.params.dt) < 1e-5
+    # kinematic pose follows the prescribed twist
+    bs = sim.body_state()[1]
+    assert np.allclose(bs[0:3], o.body_pose(1)[0:3], atol=1e-6)
+    assert np.allclose(np.abs(np.dot(bs[3:7], o.body_pose(1)[3:7])), 1.0, atol=1e-6)
+
+
+def test_scoop_scene_ten_steps(gg, orc):
+    sc = S.scoop_bed(n=4096, n_steps=40, dims=(16, 16, 16))
+    sim = gg.Sim.from_scene(sc)
+    sim.step(20)
+    o = oracle_from_gpu(sim, sc, 20)
+    sim.step(10)
+    o.step(10)
+    d = np.linalg.norm(sim.pos()[:, :3].astype(np.float64) - o.x, axis=1)
+    assert np.all(d <= 1e-3 * sc.pos_r[:, 3])
+
+
+# --------------------------------------------------------------------------- #
+# invariance, determinism, checkpoints
+# --------------------------------------------------------------------------- #
+
+def test_results_invariant_to_launch_shape_and_table_size(gg):
+    sc = squeezed_box(3000)
+    ref = None
+    for tuning in range(1, gg.load().gg_tuning_count() + 1):
+        for hf in (0, 1, 4):
+            sim = gg.Sim.from_scene(sc, tuning=tuning, hash_factor=hf)
+            sim.step(6)
+            out = np.concatenate([sim.pos().ravel(), sim.vel().ravel()])
+            if ref is None:
+                ref = out
+            assert np.array_equal(out, ref), (tuning, hf)
+            sim.close()
+
+
+def test_run_to_run_deterministic(gg):
+    sc = squeezed_box(4096)
+    outs = []
+    for _ in range(3):
+        sim = gg.Sim.from_scene(sc)
+        sim.step(15)
+        outs.append(sim.pos().copy())
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
+
+
+def test_checkpoint_resume_bit_exact(gg):
+    sc = S.scoop_bed(n=4096, n_steps=40, dims=(16, 16, 16))
+    a = gg.Sim.from_scene(sc)
+    a.step(20)
+    b = gg.Sim.from_scene(sc)
+    b.step(10)
+    blob = b.state()
+    b.step(3)   # wander off, then come back
+    b.set_state(blob)
+    b.step(10)
+    assert np.array_equal(a.pos(), b.pos()) and np.array_equal(a.vel(), b.vel())
+    assert np.array_equal(a.body_state(), b.body_state())
+
+
+# --------------------------------------------------------------------------- #
+# edge cases and errors
+# --------------------------------------------------------------------------- #
+
+def test_empty_and_single_particle(gg):
+    p = S.Params(dt=1e-4)
+    sim = gg.Sim(np.zeros((0, 4), F32), np.zeros((0, 3), F32), np.zeros(0, F32), p)
+    sim.set_bodies([S.Body(kind=S.PLANE)])
+    sim.step(3)
+    sim.sync()
+    assert sim.stats()["steps"] == 3
+    one = gg.Sim(np.array([[0, 0, 1.0, 0.01]], F32), None, None, p)
+    one.step(10)
+    v = one.vel()
+    assert abs(v[0, 2] + 10 * float(F32(1e-4)) * float(F32(9.81))) < 1e-6
+
+
+def test_overflow_is_reported(gg):
+    pr, vel = S.random_cloud(500, seed=3, box=0.02, overlap=0.5)
+    p = S.Params(dt=1e-4, max_contacts=2)
+    sim = gg.Sim(pr, vel, S.sphere_mass(pr[:, 3]), p)
+    sim.step(1)
+    with pytest.raises(gg.GGError) as e:
+        sim.sync()
+    assert e.value.status == gg.ERR_CONTACT_OVERFLOW
+
+
+def test_invalid_arguments(gg):
+    p = S.Params(dt=1e-4)
+    with pytest.raises(gg.GGError) as e:
+        gg.Sim(np.array([[0, 0, 0, -1.0]], F32), None, None, p)   # negative radius
+    assert e.value.status == gg.ERR_INVALID_ARG
+    bad = S.Params(dt=-1.0)
+    with pytest.raises(gg.GGError):
+        gg.Sim(np.array([[0, 0, 0, 1.0]], F32), None, None, bad)
+    sim = gg.Sim(np.array([[0, 0, 0, 1.0]], F32), None, None, p)
+    with pytest.raises(gg.GGError):
+        sim.set_bodies([S.Body(kind=9)])
+    with pytest.raises(gg.GGError):
+        sim.set_trajectory(3, np.zeros((4, 6), F32))   # no such body
+
+
+# --------------------------------------------------------------------------- #
+# full size: the column-collapse workload of the benchmark
+# --------------------------------------------------------------------------- #
+
+def test_column_collapse_full_size_parity(gg, orc):
+    """262,144 spheres: bit-exact binning and contacts and one-step velocities, in
+    lockstep after the bottom layers have landed."""
+    sc = S.column_collapse()
+    sim = gg.Sim.from_scene(sc)
+    sim.step(300)
+    o = oracle_from_gpu(sim, sc, 300, n_threads=8)
+    cs = orc.default_cell_size(float(sc.pos_r[:, 3].max()))
+    keys = orc.cell_keys(o.x, cs, 2 * sc.n)
+    want = o.contacts()
+    sim.step(1)
+    o.step(1)
+    assert np.array_equal(sim.cell_keys(), keys)
+    assert np.array_equal(sim.sort_perm(), orc.sort_perm(keys))
+    got = sim.contacts()
+    assert want["stats"]["n_pp"] > 10000
+    assert_contacts_equal(got, want)
+    assert vel_err(sim.vel(), o.v, sc.params.dt) < 1e-5
