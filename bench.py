@@ -1,0 +1,367 @@
+"""Benchmark of the granular contact step (GranularGym, arxiv 2306.01369) on GB300.
+
+Workload: granular column collapse of 262,144 FP32 spheres (r = 2 mm +-10 %,
+40x40-site column at 4.49 mm pitch, released onto a ground plane), mu = 0.6,
+dt = 5e-5 s, 20 projected-Jacobi iterations.  One "step" is one time step of the
+whole pipeline (binning, sort, contacts, PJA, integration, wrench).  The metric is
+particle-steps/s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Timing: K time steps after W untimed ones, each bracketed by CUDA events on the
+stream the library launches on, with an L2 flush (a 512 MiB write) between timed
+steps, outside the events.  The dominant kernel (the PJA sweep) is timed by
+events recorded inside the step graph.  Multi-GPU: one process per GPU
+(torchrun); each rank steps its own replica of the column (the single-scene
+path does not shard), barrier + max over ranks.  `--impl reference` times the
+FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (20 PJA iters)"
+UNIT = "particle-steps/s"
+WORKLOAD = "column_collapse_262144"
+
+
+def workload_config(sc):
+    return {"workload": WORKLOAD, "n_particles": sc.n, "pja_iters": sc.params.pja_iters, "dt": sc.params.dt,
+            "mu": sc.params.mu, "alpha": sc.params.alpha, "radius_m": "2e-3 +-10%", "column_sites": "40x40x164",
+            "bodies": "ground plane", "l2": "flushed between timed steps (512 MiB write)"}
+
+
+# --------------------------------------------------------------------------- #
+# distributed plumbing (host logic, covered by gloo tests)
+# --------------------------------------------------------------------------- #
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Max of a float over all ranks (identity when world == 1)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------- #
+# clocks during the timed region
+# --------------------------------------------------------------------------- #
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- #
+# roofline figures of the dominant kernel
+# --------------------------------------------------------------------------- #
+
+def pja_bytes(n: int, n_pp: int, n_body: int) -> int:
+    """Algorithmic DRAM bytes of one k_pja launch (each array read or written once):
+    per particle: velocity estimate in 16 + base velocity 16 + counts 4 + estimate out 16;
+    per particle-particle contact: partner 4 + normal/psi 16 + impulse in 12 + out 12;
+    per particle-body contact: body 4 + normal/psi 16 + contact point 16 + impulse 24."""
+    return 52 * n + 44 * n_pp + 60 * n_body
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profile_traffic(kernel_digest: str):
+    """ncu DRAM bytes per launch of k_pja from the committed profile summary, if
+    it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_pja_column_collapse.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_digest") != kernel_digest:
+        return None
+    return d.get("dram_bytes_per_launch_full_size")
+
+
+def kernel_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("gg_kernels.cu", "gg_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2306_01369_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# --------------------------------------------------------------------------- #
+# arms
+# --------------------------------------------------------------------------- #
+
+def oracle_sample(sc, state_pos, state_vel, seconds=15.0, max_steps=8, threads=None):
+    """Time the FP64 oracle, as it stands, on the column state: whole steps of all
+    n particles until `seconds` have passed (at least one step)."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    o = oracle.Sim(state_pos, state_vel, sc.mass, sc.bodies, sc.params, n_threads=threads)
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        o.step(1)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": sc.n * steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{steps} full time steps of the {sc.n}-sphere column (FP64 C oracle, {threads} OpenMP "
+                      f"threads) from the GPU state at the end of the timed region; {el:.1f} s"}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, same metric and workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2306_01369_gb300 import scenes
+    import oracle
+    oracle.build()
+    sc = scenes.column_collapse()
+    threads = os.cpu_count() or 1
+    # bounded sample per step: a contiguous block of the column (its lowest layers,
+    # where contacts form first), advanced one oracle time step
+    m = 16384
+    sub_pos = sc.pos_r[:m].copy()
+    sub_vel = sc.vel[:m].copy()
+    o = oracle.Sim(sub_pos, sub_vel, sc.mass[:m], sc.bodies, sc.params, n_threads=threads)
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    el = time.perf_counter() - t0
+    v = m * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(sc),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"each step: one FP64 oracle time step of the lowest {m} spheres of the "
+                                       f"column (same recipe), {threads} OpenMP threads"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2306_01369_gb300 import _build, gg, scenes
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _build.build()
+
+    sc = scenes.column_collapse(seed=1001 + rank)
+    sim = gg.Sim.from_scene(sc, tuning=args.tuning)
+    stream = torch.cuda.current_stream(dev)
+    sim.enable_timing(True)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # warm-up (also builds the step graph)
+    for _ in range(args.warmup):
+        sim.step(1, stream=stream)
+    sim.sync(stream)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    step_ms, pja_ms, pja_bytes_tot = [], 0.0, 0
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    for k in range(args.steps):
+        flush.fill_(float(k))                     # evict L2 between timed steps (outside the events)
+        ev0[k].record(stream)
+        sim.step(1, stream=stream)
+        ev1[k].record(stream)
+        st = sim.stage_ms()                       # waits for this step
+        pja_ms += st["pja"]
+        s = sim.stats()
+        pja_bytes_tot += sc.params.pja_iters * pja_bytes(sc.n, s["n_pp"], s["n_body"])
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    for k in range(args.steps):
+        step_ms.append(ev0[k].elapsed_time(ev1[k]))
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    sim.sync(stream)
+    stats = sim.stats()
+    value = sum_over_ranks(float(sc.n * args.steps), world, dev) / (total_ms * 1e-3)
+
+    # roofline of the dominant kernel: k_pja, I launches per step
+    launches = args.steps * sc.params.pja_iters
+    avg_launch_s = pja_ms * 1e-3 / launches
+    bytes_per_launch = pja_bytes_tot / launches
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    roof = {"bound": "hbm", "kernel": "k_pja", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+            "traffic": profile_traffic(kernel_digest()), "bytes_per_launch": bytes_per_launch,
+            "avg_launch_us": avg_launch_s * 1e6, "share_of_step": pja_ms / sum(step_ms)}
+
+    # end to end through the public API with host buffers: H2D of the state, one
+    # step, D2H of the new state, every step
+    e2e_steps = min(args.steps, args.e2e_steps)
+    pos_h = torch.from_numpy(sim.pos()).pin_memory()
+    vel_h = torch.from_numpy(sim.vel()).pin_memory()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.set_particles(pos_h, vel_h, stream=stream)
+        sim.step(1, stream=stream)
+        sim.read("POS", out=pos_h.numpy(), stream=stream)
+        sim.read("VEL", out=vel_h.numpy(), stream=stream)
+    torch.cuda.synchronize(dev)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_val = sum_over_ranks(float(sc.n * e2e_steps), world, dev) / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(sc, sim.pos(), sim.vel(), seconds=args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {**workload_config(sc), "replicas": world, "tuning_set": sim.tuning_selected},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_val, "unit": UNIT, "steps": e2e_steps,
+                        "h2d_bytes_per_step": sc.n * (16 + 12), "d2h_bytes_per_step": sc.n * (16 + 12)},
+                "gpu_launches": sim.kernels_per_step * args.steps, "clocks": clk,
+                "stage_ms_last_step": sim.stage_ms(),
+                "contacts_last_step": {"n_pp": stats["n_pp"], "n_body": stats["n_body"],
+                                       "mean_pp_per_particle": stats["n_pp"] / sc.n}}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gg", "reference"], default="gg")
+    ap.add_argument("--tuning", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -201,6 +201,20 @@ GG_API gg_status gg_readback(gg_sim *sim, gg_field field, void *dst, size_t byte
 /* Restore a GG_FIELD_STATE checkpoint taken from a simulation with the same sizes. */
 GG_API gg_status gg_set_state(gg_sim *sim, const void *state, size_t bytes, int on_device, void *stream);
 
+/*
+ * Stage timing.  gg_enable_timing(sim, 1) records CUDA events inside every
+ * subsequent step (the step graph is re-captured); gg_stage_ms then waits for the
+ * last enqueued step and writes its device time in milliseconds per stage into
+ * ms[GG_NUM_STAGES]: binning + sort, contact build, all projected-Jacobi
+ * iterations, integration + wrench.  Returns GG_ERR_INVALID_ARG when timing is off.
+ */
+#define GG_NUM_STAGES 4
+GG_API gg_status gg_enable_timing(gg_sim *sim, int on);
+GG_API gg_status gg_stage_ms(gg_sim *sim, float *ms);
+
+/* Kernel launches one step enqueues (all of them this library's own kernels). */
+GG_API uint32_t gg_kernels_per_step(const gg_sim *sim);
+
 /* Number of fixed launch-shape sets accepted by gg_params.tuning, and the set chosen. */
 GG_API uint32_t gg_tuning_count(void);
 GG_API uint32_t gg_tuning_selected(const gg_sim *sim);

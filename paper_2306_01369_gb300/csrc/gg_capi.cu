@@ -59,6 +59,8 @@ struct gg_sim {
   void *staging = nullptr;
   size_t staging_bytes = 0;
   float *vel3 = nullptr;  // n*3 staging for velocity upload / readback
+  bool timing = false;
+  cudaEvent_t ev[5] = {};
   std::string err;
 };
 
@@ -135,7 +137,7 @@ bool finite_pos(float v) { return std::isfinite(v); }
 gg_status capture(gg_sim *s) {
   free_graph(s);
   GG_CUDA(s, cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = gg::enqueue_step(s->a, s->ls, s->cap);
+  cudaError_t e = gg::enqueue_step(s->a, s->ls, s->cap, s->timing ? s->ev : nullptr);
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
   if (e != cudaSuccess) {
@@ -174,6 +176,28 @@ const char *gg_last_error(const gg_sim *sim) { return sim ? sim->err.c_str() : "
 
 uint32_t gg_tuning_count(void) { return kNumShapes; }
 
+uint32_t gg_kernels_per_step(const gg_sim *sim) { return sim ? gg::kernels_per_step(sim->a, sim->ls) : 0; }
+
+gg_status gg_enable_timing(gg_sim *s, int on) {
+  if (!s) return GG_ERR_INVALID_ARG;
+  if (on && !s->ev[0])
+    for (cudaEvent_t &ev : s->ev) GG_CUDA(s, cudaEventCreate(&ev));
+  if ((bool)on != s->timing) {
+    GG_CUDA(s, cudaDeviceSynchronize());
+    s->timing = on != 0;
+    free_graph(s);
+  }
+  return GG_OK;
+}
+
+gg_status gg_stage_ms(gg_sim *s, float *ms) {
+  if (!s || !ms) return GG_ERR_INVALID_ARG;
+  if (!s->timing || !s->steps) return fail(s, GG_ERR_INVALID_ARG, "gg_stage_ms: timing off or no step taken");
+  GG_CUDA(s, cudaEventSynchronize(s->ev[4]));
+  for (int k = 0; k < GG_NUM_STAGES; ++k) GG_CUDA(s, cudaEventElapsedTime(&ms[k], s->ev[k], s->ev[k + 1]));
+  return GG_OK;
+}
+
 uint32_t gg_tuning_selected(const gg_sim *sim) { return sim ? sim->tuning_sel : 0; }
 
 void gg_destroy(gg_sim *sim) {
@@ -181,6 +205,8 @@ void gg_destroy(gg_sim *sim) {
   cudaSetDevice(sim->device);
   cudaDeviceSynchronize();
   free_graph(sim);
+  for (cudaEvent_t &ev : sim->ev)
+    if (ev) cudaEventDestroy(ev);
   if (sim->cap) cudaStreamDestroy(sim->cap);
   for (void *p : sim->allocs) cudaFree(p);
   for (float *t : sim->traj)

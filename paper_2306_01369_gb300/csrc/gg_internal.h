@@ -12,7 +12,9 @@ struct LaunchShape {
   int pja_block;       // threads per block of k_pja
 };
 
-cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st);
+// ev (optional): 5 events recorded at the stage boundaries of the step.
+cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st, cudaEvent_t *ev = nullptr);
+uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls);
 cudaError_t enqueue_export_contacts(const StepArgs &a, uint32_t *rows, float *geom, float *lam, float *bgeom,
                                     float *blam, cudaStream_t st);
 cudaError_t enqueue_vel3_to_vel4(float4 *vel_id, const float *vel3, uint32_t n, cudaStream_t st);

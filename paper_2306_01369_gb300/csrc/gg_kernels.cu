@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(256) k_contacts(StepArgs a) {
 // 6. one projected-Jacobi sweep: U[s] -> U[s^1]
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_pja(StepArgs a, int s) {
+__global__ void __launch_bounds__(512) k_pja(StepArgs a, int s) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const float4 *__restrict__ Uin = a.U[s];
@@ -613,9 +613,22 @@ __global__ void k_body_state(const DevBody *bodies, uint32_t nbt, float *out) {
 
 static inline unsigned grid_for(uint32_t n, int bs) { return (n + bs - 1) / bs > 0 ? (n + bs - 1) / bs : 1; }
 
-cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st) {
+static inline cudaError_t mark(cudaEvent_t *ev, int k, cudaStream_t st) {
+  return ev ? cudaEventRecordWithFlags(ev[k], st, cudaEventRecordExternal) : cudaSuccess;
+}
+
+uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls) {
+  uint32_t k = 5;  // key, scan x3, wrench_final
+  if (a.n) k += 5 + ls.iters;  // scatter, reorder, contacts, pja x I, integrate
+  if (a.n_chunks) k += 1;
+  return k;
+}
+
+cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st, cudaEvent_t *ev) {
+  cudaError_t e;
   const uint32_t nbt = a.n_envs * a.maxb;
   const uint32_t nk = a.n > nbt ? a.n : nbt;
+  if ((e = mark(ev, 0, st)) != cudaSuccess) return e;
   k_key<<<grid_for(nk, 256), 256, 0, st>>>(a);
   const uint32_t nblk = a.nh_pad / kScanTile;
   k_scan_reduce<<<nblk, kScanThreads, 0, st>>>(a);
@@ -624,15 +637,20 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
   if (a.n) {
     k_scatter<<<grid_for(a.n, 256), 256, 0, st>>>(a);
     k_reorder<<<grid_for(a.n, 256), 256, 0, st>>>(a);
-    k_contacts<<<grid_for(a.n, 256), 256, 0, st>>>(a);
-    for (uint32_t it = 0; it < ls.iters; ++it) k_pja<<<grid_for(a.n, ls.pja_block), ls.pja_block, 0, st>>>(a, it & 1);
-    k_integrate<<<grid_for(a.n, 256), 256, 0, st>>>(a, ls.iters & 1);
   }
+  if ((e = mark(ev, 1, st)) != cudaSuccess) return e;
+  if (a.n) k_contacts<<<grid_for(a.n, 256), 256, 0, st>>>(a);
+  if ((e = mark(ev, 2, st)) != cudaSuccess) return e;
+  if (a.n)
+    for (uint32_t it = 0; it < ls.iters; ++it) k_pja<<<grid_for(a.n, ls.pja_block), ls.pja_block, 0, st>>>(a, it & 1);
+  if ((e = mark(ev, 3, st)) != cudaSuccess) return e;
+  if (a.n) k_integrate<<<grid_for(a.n, 256), 256, 0, st>>>(a, ls.iters & 1);
   if (a.n_chunks) {
     dim3 g(a.n_chunks, a.maxb);
     k_wrench_partial<<<g, 256, 0, st>>>(a);
   }
   k_wrench_final<<<1, 1024, 0, st>>>(a);
+  if ((e = mark(ev, 4, st)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

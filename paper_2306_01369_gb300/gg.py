@@ -39,6 +39,9 @@ SIGNATURES = {
     "gg_readback": (C.c_int, [_P, C.c_int, _P, C.c_size_t, C.c_int, _P]),
     "gg_set_state": (C.c_int, [_P, _P, C.c_size_t, C.c_int, _P]),
     "gg_tuning_count": (C.c_uint32, []),
+    "gg_enable_timing": (C.c_int, [_P, C.c_int]),
+    "gg_stage_ms": (C.c_int, [_P, C.POINTER(C.c_float)]),
+    "gg_kernels_per_step": (C.c_uint32, [_P]),
     "gg_tuning_selected": (C.c_uint32, [_P]),
     "gg_last_error": (C.c_char_p, [_P]),
     "gg_destroy": (None, [_P]),
@@ -231,6 +234,21 @@ class Sim:
 
     def sync(self, stream=None):
         self._check(self._L.gg_sync(self.h, _stream(stream)), "gg_sync")
+
+    def enable_timing(self, on=True):
+        self._check(self._L.gg_enable_timing(self.h, int(on)), "gg_enable_timing")
+
+    STAGES = ("bin_sort", "contacts", "pja", "integrate_wrench")
+
+    def stage_ms(self):
+        """Device milliseconds per stage of the last enqueued step (timing must be on)."""
+        out = (C.c_float * 4)()
+        self._check(self._L.gg_stage_ms(self.h, out), "gg_stage_ms")
+        return dict(zip(self.STAGES, [float(v) for v in out]))
+
+    @property
+    def kernels_per_step(self):
+        return self._L.gg_kernels_per_step(self.h)
 
     @property
     def tuning_selected(self):

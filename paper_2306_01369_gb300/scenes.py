@@ -149,15 +149,18 @@ def scoop_body(scale: float = 1.0, pos=(0.0, 0.0, 0.0), rotvec=(0.0, 0.0, 0.0)) 
                 quat=_quat_from_rotvec(rotvec))
 
 
-def waypoint_twists(seed, n_steps, dt, start, dig_depth, span, n_way=6, pos_jit=0.05, rot_range=0.3):
+def waypoint_twists(seed, n_steps, dt, start, dig_depth, span, n_way=6, pos_jit=0.05, rot_range=0.3,
+                    seg_time=0.2):
     """Per-step world-frame twists (vx, vy, vz, wx, wy, wz) of a tool following
-    `n_way` seeded waypoints along a dig path, piecewise constant per segment.
+    `n_way` seeded waypoints along a dig path, piecewise constant per segment of
+    `seg_time` seconds (the path takes (n_way - 1) seg_time s; runs shorter than
+    that cover only its beginning).
 
     Waypoint k sits at start + (span * k/(n_way-1), 0, -dig_depth * sin(pi k/(n_way-1)))
-    plus U(-pos_jit, pos_jit) per axis, with a rotation vector drawn from
+    plus U(-pos_jit, pos_jit) per axis (k > 0), with a rotation vector drawn from
     U(-rot_range, rot_range) per axis.  The tool moves on each segment with the
     constant linear velocity that joins the two waypoint positions and the
-    constant angular velocity (rotvec_{k+1} - rotvec_k) / T_segment.
+    constant angular velocity (rotvec_{k+1} - rotvec_k) / seg_time.
     Returns (twist float32 (n_steps, 6), rotvec of waypoint 0, position of waypoint 0).
     """
     u = uniform(seed, 6 * n_way).reshape(n_way, 6)
@@ -165,15 +168,14 @@ def waypoint_twists(seed, n_steps, dt, start, dig_depth, span, n_way=6, pos_jit=
     pts = np.stack([start[0] + span * k,
                     np.full(n_way, start[1]),
                     start[2] - dig_depth * np.sin(math.pi * k)], axis=1)
-    pts = pts + pos_jit * (2.0 * u[:, 0:3] - 1.0)
+    pts[1:] += pos_jit * (2.0 * u[1:, 0:3] - 1.0)
     rv = rot_range * (2.0 * u[:, 3:6] - 1.0)
-    seg = max(1, n_steps // (n_way - 1))
+    seg = max(1, int(round(seg_time / dt)))
     tw = np.zeros((n_steps, 6), np.float64)
     for s in range(n_steps):
         kseg = min(s // seg, n_way - 2)
-        T = seg * dt
-        tw[s, 0:3] = (pts[kseg + 1] - pts[kseg]) / T
-        tw[s, 3:6] = (rv[kseg + 1] - rv[kseg]) / T
+        tw[s, 0:3] = (pts[kseg + 1] - pts[kseg]) / seg_time
+        tw[s, 3:6] = (rv[kseg + 1] - rv[kseg]) / seg_time
     return tw.astype(np.float32), rv[0], pts[0]
 
 
@@ -231,9 +233,9 @@ def _bed_env(n, r0, jit, seed, side=None, layers=None, n_steps=500, dt=1e-4, sco
     # the scoop starts above one side of the bed and digs across it
     ts = seed * 7 + 3 if tool_seed is None else tool_seed
     span = 0.6 * foot
-    start = (-0.3 * foot, 0.0, height + 0.05 * scoop_scale)
-    tw, rv0, p0 = waypoint_twists(ts, n_steps, dt, start, dig_depth=0.5 * height + 0.05 * scoop_scale,
-                                  span=span, pos_jit=0.05 * scoop_scale)
+    start = (-0.3 * foot, 0.0, height + 0.02 * scoop_scale)
+    tw, rv0, p0 = waypoint_twists(ts, n_steps, dt, start, dig_depth=0.5 * height,
+                                  span=span, pos_jit=0.02 * scoop_scale, rot_range=0.2)
     scoop = scoop_body(scoop_scale, pos=p0, rotvec=rv0)
     return pr, [container, scoop], tw, {"side": side, "layers": layers, "pitch": pitch, "height": height}
 
