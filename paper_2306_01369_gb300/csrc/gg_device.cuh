@@ -24,7 +24,7 @@ constexpr int kMaxKb = 8;   // particle-body capacity limit
 constexpr int kScanItems = 16;          // counts per thread in the bucket scan
 constexpr int kScanThreads = 256;
 constexpr int kScanTile = kScanItems * kScanThreads;
-constexpr int kWrenchChunk = 8192;      // slots per wrench partial
+constexpr int kWrenchChunk = 1024;      // slots per wrench partial
 
 struct DevEnv {
   uint32_t off, n;        // particle range [off, off + n)

@@ -11,7 +11,8 @@
 //   k_pja  x I       projected-Jacobi sweeps (Alg. 1), one launch per iteration
 //   k_integrate      symplectic Euler (Eq. 4-5), back to particle-id order
 //   k_wrench_partial per-body impulse sums over fixed slot chunks (deterministic)
-//   k_wrench_final   wrench readback ring, kinematic body poses, step counter
+//   k_wrench_sum     per-body sums over chunks into the wrench readback ring
+//   k_body_update    kinematic body poses, step counter
 // Detection and impulse computation are separate launches, the split the paper
 // finds fastest (Sec. II-D).
 #include "gg_device.cuh"
@@ -462,28 +463,42 @@ __global__ void __launch_bounds__(256) k_wrench_partial(StepArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(1024) k_wrench_final(StepArgs a) {
-  const uint32_t step = a.ctrl->step;
+// One warp per body: sum its environment's chunk partials in a fixed order
+// (lane-strided, then a fixed butterfly) into the wrench ring.
+__global__ void __launch_bounds__(256) k_wrench_sum(StepArgs a) {
+  const uint32_t gb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   const uint32_t nbt = a.n_envs * a.maxb;
-  for (uint32_t gb = threadIdx.x; gb < nbt; gb += blockDim.x) {
-    DevBody &B = a.bodies[gb];
-    float *dst = a.wrench + ((size_t)(step % a.wrench_hist) * nbt + gb) * 6;
-    if (!B.active) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) dst[k] = 0.f;
-      continue;
-    }
+  if (gb >= nbt) return;
+  const uint32_t step = a.ctrl->step;
+  float *dst = a.wrench + ((size_t)(step % a.wrench_hist) * nbt + gb) * 6;
+  const DevBody &B = a.bodies[gb];
+  float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (B.active) {
     const uint32_t e = gb / a.maxb, lb = gb % a.maxb;
     const DevEnv &E = a.envs[e];
-    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (uint32_t c = E.chunk0; c < E.chunk0 + E.nchunks; ++c) {
+    for (uint32_t c = E.chunk0 + lane; c < E.chunk0 + E.nchunks; c += 32) {
       const float *src = a.wpart + ((size_t)c * a.maxb + lb) * 6;
 #pragma unroll
       for (int k = 0; k < 6; ++k) v[k] += src[k];
     }
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  if (lane == 0)
 #pragma unroll
     for (int k = 0; k < 6; ++k) dst[k] = v[k];
-    // pose update with this step's twist: p += dt v, q <- exp(dt w / 2) q
+}
+
+// Body poses after the step (p += dt v, q <- exp(dt w / 2) q), then the step counter.
+__global__ void __launch_bounds__(256) k_body_update(StepArgs a) {
+  const uint32_t step = a.ctrl->step;
+  const uint32_t nbt = a.n_envs * a.maxb;
+  for (uint32_t gb = threadIdx.x; gb < nbt; gb += blockDim.x) {
+    DevBody &B = a.bodies[gb];
+    if (!B.active) continue;
 #pragma unroll
     for (int k = 0; k < 3; ++k) B.p[k] += a.dt * B.v[k];
     const float tx = a.dt * B.w[0], ty = a.dt * B.w[1], tz = a.dt * B.w[2];
@@ -618,7 +633,7 @@ static inline cudaError_t mark(cudaEvent_t *ev, int k, cudaStream_t st) {
 }
 
 uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls) {
-  uint32_t k = 5;  // key, scan x3, wrench_final
+  uint32_t k = 6;  // key, scan x3, wrench_sum, body_update
   if (a.n) k += 5 + ls.iters;  // scatter, reorder, contacts, pja x I, integrate
   if (a.n_chunks) k += 1;
   return k;
@@ -649,7 +664,8 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
     dim3 g(a.n_chunks, a.maxb);
     k_wrench_partial<<<g, 256, 0, st>>>(a);
   }
-  k_wrench_final<<<1, 1024, 0, st>>>(a);
+  k_wrench_sum<<<grid_for(nbt * 32, 256), 256, 0, st>>>(a);
+  k_body_update<<<1, 256, 0, st>>>(a);
   if ((e = mark(ev, 4, st)) != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -29,27 +29,46 @@ def assert_contacts_equal(got, want):
     assert np.array_equal(got["bc_b"], want["bc_b"]), "body indices differ"
 
 
-def bodies_from_gpu(scene_bodies, bstate):
-    """Scene bodies with the GPU's FP32 pose (lockstep input for the oracle)."""
-    from paper_2306_01369_gb300 import scenes as S
-    out = []
-    for b, body in enumerate(scene_bodies):
-        row = bstate[b]
-        out.append(S.Body(kind=body.kind, shape=body.shape, pos=tuple(float(v) for v in row[0:3]),
-                          quat=tuple(float(v) for v in row[3:7]), lin_vel=body.lin_vel, ang_vel=body.ang_vel,
-                          is_free=body.is_free, mass=body.mass, inertia=body.inertia))
-    return out
-
-
-def oracle_from_gpu(sim, scene, step_index, n_threads=4):
-    """An oracle Sim started from the GPU's current FP32 state (lockstep)."""
+def oracle_advanced(scene, k, n_threads=8):
+    """The FP64 oracle run k steps from the scene's initial state."""
     import oracle
-    pos = sim.pos()
-    vel = sim.vel()
-    bodies = bodies_from_gpu(scene.bodies, sim.body_state()) if scene.bodies else []
-    o = oracle.Sim(pos, vel, scene.mass, bodies, scene.params, twist=scene.twist, n_threads=n_threads)
-    o.step_index = step_index
+    o = oracle.Sim(scene.pos_r, scene.vel, scene.mass, scene.bodies, scene.params, twist=scene.twist,
+                   n_threads=n_threads)
+    if k:
+        o.step(k)
     return o
+
+
+def fp32_scene(scene, o):
+    """The oracle's state after o.step_index steps, rounded to float32, as a new scene
+    (bodies at the oracle's pose, tool twists from that step on).  Both the GPU and
+    a fresh oracle start from it: lockstep inputs that never come from the GPU."""
+    from paper_2306_01369_gb300 import scenes as S
+    k = o.step_index
+    pos_r = np.empty((scene.n, 4), F32)
+    pos_r[:, :3] = o.x
+    pos_r[:, 3] = scene.pos_r[:, 3]
+    bodies = []
+    for b, body in enumerate(scene.bodies):
+        pose = o.body_pose(b)
+        tw = o.body_twist(b)
+        bodies.append(S.Body(kind=body.kind, shape=body.shape, pos=tuple(float(F32(v)) for v in pose[:3]),
+                             quat=tuple(float(F32(v)) for v in pose[3:]),
+                             lin_vel=tuple(float(v) for v in tw[:3]), ang_vel=tuple(float(v) for v in tw[3:]),
+                             is_free=body.is_free, mass=body.mass, inertia=body.inertia))
+    twist = {b: t[k:] for b, t in scene.twist.items() if t.shape[0] > k}
+    return S.Scene(f"{scene.name}@{k}", pos_r, o.v.astype(F32), scene.mass, bodies, scene.params,
+                   max(0, scene.n_steps - k), twist=twist, env_offsets=scene.env_offsets,
+                   body_offsets=scene.body_offsets, info=dict(scene.info))
+
+
+def lockstep_pair(gg, scene, k, n_threads=8, **sim_kw):
+    """(GPU sim, oracle sim, scene) both starting from the oracle's FP32 state after k steps."""
+    import oracle
+    s32 = fp32_scene(scene, oracle_advanced(scene, k, n_threads)) if k else scene
+    sim = gg.Sim.from_scene(s32, **sim_kw)
+    o = oracle.Sim(s32.pos_r, s32.vel, s32.mass, s32.bodies, s32.params, twist=s32.twist, n_threads=n_threads)
+    return sim, o, s32
 
 
 def vel_err(v_gpu, v_orc, dt, g=9.81):

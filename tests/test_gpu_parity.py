@@ -11,7 +11,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_helpers import (F32, assert_contacts_equal, bodies_from_gpu, need_gpu, oracle_from_gpu, vel_err)
+from gpu_helpers import F32, assert_contacts_equal, lockstep_pair, need_gpu, vel_err
 from paper_2306_01369_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -69,17 +69,22 @@ def test_binning_sort_table_bit_exact(gg, orc, n, hash_size):
     assert np.array_equal(sim.cell_start(), start)
 
 
-@pytest.mark.parametrize("steps_before", [0, 3, 40])
-def test_contacts_bit_exact_lockstep(gg, orc, steps_before):
-    sc = squeezed_box(4096)
-    sim = gg.Sim.from_scene(sc)
-    sim.step(steps_before)
-    o = oracle_from_gpu(sim, sc, steps_before)
+LOCKSTEP_CASES = [("squeezed", 0), ("squeezed", 3), ("settle", 400), ("settle", 1200)]
+
+
+def lockstep_scene(kind):
+    return squeezed_box(4096) if kind == "squeezed" else S.settle_box(n=4096)
+
+
+@pytest.mark.parametrize("kind,steps_before", LOCKSTEP_CASES)
+def test_contacts_bit_exact_lockstep(gg, orc, kind, steps_before):
+    """Contact sets from the same FP32 state (the oracle's after k steps)."""
+    sim, o, _ = lockstep_pair(gg, lockstep_scene(kind), steps_before)
     want = o.contacts()
     sim.step(1)
     sim.sync()
     got = sim.contacts()
-    assert want["stats"]["n_pp"] > 5000 and want["stats"]["n_body"] > 100
+    assert want["stats"]["n_pp"] > 3000 and want["stats"]["n_body"] > 100
     assert_contacts_equal(got, want)
     # brute force agrees too (the bucket walk misses nothing)
     brute = o.contacts(brute=True)
@@ -114,22 +119,16 @@ def test_one_step_dynamics(gg, orc):
     assert dx < 1e-5 * max(float(np.abs(o.x).max()), 0.2), dx
 
 
-@pytest.mark.parametrize("steps_before", [5, 60])
-def test_one_step_dynamics_lockstep(gg, orc, steps_before):
-    sc = squeezed_box(4096)
-    sim = gg.Sim.from_scene(sc)
-    sim.step(steps_before)
-    o = oracle_from_gpu(sim, sc, steps_before)
+@pytest.mark.parametrize("kind,steps_before", LOCKSTEP_CASES[1:])
+def test_one_step_dynamics_lockstep(gg, orc, kind, steps_before):
+    sim, o, sc = lockstep_pair(gg, lockstep_scene(kind), steps_before)
     sim.step(1)
     o.step(1)
     assert vel_err(sim.vel(), o.v, sc.params.dt) < 1e-5
 
 
 def test_contact_geometry_and_impulses(gg, orc):
-    sc = squeezed_box(2048)
-    sim = gg.Sim.from_scene(sc)
-    sim.step(4)
-    o = oracle_from_gpu(sim, sc, 4)
+    sim, o, sc = lockstep_pair(gg, squeezed_box(2048), 4)
     want = o.contacts()
     npp, nbc = int(want["pp_off"][-1]), int(want["bc_off"][-1])
     lam = np.zeros((npp, 3))
@@ -148,10 +147,11 @@ def test_contact_geometry_and_impulses(gg, orc):
     assert np.abs(got["bc_lam"] - blam).max() < 1e-4 * scale
 
 
-def test_ten_steps_within_radius_fraction(gg, orc):
-    sc = squeezed_box(4096)
-    sim = gg.Sim.from_scene(sc)
-    o = orc.Sim(sc.pos_r, sc.vel, sc.mass, sc.bodies, sc.params, n_threads=4)
+@pytest.mark.parametrize("steps_before", [0, 1200])
+def test_ten_steps_within_radius_fraction(gg, orc, steps_before):
+    """From the lattice at rest, and from the settled box (the oracle's state after
+    1200 steps), ten steps stay within 1e-3 r_i of the oracle."""
+    sim, o, sc = lockstep_pair(gg, S.settle_box(n=4096), steps_before)
     sim.step(10)
     o.step(10)
     d = np.linalg.norm(sim.pos()[:, :3].astype(np.float64) - o.x, axis=1)
@@ -216,10 +216,8 @@ def test_incline_threshold(gg, dtheta_deg):
 
 
 def test_wrench_matches_oracle_with_kinematic_scoop(gg, orc):
-    sc = S.scoop_bed(n=4096, n_steps=60, dims=(16, 16, 16))
-    sim = gg.Sim.from_scene(sc, wrench_history=8)
-    sim.step(50)
-    o = oracle_from_gpu(sim, sc, 50)
+    sim, o, sc = lockstep_pair(gg, S.scoop_bed(n=4096, n_steps=200, dims=(16, 16, 16)), 150,
+                               wrench_history=8)
     want = o.contacts()
     sim.step(1)
     o.step(1)
@@ -237,10 +235,7 @@ def test_wrench_matches_oracle_with_kinematic_scoop(gg, orc):
 
 
 def test_scoop_scene_ten_steps(gg, orc):
-    sc = S.scoop_bed(n=4096, n_steps=40, dims=(16, 16, 16))
-    sim = gg.Sim.from_scene(sc)
-    sim.step(20)
-    o = oracle_from_gpu(sim, sc, 20)
+    sim, o, sc = lockstep_pair(gg, S.scoop_bed(n=4096, n_steps=200, dims=(16, 16, 16)), 150)
     sim.step(10)
     o.step(10)
     d = np.linalg.norm(sim.pos()[:, :3].astype(np.float64) - o.x, axis=1)
@@ -336,12 +331,9 @@ def test_invalid_arguments(gg):
 # --------------------------------------------------------------------------- #
 
 def test_column_collapse_full_size_parity(gg, orc):
-    """262,144 spheres: bit-exact binning and contacts and one-step velocities, in
-    lockstep after the bottom layers have landed."""
-    sc = S.column_collapse()
-    sim = gg.Sim.from_scene(sc)
-    sim.step(800)
-    o = oracle_from_gpu(sim, sc, 800, n_threads=8)
+    """262,144 spheres: bit-exact binning and contacts and one-step velocities from
+    the oracle's state after 800 steps, when the bottom layers have landed."""
+    sim, o, sc = lockstep_pair(gg, S.column_collapse(), 800, n_threads=16)
     cs = orc.default_cell_size(float(sc.pos_r[:, 3].max()))
     keys = orc.cell_keys(o.x, cs, 2 * sc.n)
     want = o.contacts()
