@@ -163,17 +163,24 @@ def measured_peaks():
 
 
 def profile_traffic(kernel_digest: str):
-    """ncu DRAM bytes per launch of k_pja from the committed profile summary, if
-    it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_pja_column_collapse.json")
+    """ncu DRAM bytes per launch of k_pja from the committed profile summary
+    ("key: value" lines), if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_pja_column_collapse.txt")
     try:
+        kv = {}
         with open(path) as f:
-            d = json.load(f)
-    except (OSError, ValueError):
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+    except OSError:
         return None
-    if d.get("kernel_digest") != kernel_digest:
+    if kv.get("kernel_digest") != kernel_digest:
         return None
-    return d.get("dram_bytes_per_launch_full_size")
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def kernel_digest() -> str:

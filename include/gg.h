@@ -90,11 +90,16 @@ typedef struct {
   uint32_t tuning;           /* 0: pick launch shapes by timing (results do not depend on it);
                                 k >= 1: fixed launch-shape set k (see gg_tuning_count) */
   uint32_t wrench_history;   /* per-step body wrenches kept for readback; 0 -> 1 */
+  uint32_t max_free_bodies;  /* free rigid bodies over all environments (beyond the paper's
+                                kinematic bodies, Sec. V two-way coupling); 0 -> none */
+  uint32_t free_contact_capacity; /* particle contacts per free body per step, 1..8192; 0 -> 4096 */
 } gg_params;
 
 typedef struct {
   uint32_t kind;             /* gg_body_kind */
-  uint32_t is_free;          /* 0: kinematic, follows its twist (paper); 1: free rigid body */
+  uint32_t is_free;          /* 0: kinematic, follows its twist (paper); 1: free rigid body that
+                                takes contact reactions (needs max_free_bodies; box corners also
+                                collide with the environment's non-free bodies) */
   float shape[12];           /* see gg_body_kind */
   float pos[3];              /* world position of the body origin (translation of 0_X_b) */
   float quat[4];             /* orientation (w, x, y, z), body -> world; normalised by the library */
@@ -112,7 +117,8 @@ typedef enum {
   GG_FIELD_VEL = 1,            /* float[n][3] */
   GG_FIELD_BODY_STATE = 2,     /* float[B][16]: pos[3], quat[4], lin_vel[3], ang_vel[3], 0, 0, 0 */
   GG_FIELD_BODY_WRENCH = 3,    /* float[wrench_history][B][6]: force, torque on each body over the
-                                  last wrench_history steps, oldest first (Sec. III-C force readback) */
+                                  last wrench_history steps, oldest first, newest in the last row
+                                  (rows before the first step are zero) (Sec. III-C force readback) */
   GG_FIELD_CELL_KEY = 4,       /* uint32[n]: hash bucket of each particle at the last binning
                                   (environment base + Eq. 6 value) */
   GG_FIELD_SORT_PERM = 5,      /* uint32[n]: particle ids in ascending (bucket, id) order */
@@ -223,6 +229,7 @@ GG_API uint32_t gg_tuning_selected(const gg_sim *sim);
 GG_API const char *gg_last_error(const gg_sim *sim);
 
 GG_API void gg_destroy(gg_sim *sim);
+
 
 #ifdef __cplusplus
 }

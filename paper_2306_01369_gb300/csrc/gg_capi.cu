@@ -47,6 +47,8 @@ struct gg_sim {
   std::vector<DevEnv> envs;
   std::vector<uint32_t> nbodies;
   std::vector<float *> traj;  // per body slot
+  std::vector<uint32_t> fgb;  // free-body slot -> global body index (~0u when unused)
+  uint32_t F = 0, Lcap = 0;
   std::vector<void *> allocs;
   StepArgs a{};
   gg::LaunchShape ls{};
@@ -254,6 +256,9 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
   if (s->K > (uint32_t)gg::kMaxK || s->Kb > (uint32_t)gg::kMaxKb || s->maxb > 64 || s->H > (1u << 20))
     return bail(GG_ERR_INVALID_ARG);
   if (P.tuning > kNumShapes) return bail(GG_ERR_INVALID_ARG);
+  s->F = P.max_free_bodies;
+  s->Lcap = P.free_contact_capacity ? P.free_contact_capacity : 4096;
+  if (s->F > 4096 || s->Lcap > 8192) return bail(GG_ERR_INVALID_ARG);
   s->n = n;
   s->n_envs = n_envs;
 
@@ -352,8 +357,13 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
       (rc = dalloc(s, &a.envs, n_envs)) || (rc = dalloc(s, &a.bodies, nbt)) ||
       (rc = dalloc(s, &a.chunk_env, chunks)) || (rc = dalloc(s, &a.wpart, (size_t)std::max(chunks, 1u) * s->maxb * 6)) ||
       (rc = dalloc(s, &a.wrench, (size_t)s->H * nbt * 6)) || (rc = dalloc(s, &a.ctrl, 1)) ||
-      (rc = dalloc(s, &s->vel3, (size_t)n * 3)))
+      (rc = dalloc(s, &s->vel3, (size_t)n * 3)) || (rc = dalloc(s, &a.ncb, nbt)) ||
+      (rc = dalloc(s, &a.fcount, s->F)) || (rc = dalloc(s, &a.flist, (size_t)s->F * s->Lcap)) ||
+      (rc = dalloc(s, &a.fgb, s->F)) || (rc = dalloc(s, &a.fcc, (size_t)s->F * 8 * s->maxb)))
     return bail(rc);
+  a.F = s->F;
+  a.Lcap = s->Lcap;
+  s->fgb.assign(s->F, 0xffffffffu);
   std::vector<uint32_t> h_chunk_env(std::max(chunks, 1u), 0);
   for (uint32_t e = 0; e < n_envs; ++e)
     for (uint32_t c = 0; c < s->envs[e].nchunks; ++c) h_chunk_env[s->envs[e].chunk0 + c] = e;
@@ -376,7 +386,12 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
       (e = cudaMemset(a.ccount, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
       (e = cudaMemset(a.sid, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
       (e = cudaMemset(a.key_id, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
-      (e = cudaMemset(a.ctrl, 0, sizeof(DevCtrl))) != cudaSuccess)
+      (e = cudaMemset(a.ctrl, 0, sizeof(DevCtrl))) != cudaSuccess ||
+      (e = cudaMemset(a.ncb, 0, sizeof(uint32_t) * nbt)) != cudaSuccess ||
+      (e = cudaMemset(a.fgb, 0xff, sizeof(uint32_t) * std::max(s->F, 1u))) != cudaSuccess ||
+      (e = cudaMemset(a.fcount, 0, sizeof(uint32_t) * std::max(s->F, 1u))) != cudaSuccess ||
+      (e = cudaMemset(a.fcc, 0, sizeof(gg::CornerContact) * std::max<size_t>((size_t)s->F * 8 * s->maxb, 1))) !=
+          cudaSuccess)
     return bail(cuda_fail(s, e, "initialising buffers"));
   if ((e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(cuda_fail(s, e, "cudaStreamCreate"));
@@ -403,7 +418,8 @@ gg_status gg_set_bodies(gg_sim *s, uint32_t env, uint32_t n_bodies, const gg_bod
     const gg_body &in = bodies[b];
     DevBody &o = hb[b];
     if (in.kind > GG_BODY_OPEN_BOX) return fail(s, GG_ERR_INVALID_ARG, "unknown body kind");
-    if (in.is_free) return fail(s, GG_ERR_UNSUPPORTED, "free rigid bodies are not supported by this build");
+    if (in.is_free && !(in.mass > 0.f && in.inertia[0] > 0.f && in.inertia[1] > 0.f && in.inertia[2] > 0.f))
+      return fail(s, GG_ERR_INVALID_ARG, "a free body needs a positive mass and inertia");
     double qn = std::sqrt((double)in.quat[0] * in.quat[0] + (double)in.quat[1] * in.quat[1] +
                           (double)in.quat[2] * in.quat[2] + (double)in.quat[3] * in.quat[3]);
     if (!(qn > 0.0) || !std::isfinite(qn)) return fail(s, GG_ERR_INVALID_ARG, "body quaternion must be non-zero");
@@ -422,8 +438,23 @@ gg_status gg_set_bodies(gg_sim *s, uint32_t env, uint32_t n_bodies, const gg_bod
     o.mass = in.mass;
     o.env = env;
     o.active = 1;
+    o.fid = 0xffffffffu;
+  }
+  // free-body slots: release this environment's, then assign in body order
+  std::vector<uint32_t> fgb = s->fgb;
+  for (uint32_t &g : fgb)
+    if (g != 0xffffffffu && g / s->maxb == env) g = 0xffffffffu;
+  for (uint32_t b = 0; b < n_bodies; ++b) {
+    if (!bodies[b].is_free) continue;
+    uint32_t f = 0;
+    while (f < s->F && fgb[f] != 0xffffffffu) ++f;
+    if (f == s->F) return fail(s, GG_ERR_INVALID_ARG, "more free bodies than gg_params.max_free_bodies");
+    fgb[f] = env * s->maxb + b;
+    hb[b].fid = f;
   }
   GG_CUDA(s, cudaDeviceSynchronize());
+  s->fgb = fgb;
+  if (s->F) GG_CUDA(s, cudaMemcpy(s->a.fgb, fgb.data(), sizeof(uint32_t) * s->F, cudaMemcpyHostToDevice));
   for (uint32_t b = 0; b < s->maxb; ++b) {
     float *&t = s->traj[env * s->maxb + b];
     if (t) cudaFree(t);
@@ -565,7 +596,14 @@ gg_status gg_readback(gg_sim *s, gg_field f, void *dst, size_t bytes, int dst_on
     const uint64_t oldest = s->steps >= H ? s->steps % H : 0;
     char *d = static_cast<char *>(dst);
     const char *src = reinterpret_cast<const char *>(s->a.wrench);
-    if (oldest) {  // ring has wrapped: rows [oldest, H) then [0, oldest)
+    if (s->steps < H) {  // newest step in the last row: zero rows, then steps 0 .. steps-1
+      const size_t z = (H - s->steps) * row;
+      if (dst_on_device)
+        GG_CUDA(s, cudaMemsetAsync(d, 0, z, st));
+      else
+        std::memset(d, 0, z);
+      if (s->steps) GG_CUDA(s, cudaMemcpyAsync(d + z, src, s->steps * row, d2x, st));
+    } else if (oldest) {  // ring has wrapped: rows [oldest, H) then [0, oldest)
       GG_CUDA(s, cudaMemcpyAsync(d, src + oldest * row, (H - oldest) * row, d2x, st));
       GG_CUDA(s, cudaMemcpyAsync(d + (H - oldest) * row, src, oldest * row, d2x, st));
     } else {

@@ -47,6 +47,15 @@ struct DevBody {
   uint32_t traj_len;
   uint32_t traj_start;  // step index at which traj[0] applies
   uint32_t env, active;
+  uint32_t fid;         // free bodies: index into the free-body arrays
+};
+
+// A corner of a free box touching a non-free body of its environment.
+struct CornerContact {
+  uint32_t o, valid;
+  float n[3], psi;   // normal (other body -> box), penetration
+  float xc[3];       // contact point
+  float lam[3];      // accumulated impulse on the box
 };
 
 struct DevCtrl {
@@ -91,6 +100,13 @@ struct StepArgs {
   float *wpart;           // [n_chunks][maxb][6]
   float *wrench;          // [wrench_hist][n_envs * maxb][6]
   DevCtrl *ctrl;
+  // free rigid bodies
+  uint32_t F, Lcap;       // free-body slots, contact-list capacity per free body
+  uint32_t *ncb;          // [n_envs * maxb] contacts per body this step
+  uint32_t *fcount;       // [F] particle contacts of each free body
+  uint32_t *flist;        // [F][Lcap] (slot * Kb + k), sorted ascending
+  uint32_t *fgb;          // [F] global body index of each free slot (or ~0u)
+  CornerContact *fcc;     // [F][8 * maxb]
 };
 
 // ---------------------------------------------------------------------------

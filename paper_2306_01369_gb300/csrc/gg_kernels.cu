@@ -8,7 +8,9 @@
 //   k_reorder        stable order inside each bucket (ascending id) + gather of
 //                    positions / velocities into sorted slots
 //   k_contacts       27-cell bucket walk, sphere test, SDF tests (Sec. II-B, II-C)
-//   k_pja  x I       projected-Jacobi sweeps (Alg. 1), one launch per iteration
+//   k_free_prep      (free bodies) sorted contact lists, box-corner contacts
+//   k_pja  x I       projected-Jacobi sweeps (Alg. 1), one launch per iteration,
+//   k_free_update    each followed (free bodies) by the bodies' twist update
 //   k_integrate      symplectic Euler (Eq. 4-5), back to particle-id order
 //   k_wrench_partial per-body impulse sums over fixed slot chunks (deterministic)
 //   k_wrench_sum     per-body sums over chunks into the wrench readback ring
@@ -95,7 +97,11 @@ __global__ void k_key(StepArgs a) {
     a.key_id[i] = key;
     atomicAdd(&a.cnt[key], 1u);
   }
-  if (i < a.n_envs * a.maxb) prep_body(a, i);
+  if (i < a.n_envs * a.maxb) {
+    prep_body(a, i);
+    a.ncb[i] = 0;
+  }
+  if (i < a.F) a.fcount[i] = 0;
   if (i == 0) {
     a.ctrl->n_pp = 0;
     a.ctrl->n_body = 0;
@@ -317,6 +323,14 @@ __global__ void __launch_bounds__(256) k_contacts(StepArgs a) {
       const float psi = pi.w - f;
       psi_max = fmaxf(psi_max, psi);
       const size_t o = (size_t)nbc * n + i;
+      if (B.is_free) {
+        atomicAdd(&a.ncb[gb], 1u);
+        const uint32_t pos = atomicAdd(&a.fcount[B.fid], 1u);
+        if (pos < a.Lcap)
+          a.flist[(size_t)B.fid * a.Lcap + pos] = i * a.Kb + nbc;
+        else
+          flag(a.ctrl, kFlagBodyOverflow);
+      }
       a.bj[o] = gb;
       a.bn[o] = make_float4(nn.x, nn.y, nn.z, psi);
       a.bxc[o] = make_float4(xi.x - f * nn.x, xi.y - f * nn.y, xi.z - f * nn.z, 0.f);
@@ -392,7 +406,16 @@ __global__ void __launch_bounds__(512) k_pja(StepArgs a, int s) {
     const float ubx = B.v[0] + (B.w[1] * rz - B.w[2] * ry);
     const float uby = B.v[1] + (B.w[2] * rx - B.w[0] * rz);
     const float ubz = B.v[2] + (B.w[0] * ry - B.w[1] * rx);
-    const float w = 1.0f / ui.w;
+    float invb = 0.f;
+    if (B.is_free) {  // n_b (1/M + (a x n) . I_w^-1 (a x n)), mass split over the body's contacts
+      const float cx = ry * nn.z - rz * nn.y, cy = rz * nn.x - rx * nn.z, cz = rx * nn.y - ry * nn.x;
+      const float t0 = B.R[0] * cx + B.R[3] * cy + B.R[6] * cz;
+      const float t1 = B.R[1] * cx + B.R[4] * cy + B.R[7] * cz;
+      const float t2 = B.R[2] * cx + B.R[5] * cy + B.R[8] * cz;
+      invb = (float)a.ncb[a.bj[o]] * (1.0f / B.mass + t0 * t0 / B.inertia[0] + t1 * t1 / B.inertia[1] +
+                                      t2 * t2 / B.inertia[2]);
+    }
+    const float w = 1.0f / (ui.w + invb);
     const float3 u = make_float3(ui.x - ubx, ui.y - uby, ui.z - ubz);
     const float3 l = pja_project(lam, u, make_float3(nn.x, nn.y, nn.z), a.ab * nn.w, w, a.mu);
     a.blam[o] = l.x;
@@ -403,6 +426,155 @@ __global__ void __launch_bounds__(512) k_pja(StepArgs a, int s) {
     sz += l.z;
   }
   a.U[s ^ 1][i] = make_float4(base.x + base.w * sx, base.y + base.w * sy, base.z + base.w * sz, ui.w);
+}
+
+// ---------------------------------------------------------------------------
+// 6b. free rigid bodies: contact list order, corner contacts, per-iteration update
+// ---------------------------------------------------------------------------
+
+constexpr int kFreeSortMax = 8192;  // contact-list capacity limit (shared-memory sort)
+
+// One block per free body: sort its contact list (bitonic, ascending), then find
+// its box corners touching the environment's non-free bodies (FP32 decision).
+__global__ void __launch_bounds__(1024) k_free_prep(StepArgs a) {
+  __shared__ uint32_t sk[kFreeSortMax];
+  const uint32_t fid = blockIdx.x;
+  const uint32_t gb = a.fgb[fid];
+  if (gb == 0xffffffffu) return;
+  const uint32_t cnt = min(a.fcount[fid], a.Lcap);
+  uint32_t P = 1;
+  while (P < cnt) P <<= 1;
+  uint32_t *lst = a.flist + (size_t)fid * a.Lcap;
+  for (uint32_t t = threadIdx.x; t < P; t += blockDim.x) sk[t] = t < cnt ? lst[t] : 0xffffffffu;
+  __syncthreads();
+  for (uint32_t k = 2; k <= P; k <<= 1)
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t t = threadIdx.x; t < P; t += blockDim.x) {
+        const uint32_t p = t ^ j;
+        if (p > t) {
+          const bool up = (t & k) == 0;
+          const uint32_t x = sk[t], y = sk[p];
+          if ((x > y) == up) {
+            sk[t] = y;
+            sk[p] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) lst[t] = sk[t];
+  // corners of a free box against the non-free bodies of its environment
+  const DevBody &B = a.bodies[gb];
+  const uint32_t e = gb / a.maxb;
+  CornerContact *cc = a.fcc + (size_t)fid * 8 * a.maxb;
+  for (uint32_t t = threadIdx.x; t < 8 * a.maxb; t += blockDim.x) {
+    const uint32_t corner = t / a.maxb, ob = t % a.maxb;
+    CornerContact c{};
+    c.o = ob;
+    const DevBody &O = a.bodies[e * a.maxb + ob];
+    if (B.kind == 1 && e * a.maxb + ob != gb && O.active && !O.is_free) {
+      float cw[3];
+      const float cf[3] = {(corner & 1) ? B.shape[0] : -B.shape[0], (corner & 2) ? B.shape[1] : -B.shape[1],
+                           (corner & 4) ? B.shape[2] : -B.shape[2]};
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        cw[q] = __fadd_rn(B.p[q], __fadd_rn(__fadd_rn(__fmul_rn(B.R[3 * q], cf[0]), __fmul_rn(B.R[3 * q + 1], cf[1])),
+                                            __fmul_rn(B.R[3 * q + 2], cf[2])));
+      const float3 xw = make_float3(cw[0], cw[1], cw[2]);
+      const float3 y = world_to_body(O, xw);
+      int br;
+      const float f = body_sdf(O, y, &br);
+      if (f <= 0.0f) {
+        const float3 nn = rot_apply(O.R, body_grad(O, y, br));
+        c.valid = 1;
+        c.n[0] = nn.x;
+        c.n[1] = nn.y;
+        c.n[2] = nn.z;
+        c.psi = -f;
+        c.xc[0] = xw.x - f * nn.x;
+        c.xc[1] = xw.y - f * nn.y;
+        c.xc[2] = xw.z - f * nn.z;
+        atomicAdd(&a.ncb[gb], 1u);
+      }
+    }
+    cc[t] = c;
+  }
+}
+
+__device__ __forceinline__ float free_inv_mass(const DevBody &B, float3 r, float3 n) {
+  const float cx = r.y * n.z - r.z * n.y, cy = r.z * n.x - r.x * n.z, cz = r.x * n.y - r.y * n.x;
+  const float t0 = B.R[0] * cx + B.R[3] * cy + B.R[6] * cz;
+  const float t1 = B.R[1] * cx + B.R[4] * cy + B.R[7] * cz;
+  const float t2 = B.R[2] * cx + B.R[5] * cy + B.R[8] * cz;
+  return 1.0f / B.mass + t0 * t0 / B.inertia[0] + t1 * t1 / B.inertia[1] + t2 * t2 / B.inertia[2];
+}
+
+// After each sweep, one block per free body: update its corner contacts (against
+// the twist of this iteration), sum every impulse it received in a fixed order,
+// and set its twist for the next iteration (Newton-Euler, gyroscopic term dropped).
+__global__ void __launch_bounds__(256) k_free_update(StepArgs a) {
+  const uint32_t fid = blockIdx.x;
+  const uint32_t gb = a.fgb[fid];
+  if (gb == 0xffffffffu) return;
+  DevBody &B = a.bodies[gb];
+  const uint32_t e = gb / a.maxb;
+  const float nb = (float)a.ncb[gb];
+  const float3 V = make_float3(B.v[0], B.v[1], B.v[2]), W = make_float3(B.w[0], B.w[1], B.w[2]);
+  float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  CornerContact *cc = a.fcc + (size_t)fid * 8 * a.maxb;
+  for (uint32_t t = threadIdx.x; t < 8 * a.maxb; t += blockDim.x) {
+    CornerContact c = cc[t];
+    if (!c.valid) continue;
+    const DevBody &O = a.bodies[e * a.maxb + c.o];
+    const float3 r = make_float3(c.xc[0] - B.p[0], c.xc[1] - B.p[1], c.xc[2] - B.p[2]);
+    const float3 ro = make_float3(c.xc[0] - O.p[0], c.xc[1] - O.p[1], c.xc[2] - O.p[2]);
+    const float3 ub = make_float3(V.x + W.y * r.z - W.z * r.y, V.y + W.z * r.x - W.x * r.z, V.z + W.x * r.y - W.y * r.x);
+    const float3 uo = make_float3(O.v[0] + O.w[1] * ro.z - O.w[2] * ro.y, O.v[1] + O.w[2] * ro.x - O.w[0] * ro.z,
+                                  O.v[2] + O.w[0] * ro.y - O.w[1] * ro.x);
+    const float3 nn = make_float3(c.n[0], c.n[1], c.n[2]);
+    const float w = 1.0f / (nb * free_inv_mass(B, r, nn));
+    const float3 l = pja_project(make_float3(c.lam[0], c.lam[1], c.lam[2]),
+                                 make_float3(ub.x - uo.x, ub.y - uo.y, ub.z - uo.z), nn, a.ab * c.psi, w, a.mu);
+    cc[t].lam[0] = l.x;
+    cc[t].lam[1] = l.y;
+    cc[t].lam[2] = l.z;
+    v[0] += l.x;
+    v[1] += l.y;
+    v[2] += l.z;
+    v[3] += r.y * l.z - r.z * l.y;
+    v[4] += r.z * l.x - r.x * l.z;
+    v[5] += r.x * l.y - r.y * l.x;
+  }
+  const size_t n = a.n, KbN = (size_t)a.Kb * n;
+  const uint32_t cnt = min(a.fcount[fid], a.Lcap);
+  const uint32_t *lst = a.flist + (size_t)fid * a.Lcap;
+  for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const uint32_t code = lst[t];
+    const size_t o = (size_t)(code % a.Kb) * n + code / a.Kb;
+    const float fx = -a.blam[o], fy = -a.blam[o + KbN], fz = -a.blam[o + 2 * KbN];
+    const float4 xc = a.bxc[o];
+    const float rx = xc.x - B.p[0], ry = xc.y - B.p[1], rz = xc.z - B.p[2];
+    v[0] += fx;
+    v[1] += fy;
+    v[2] += fz;
+    v[3] += ry * fz - rz * fy;
+    v[4] += rz * fx - rx * fz;
+    v[5] += rx * fy - ry * fx;
+  }
+  block_sum6<256>(v);
+  if (threadIdx.x == 0) {
+    const float im = 1.0f / B.mass;
+    // I_w^-1 L = R diag(1/I) R^T L
+    const float t0 = (B.R[0] * v[3] + B.R[3] * v[4] + B.R[6] * v[5]) / B.inertia[0];
+    const float t1 = (B.R[1] * v[3] + B.R[4] * v[4] + B.R[7] * v[5]) / B.inertia[1];
+    const float t2 = (B.R[2] * v[3] + B.R[5] * v[4] + B.R[8] * v[5]) / B.inertia[2];
+    B.v[0] = B.own_v[0] + a.dt * a.g[0] + im * v[0];
+    B.v[1] = B.own_v[1] + a.dt * a.g[1] + im * v[1];
+    B.v[2] = B.own_v[2] + a.dt * a.g[2] + im * v[2];
+    B.w[0] = B.own_w[0] + (B.R[0] * t0 + B.R[1] * t1 + B.R[2] * t2);
+    B.w[1] = B.own_w[1] + (B.R[3] * t0 + B.R[4] * t1 + B.R[5] * t2);
+    B.w[2] = B.own_w[2] + (B.R[6] * t0 + B.R[7] * t1 + B.R[8] * t2);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -487,6 +659,28 @@ __global__ void __launch_bounds__(256) k_wrench_sum(StepArgs a) {
   for (int k = 0; k < 6; ++k)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  if (lane == 0 && B.active && a.F) {  // free-box corners: +lambda on the box, -lambda on the other body
+    const uint32_t e = gb / a.maxb;
+    const float inv_dt = 1.0f / a.dt;
+    for (uint32_t lb = 0; lb < a.maxb; ++lb) {
+      const DevBody &Fb = a.bodies[e * a.maxb + lb];
+      if (!Fb.active || !Fb.is_free) continue;
+      const CornerContact *cc = a.fcc + (size_t)Fb.fid * 8 * a.maxb;
+      for (uint32_t t = 0; t < 8 * a.maxb; ++t) {
+        if (!cc[t].valid) continue;
+        const float sg = (e * a.maxb + lb == gb) ? inv_dt : ((e * a.maxb + cc[t].o == gb) ? -inv_dt : 0.f);
+        if (sg == 0.f) continue;
+        const float fx = sg * cc[t].lam[0], fy = sg * cc[t].lam[1], fz = sg * cc[t].lam[2];
+        const float rx = cc[t].xc[0] - B.p[0], ry = cc[t].xc[1] - B.p[1], rz = cc[t].xc[2] - B.p[2];
+        v[0] += fx;
+        v[1] += fy;
+        v[2] += fz;
+        v[3] += ry * fz - rz * fy;
+        v[4] += rz * fx - rx * fz;
+        v[5] += rx * fy - ry * fx;
+      }
+    }
+  }
   if (lane == 0)
 #pragma unroll
     for (int k = 0; k < 6; ++k) dst[k] = v[k];
@@ -636,6 +830,7 @@ uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls) {
   uint32_t k = 6;  // key, scan x3, wrench_sum, body_update
   if (a.n) k += 5 + ls.iters;  // scatter, reorder, contacts, pja x I, integrate
   if (a.n_chunks) k += 1;
+  if (a.F) k += 1 + ls.iters;  // free_prep, free_update x I
   return k;
 }
 
@@ -655,9 +850,12 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
   }
   if ((e = mark(ev, 1, st)) != cudaSuccess) return e;
   if (a.n) k_contacts<<<grid_for(a.n, 256), 256, 0, st>>>(a);
+  if (a.F) k_free_prep<<<a.F, 1024, 0, st>>>(a);
   if ((e = mark(ev, 2, st)) != cudaSuccess) return e;
-  if (a.n)
-    for (uint32_t it = 0; it < ls.iters; ++it) k_pja<<<grid_for(a.n, ls.pja_block), ls.pja_block, 0, st>>>(a, it & 1);
+  for (uint32_t it = 0; it < ls.iters; ++it) {
+    if (a.n) k_pja<<<grid_for(a.n, ls.pja_block), ls.pja_block, 0, st>>>(a, it & 1);
+    if (a.F) k_free_update<<<a.F, 256, 0, st>>>(a);
+  }
   if ((e = mark(ev, 3, st)) != cudaSuccess) return e;
   if (a.n) k_integrate<<<grid_for(a.n, 256), 256, 0, st>>>(a, ls.iters & 1);
   if (a.n_chunks) {

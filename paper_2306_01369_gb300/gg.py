@@ -53,7 +53,8 @@ class GGParams(C.Structure):
                 ("alpha", C.c_float), ("pja_iters", C.c_uint32), ("cell_size", C.c_float),
                 ("hash_factor", C.c_uint32), ("hash_size", C.c_uint32), ("max_contacts", C.c_uint32),
                 ("max_body_contacts", C.c_uint32), ("max_bodies", C.c_uint32), ("density", C.c_float),
-                ("tuning", C.c_uint32), ("wrench_history", C.c_uint32)]
+                ("tuning", C.c_uint32), ("wrench_history", C.c_uint32), ("max_free_bodies", C.c_uint32),
+                ("free_contact_capacity", C.c_uint32)]
 
 
 class GGBody(C.Structure):
@@ -117,7 +118,7 @@ def _stream(stream):
     return C.c_void_p(int(stream))
 
 
-def make_params(p, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0) -> GGParams:
+def make_params(p, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0, max_free_bodies=0) -> GGParams:
     q = GGParams()
     q.struct_size = C.sizeof(GGParams)
     q.dt = p.dt
@@ -135,6 +136,8 @@ def make_params(p, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0) -> G
     q.density = 0.0
     q.tuning = tuning
     q.wrench_history = wrench_history
+    q.max_free_bodies = max_free_bodies
+    q.free_contact_capacity = 0
     return q
 
 
@@ -161,11 +164,11 @@ class Sim:
     """One libgg simulation (single environment, or batched when env_offsets is given)."""
 
     def __init__(self, pos_r, vel=None, mass=None, params=None, env_offsets=None, tuning=0, wrench_history=1,
-                 max_bodies=8, hash_factor=0):
+                 max_bodies=8, hash_factor=0, max_free_bodies=0):
         L = load()
         self._L = L
         self.params = params
-        self.gp = make_params(params, tuning, wrench_history, max_bodies, hash_factor)
+        self.gp = make_params(params, tuning, wrench_history, max_bodies, hash_factor, max_free_bodies)
         n = int(pos_r.shape[0])
         self.n = n
         pp, dev = _ptr(pos_r)
@@ -212,8 +215,10 @@ class Sim:
     @classmethod
     def from_scene(cls, scene, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0, device_inputs=None):
         args = (scene.pos_r, scene.vel, scene.mass) if device_inputs is None else device_inputs
+        n_free = sum(1 for b in scene.bodies if b.is_free)
         sim = cls(*args, params=scene.params, env_offsets=scene.env_offsets, tuning=tuning,
-                  wrench_history=wrench_history, max_bodies=max_bodies, hash_factor=hash_factor)
+                  wrench_history=wrench_history, max_bodies=max_bodies, hash_factor=hash_factor,
+                  max_free_bodies=n_free)
         if scene.body_offsets is None:
             if scene.bodies:
                 sim.set_bodies(scene.bodies, 0)

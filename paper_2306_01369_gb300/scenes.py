@@ -243,18 +243,22 @@ def _bed_env(n, r0, jit, seed, side=None, layers=None, n_steps=500, dt=1e-4, sco
 def excavation(n=1048576, seed=1002, n_steps=1000, with_cubes=True):
     """Bed of n spheres (r = 2 mm +-15 %) 128x128 sites wide in a 0.61 m container,
     one kinematic box-minus-box scoop on 6 seeded waypoints, two free 3 cm cubes;
-    dt = 1e-4 s, 30 PJA iterations, mu = 0.5."""
+    dt = 1e-4 s, 30 PJA iterations, mu = 0.5.  Smaller n: a 16-layer bed, scoop
+    scaled with the bed's footprint."""
     r0, jit = 2e-3, 0.15
-    side = 128 if n >= 128 * 128 else int(math.ceil(math.sqrt(n / 16)))
+    side = 128 if n >= 128 * 128 * 64 else int(math.ceil(math.sqrt(n / 16)))
+    foot = side * 2 * r0 * (1 + jit) * 1.02
     pr, bodies, tw, info = _bed_env(n, r0, jit, seed, side=side, n_steps=n_steps, dt=1e-4,
-                                    margin=0.5 * (0.61 - 128 * 2 * r0 * (1 + jit) * 1.02) if side == 128 else 0.005)
+                                    margin=0.5 * (0.61 - foot) if side == 128 else 0.005,
+                                    scoop_scale=min(1.0, foot / 0.6))
     if with_cubes:
         s = 0.03
         m = DENSITY * s ** 3
         inertia = m * s * s / 6.0
-        zc = info["height"] + 0.5 * s + 0.002
-        for x in (0.15 * side * info["pitch"], 0.3 * side * info["pitch"]):
-            bodies.append(Body(kind=BOX, shape=(0.5 * s, 0.5 * s, 0.5 * s), pos=(x, 0.05, zc), is_free=1,
+        zc = info["height"] + 0.5 * s + 0.001
+        foot = side * info["pitch"]
+        for x in (0.1 * foot, 0.3 * foot):
+            bodies.append(Body(kind=BOX, shape=(0.5 * s, 0.5 * s, 0.5 * s), pos=(x, 0.2 * foot, zc), is_free=1,
                                mass=m, inertia=(inertia,) * 3))
     return Scene(f"excavation_{n}", pr, np.zeros((n, 3), np.float32), sphere_mass(pr[:, 3]), bodies,
                  Params(dt=1e-4, mu=0.5, pja_iters=30, max_body_contacts=4), n_steps, twist={1: tw},

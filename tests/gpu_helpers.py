@@ -71,8 +71,22 @@ def lockstep_pair(gg, scene, k, n_threads=8, **sim_kw):
     return sim, o, s32
 
 
-def vel_err(v_gpu, v_orc, dt, g=9.81):
-    """Largest velocity difference relative to the scene's velocity scale
-    max(max_i |v_i|, g dt)."""
-    vref = max(float(np.abs(v_orc).max()), g * dt)
-    return float(np.abs(v_gpu.astype(np.float64) - v_orc).max()) / vref
+EPS32 = 2.0 ** -24
+
+
+def vel_tol(scene, v_orc, length=None):
+    """Tolerance of one-step velocities, GPU (FP32) vs oracle (FP64), from the same
+    FP32 state: 1e-5 of the scene's velocity scale max(max_i |v_i|, g dt), plus the
+    FP32 floor of the Baumgarte bias.  psi = (r_i + r_j) - |x_i - x_j| evaluated in
+    FP32 carries up to ~8 eps32 * L of rounding (L = 2 r_max for particle pairs, the
+    body-frame coordinate scale for SDF contacts), which the bias alpha psi / dt turns
+    into (alpha / dt) 8 eps32 L of velocity."""
+    p = scene.params
+    vscale = max(float(np.abs(v_orc).max()), 9.81 * p.dt)
+    L = 2.0 * float(scene.pos_r[:, 3].max()) if length is None else length
+    return 1e-5 * vscale + (p.alpha / p.dt) * 8.0 * EPS32 * L
+
+
+def vel_err(v_gpu, v_orc, scene, length=None):
+    """Largest one-step velocity difference as a fraction of vel_tol (pass: < 1)."""
+    return float(np.abs(v_gpu.astype(np.float64) - v_orc).max()) / vel_tol(scene, v_orc, length)
