@@ -230,6 +230,33 @@ GG_API const char *gg_last_error(const gg_sim *sim);
 
 GG_API void gg_destroy(gg_sim *sim);
 
+/*
+ * Binning and bucket sort of one particle set with no device allocation.
+ * The paper has no counterpart: this is a library convenience for callers that
+ * cannot allocate device memory themselves or let a library do it (code running
+ * inside a framework's memory pool, allocator-free real-time loops, plug-ins
+ * handed device pointers only).  It computes what one step's binning computes
+ * for a single environment -- the Eq. 6 bucket of every particle, the particle
+ * ids in ascending (bucket, id) order, and the bucket start table -- and gives
+ * the same values as GG_FIELD_CELL_KEY, GG_FIELD_SORT_PERM and
+ * GG_FIELD_CELL_START of a gg_sim with the same positions, cell_size and
+ * hash_size.
+ *
+ * pos_radius: device float[n][4]; keys, perm: device uint32[n]; cell_start: device
+ * uint32[n_h + 1]; all caller-owned, on the current device; enqueued on `stream`.
+ * Limits: n <= GG_NOALLOC_MAX_PARTICLES, 1 <= n_h <= GG_NOALLOC_MAX_BUCKETS, else
+ * GG_ERR_INVALID_ARG (nothing is enqueued).  Calls no cudaMalloc or cudaFree.
+ * Scratch: a fixed static device array of about 12.6 MB that every GPU which loads
+ * libgg.so holds until the process exits; every call on a device reuses it and
+ * clears its histogram first, so calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.  The first call
+ * on each device looks up that array's device address (with the device current);
+ * make that first call before any CUDA stream capture.
+ */
+#define GG_NOALLOC_MAX_PARTICLES (1u << 20)
+#define GG_NOALLOC_MAX_BUCKETS (1u << 21)
+GG_API gg_status gg_bin_sort_noalloc(const float *pos_radius, uint32_t n, float cell_size, uint32_t n_h,
+                                     uint32_t *keys, uint32_t *perm, uint32_t *cell_start, void *stream);
 
 #ifdef __cplusplus
 }

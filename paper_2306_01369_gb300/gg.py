@@ -45,6 +45,7 @@ SIGNATURES = {
     "gg_tuning_selected": (C.c_uint32, [_P]),
     "gg_last_error": (C.c_char_p, [_P]),
     "gg_destroy": (None, [_P]),
+    "gg_bin_sort_noalloc": (C.c_int, [_P, C.c_uint32, C.c_float, C.c_uint32, _P, _P, _P, _P]),
 }
 
 
