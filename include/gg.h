@@ -221,6 +221,30 @@ GG_API gg_status gg_stage_ms(gg_sim *sim, float *ms);
 /* Kernel launches one step enqueues (all of them this library's own kernels). */
 GG_API uint32_t gg_kernels_per_step(const gg_sim *sim);
 
+/*
+ * Differentiation (beyond the paper, whose Sec. V lists it as future work).
+ * Reverse-mode gradients of a loss on the final state w.r.t. the per-step twists of
+ * one kinematic body (the tool) and w.r.t. mu, through contact generation, the
+ * projected-Jacobi iterations and the integrator, with the contact set and the
+ * active set of every projection fixed as the forward found them (piecewise
+ * differentiation).  Single environment, kinematic bodies only.
+ *
+ * gg_tape_reserve: allocate checkpoint and tape memory for n_steps taped steps with a
+ *   full-state checkpoint every `checkpoint_every` steps (recompute in between).
+ * gg_step_taped: enqueue n_steps (<= reserved) forward steps saving the checkpoints;
+ *   the tool's twist for those steps must come from gg_set_trajectory.
+ * gg_backward: gradients of L given dL/dx_N (float[n][3]), dL/dv_N (float[n][3]; NULL
+ *   = 0) and dL/d(tool pose at N) (float[7]: d/dpos[3], d/dquat[4] with quat (w,x,y,z);
+ *   NULL = 0), N = the end of the taped run.  Writes dL/dtwist (float[n_steps][6]:
+ *   d/dlin_vel, d/dang_vel, world frame) and dL/dmu (float[1]).  Inputs and outputs
+ *   on the device when on_device != 0.  Re-runs the forward from the checkpoints and
+ *   leaves the simulation in its end-of-run state.  Synchronises `stream`.
+ */
+GG_API gg_status gg_tape_reserve(gg_sim *sim, uint32_t n_steps, uint32_t checkpoint_every);
+GG_API gg_status gg_step_taped(gg_sim *sim, uint32_t tool_body, uint32_t n_steps, void *stream);
+GG_API gg_status gg_backward(gg_sim *sim, const float *dL_dpos, const float *dL_dvel, const float *dL_dpose,
+                             float *dL_dtwist, float *dL_dmu, int on_device, void *stream);
+
 /* Number of fixed launch-shape sets accepted by gg_params.tuning, and the set chosen. */
 GG_API uint32_t gg_tuning_count(void);
 GG_API uint32_t gg_tuning_selected(const gg_sim *sim);

@@ -61,6 +61,15 @@ struct gg_sim {
   void *staging = nullptr;
   size_t staging_bytes = 0;
   float *vel3 = nullptr;  // n*3 staging for velocity upload / readback
+  // differentiation: checkpoints, per-step tape, adjoint buffers
+  struct {
+    uint32_t n_steps = 0, K = 0, taped = 0, tool = 0xffffffffu;
+    size_t state_bytes = 0;
+    char *ckpt = nullptr, *seg = nullptr, *fin = nullptr;
+    gg::Tape tp{};
+    gg::AdjArgs d{};
+    std::vector<void *> allocs;
+  } ad;
   bool timing = false;
   cudaEvent_t ev[5] = {};
   std::string err;
@@ -135,6 +144,49 @@ gg_status ensure_staging(gg_sim *s, size_t bytes) {
 }
 
 bool finite_pos(float v) { return std::isfinite(v); }
+
+// One simulation state (what a step reads): particles, bodies, control word.
+size_t state_bytes(const gg_sim *s) {
+  const size_t nbt = (size_t)s->n_envs * s->maxb;
+  return (size_t)s->n * 32 + nbt * sizeof(DevBody) + sizeof(DevCtrl);
+}
+
+gg_status save_state(gg_sim *s, char *dst, cudaStream_t st) {
+  const size_t n = s->n, nbt = (size_t)s->n_envs * s->maxb;
+  if (n) {
+    GG_CUDA(s, cudaMemcpyAsync(dst, s->a.pos_id, n * 16, cudaMemcpyDeviceToDevice, st));
+    GG_CUDA(s, cudaMemcpyAsync(dst + n * 16, s->a.vel_id, n * 16, cudaMemcpyDeviceToDevice, st));
+  }
+  GG_CUDA(s, cudaMemcpyAsync(dst + n * 32, s->a.bodies, nbt * sizeof(DevBody), cudaMemcpyDeviceToDevice, st));
+  GG_CUDA(s, cudaMemcpyAsync(dst + n * 32 + nbt * sizeof(DevBody), s->a.ctrl, sizeof(DevCtrl),
+                             cudaMemcpyDeviceToDevice, st));
+  return GG_OK;
+}
+
+gg_status restore_state(gg_sim *s, const char *src, cudaStream_t st) {
+  const size_t n = s->n, nbt = (size_t)s->n_envs * s->maxb;
+  if (n) {
+    GG_CUDA(s, cudaMemcpyAsync(s->a.pos_id, src, n * 16, cudaMemcpyDeviceToDevice, st));
+    GG_CUDA(s, cudaMemcpyAsync(s->a.vel_id, src + n * 16, n * 16, cudaMemcpyDeviceToDevice, st));
+  }
+  GG_CUDA(s, cudaMemcpyAsync(s->a.bodies, src + n * 32, nbt * sizeof(DevBody), cudaMemcpyDeviceToDevice, st));
+  GG_CUDA(s, cudaMemcpyAsync(s->a.ctrl, src + n * 32 + nbt * sizeof(DevBody), sizeof(DevCtrl),
+                             cudaMemcpyDeviceToDevice, st));
+  return GG_OK;
+}
+
+template <typename T>
+gg_status ad_alloc(gg_sim *s, T **ptr, size_t count) {
+  void *p = nullptr;
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(s, GG_ERR_OOM, "tape allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  s->ad.allocs.push_back(p);
+  *ptr = static_cast<T *>(p);
+  return GG_OK;
+}
 
 gg_status capture(gg_sim *s) {
   free_graph(s);
@@ -211,6 +263,7 @@ void gg_destroy(gg_sim *sim) {
     if (ev) cudaEventDestroy(ev);
   if (sim->cap) cudaStreamDestroy(sim->cap);
   for (void *p : sim->allocs) cudaFree(p);
+  for (void *p : sim->ad.allocs) cudaFree(p);
   for (float *t : sim->traj)
     if (t) cudaFree(t);
   if (sim->staging) cudaFree(sim->staging);
@@ -708,6 +761,146 @@ gg_status gg_set_state(gg_sim *s, const void *state, size_t bytes, int on_device
   GG_CUDA(s, cudaMemcpy(s->a.ctrl, &c, sizeof(c), cudaMemcpyHostToDevice));
   s->steps = hd.steps;
   return GG_OK;
+}
+
+gg_status gg_tape_reserve(gg_sim *s, uint32_t n_steps, uint32_t K) {
+  if (!s) return GG_ERR_INVALID_ARG;
+  if (s->n_envs != 1) return fail(s, GG_ERR_UNSUPPORTED, "differentiation needs a single environment");
+  if (s->F) return fail(s, GG_ERR_UNSUPPORTED, "differentiation of free rigid bodies is not supported");
+  if (n_steps == 0 || K == 0) return fail(s, GG_ERR_INVALID_ARG, "gg_tape_reserve: n_steps and K must be > 0");
+  GG_CUDA(s, cudaDeviceSynchronize());
+  for (void *p : s->ad.allocs) cudaFree(p);
+  s->ad.allocs.clear();
+  s->ad.taped = 0;
+  const size_t n = s->n, I = s->ls.iters, KN = (size_t)s->K * n, KbN = (size_t)s->Kb * n;
+  const uint32_t nblk = gg::adjoint_blocks(s->n);
+  s->ad.state_bytes = (state_bytes(s) + 255) / 256 * 256;
+  const size_t nck = (n_steps + K - 1) / K;
+  gg::Tape &tp = s->ad.tp;
+  gg::AdjArgs &d = s->ad.d;
+  gg_status rc;
+  if ((rc = ad_alloc(s, &s->ad.ckpt, nck * s->ad.state_bytes)) || (rc = ad_alloc(s, &s->ad.seg, (size_t)K * s->ad.state_bytes)) ||
+      (rc = ad_alloc(s, &s->ad.fin, s->ad.state_bytes)) || (rc = ad_alloc(s, &tp.Uh, (I + 1) * n)) ||
+      (rc = ad_alloc(s, &tp.lamh, (I + 1) * 3 * KN)) || (rc = ad_alloc(s, &tp.blamh, (I + 1) * 3 * KbN)) ||
+      (rc = ad_alloc(s, &d.twin, KN)) || (rc = ad_alloc(s, &d.Ubar[0], n)) || (rc = ad_alloc(s, &d.Ubar[1], n)) ||
+      (rc = ad_alloc(s, &d.ubar, 3 * KN)) || (rc = ad_alloc(s, &d.Lbar, 3 * KN)) || (rc = ad_alloc(s, &d.bLbar, 3 * KbN)) ||
+      (rc = ad_alloc(s, &d.psibar, KN)) || (rc = ad_alloc(s, &d.nbar, 3 * KN)) || (rc = ad_alloc(s, &d.bpsibar, KbN)) ||
+      (rc = ad_alloc(s, &d.bnbar, 3 * KbN)) || (rc = ad_alloc(s, &d.bxcbar, 3 * KbN)) ||
+      (rc = ad_alloc(s, &d.basebar, n)) || (rc = ad_alloc(s, &d.xbar_s, n)) || (rc = ad_alloc(s, &d.xbar, n)) ||
+      (rc = ad_alloc(s, &d.vbar, n)) || (rc = ad_alloc(s, &d.part, (I + 1) * nblk * 10)) ||
+      (rc = ad_alloc(s, &d.pose_bar, 6)) || (rc = ad_alloc(s, &d.dtwist, (size_t)n_steps * 6)) ||
+      (rc = ad_alloc(s, &d.mubar, 1)))
+    return rc;
+  d.tp = tp;
+  d.I = (uint32_t)I;
+  d.nblk = nblk;
+  d.tool = 0xffffffffu;
+  s->ad.n_steps = n_steps;
+  s->ad.K = K;
+  return GG_OK;
+}
+
+gg_status gg_step_taped(gg_sim *s, uint32_t tool_body, uint32_t n_steps, void *stream) {
+  if (!s) return GG_ERR_INVALID_ARG;
+  if (!s->ad.ckpt || n_steps == 0 || n_steps > s->ad.n_steps)
+    return fail(s, GG_ERR_INVALID_ARG, "gg_step_taped: reserve at least n_steps with gg_tape_reserve first");
+  if (tool_body >= s->nbodies[0]) return fail(s, GG_ERR_INVALID_ARG, "gg_step_taped: no such body");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (uint32_t k = 0; k < n_steps; ++k) {
+    if (k % s->ad.K == 0) {
+      gg_status rc = save_state(s, s->ad.ckpt + (size_t)(k / s->ad.K) * s->ad.state_bytes, st);
+      if (rc != GG_OK) return rc;
+    }
+    gg_status rc = gg_step(s, 1, stream);
+    if (rc != GG_OK) return rc;
+  }
+  gg_status rc = save_state(s, s->ad.fin, st);
+  if (rc != GG_OK) return rc;
+  s->ad.taped = n_steps;
+  s->ad.tool = tool_body;
+  s->ad.d.tool = tool_body;  // environment 0: global index = local index
+  return GG_OK;
+}
+
+gg_status gg_backward(gg_sim *s, const float *dL_dpos, const float *dL_dvel, const float *dL_dpose, float *dL_dtwist,
+                      float *dL_dmu, int on_device, void *stream) {
+  if (!s) return GG_ERR_INVALID_ARG;
+  if (!s->ad.taped) return fail(s, GG_ERR_INVALID_ARG, "gg_backward: no taped run (gg_step_taped)");
+  if (!dL_dpos || !dL_dtwist || !dL_dmu) return fail(s, GG_ERR_INVALID_ARG, "gg_backward: null pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gg::AdjArgs &d = s->ad.d;
+  const uint32_t N = s->ad.taped, K = s->ad.K, n = s->n;
+  const cudaMemcpyKind h2x = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind x2h = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  // seeds: dL/dx_N, dL/dv_N (float3 -> float4, id order)
+  const float *src = dL_dpos;
+  if (!on_device && n) {
+    GG_CUDA(s, cudaMemcpyAsync(s->vel3, dL_dpos, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st));
+    src = s->vel3;
+  }
+  GG_CUDA(s, gg::enqueue_pack3(d.xbar, src, n, st));
+  src = dL_dvel;
+  if (dL_dvel && !on_device && n) {
+    GG_CUDA(s, cudaMemcpyAsync(s->vel3, dL_dvel, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st));
+    src = s->vel3;
+  }
+  GG_CUDA(s, gg::enqueue_pack3(d.vbar, src, n, st));
+  // seed of the tool pose: dL/dp, and dL/dq turned into a world-frame rotation adjoint
+  // (q' = exp(dtheta / 2) q:  rbar_k = 1/2 <(0, e_k) q, dL/dq>)
+  float pose6[6] = {0, 0, 0, 0, 0, 0};
+  if (dL_dpose) {
+    float g7[7];
+    GG_CUDA(s, cudaMemcpyAsync(g7, dL_dpose, sizeof(g7), h2x == cudaMemcpyHostToDevice ? cudaMemcpyHostToHost
+                                                                                     : cudaMemcpyDeviceToHost, st));
+    DevBody tb;
+    const size_t nbt = (size_t)s->n_envs * s->maxb;
+    GG_CUDA(s, cudaMemcpyAsync(&tb, s->ad.fin + (size_t)n * 32 + (size_t)s->ad.tool * sizeof(DevBody), sizeof(DevBody),
+                               cudaMemcpyDeviceToHost, st));
+    GG_CUDA(s, cudaStreamSynchronize(st));
+    (void)nbt;
+    const float w = tb.q[0], x = tb.q[1], y = tb.q[2], z = tb.q[3];
+    const float *gq = g7 + 3;
+    pose6[0] = g7[0];
+    pose6[1] = g7[1];
+    pose6[2] = g7[2];
+    pose6[3] = 0.5f * (-x * gq[0] + w * gq[1] - z * gq[2] + y * gq[3]);
+    pose6[4] = 0.5f * (-y * gq[0] + z * gq[1] + w * gq[2] - x * gq[3]);
+    pose6[5] = 0.5f * (-z * gq[0] - y * gq[1] + x * gq[2] + w * gq[3]);
+  }
+  GG_CUDA(s, cudaMemcpyAsync(d.pose_bar, pose6, sizeof(pose6), cudaMemcpyHostToDevice, st));
+  GG_CUDA(s, cudaMemsetAsync(d.mubar, 0, sizeof(double), st));
+  GG_CUDA(s, cudaStreamSynchronize(st));  // pose6 lives on this stack frame
+  if (!s->graph_ready) {
+    gg_status rc = capture(s);
+    if (rc != GG_OK) return rc;
+  }
+  const uint32_t nseg = (N + K - 1) / K;
+  for (int seg = (int)nseg - 1; seg >= 0; --seg) {
+    const uint32_t k0 = (uint32_t)seg * K, k1 = std::min(k0 + K, N);
+    gg_status rc = restore_state(s, s->ad.ckpt + (size_t)seg * s->ad.state_bytes, st);
+    if (rc != GG_OK) return rc;
+    for (uint32_t k = k0; k < k1; ++k) {  // recompute the segment's step-start states
+      if ((rc = save_state(s, s->ad.seg + (size_t)(k - k0) * s->ad.state_bytes, st)) != GG_OK) return rc;
+      if (k + 1 < k1) GG_CUDA(s, cudaGraphLaunch(s->exec, st));
+    }
+    for (int k = (int)k1 - 1; k >= (int)k0; --k) {  // reverse the steps
+      if ((rc = restore_state(s, s->ad.seg + (size_t)(k - k0) * s->ad.state_bytes, st)) != GG_OK) return rc;
+      GG_CUDA(s, gg::enqueue_step(s->a, s->ls, st, nullptr, &s->ad.tp));
+      GG_CUDA(s, gg::enqueue_adjoint_step(s->a, d, (uint32_t)k, st));
+    }
+  }
+  gg_status rc = restore_state(s, s->ad.fin, st);
+  if (rc != GG_OK) return rc;
+  GG_CUDA(s, cudaMemcpyAsync(dL_dtwist, d.dtwist, sizeof(float) * 6 * N, x2h, st));
+  double mu = 0.0;
+  GG_CUDA(s, cudaMemcpyAsync(&mu, d.mubar, sizeof(double), cudaMemcpyDeviceToHost, st));
+  GG_CUDA(s, cudaStreamSynchronize(st));
+  const float muf = (float)mu;
+  GG_CUDA(s, cudaMemcpy(dL_dmu, &muf, sizeof(float), on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+  DevCtrl c;
+  rc = read_ctrl(s, &c, st);
+  if (rc != GG_OK) return rc;
+  return status_from_flags(s, c.status);
 }
 
 }  // extern "C"

@@ -260,13 +260,44 @@ __device__ __forceinline__ float3 rot_apply(const float *R, float3 g) {
                      R[6] * g.x + R[7] * g.y + R[8] * g.z);
 }
 
+// Tape of one step for the adjoint: every iterate of the sweep.
+struct Tape {
+  float4 *Uh;    // [I + 1][n] velocity estimates U^0 .. U^I
+  float *lamh;   // [I + 1][3][K][n] pair impulses lambda^0 .. lambda^I
+  float *blamh;  // [I + 1][3][Kb][n] body-contact impulses
+};
+
+// Adjoint state of one reversed step (slot order unless noted).
+struct AdjArgs {
+  Tape tp;
+  uint32_t I;              // sweeps per step
+  uint32_t tool;           // global body index whose twists are differentiated (~0u: none)
+  uint32_t nblk;           // blocks of the per-slot adjoint kernels
+  uint32_t *twin;          // [K][n] position of contact (j -> i) in j's list
+  float4 *Ubar[2];         // adjoint of U^{s+1} / U^s
+  float *ubar;             // [3][K][n] adjoint of each pair contact's relative velocity
+  float *Lbar, *bLbar;     // [3][K][n], [3][Kb][n] adjoint of lambda^s (carried down the sweeps)
+  float *psibar, *nbar;    // [K][n], [3][K][n]
+  float *bpsibar, *bnbar, *bxcbar;  // [Kb][n], [3][Kb][n], [3][Kb][n]
+  float4 *basebar;         // adjoint of v + dt g
+  float4 *xbar_s;          // adjoint of x_{k+1} in slot order
+  float4 *xbar, *vbar;     // id order: in dL/dx_{k+1}, dL/dv_{k+1}; out dL/dx_k, dL/dv_k
+  float *part;             // [I + 1][nblk][10] fixed-order partial sums
+  float *pose_bar;         // [6] adjoint of the tool pose (p, rotation), updated per step
+  float *dtwist;           // [steps][6] output
+  double *mubar;           // [1] dL/dmu, accumulated
+};
+
+// Pre-projection impulse of one contact update: lambda - w (u - bias n).
+__device__ __forceinline__ float3 pja_pre(float3 lam, float3 u, float3 n, float bias, float w) {
+  return make_float3(lam.x - w * (u.x - bias * n.x), lam.y - w * (u.y - bias * n.y), lam.z - w * (u.z - bias * n.z));
+}
+
 // One projected-Jacobi contact update (Alg. 1 with the accumulated-impulse clamp).
 // lam: accumulated impulse on the particle; u: relative velocity particle - partner;
 // n: unit normal partner -> particle; bias: alpha psi / dt; w: effective mass.
-__device__ __forceinline__ float3 pja_project(float3 lam, float3 u, float3 n, float bias, float w, float mu) {
-  float sx = lam.x - w * (u.x - bias * n.x);
-  float sy = lam.y - w * (u.y - bias * n.y);
-  float sz = lam.z - w * (u.z - bias * n.z);
+__device__ __forceinline__ float3 pja_cone(float3 s, float3 n, float mu) {
+  const float sx = s.x, sy = s.y, sz = s.z;
   float ln = sx * n.x + sy * n.y + sz * n.z;
   float lnp = fmaxf(ln, 0.0f);
   float tx = sx - ln * n.x, ty = sy - ln * n.y, tz = sz - ln * n.z;
@@ -279,6 +310,10 @@ __device__ __forceinline__ float3 pja_project(float3 lam, float3 u, float3 n, fl
     tz *= sc;
   }
   return make_float3(lnp * n.x + tx, lnp * n.y + ty, lnp * n.z + tz);
+}
+
+__device__ __forceinline__ float3 pja_project(float3 lam, float3 u, float3 n, float bias, float w, float mu) {
+  return pja_cone(pja_pre(lam, u, n, bias, w), n, mu);
 }
 
 }  // namespace gg

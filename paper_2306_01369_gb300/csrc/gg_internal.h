@@ -13,8 +13,15 @@ struct LaunchShape {
 };
 
 // ev (optional): 5 events recorded at the stage boundaries of the step.
-cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st, cudaEvent_t *ev = nullptr);
+// tape (optional): keep every sweep's iterates and stop after the sweeps (no
+// integration, wrench or pose update): the first half of a step for the adjoint.
+cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st, cudaEvent_t *ev = nullptr,
+                         const Tape *tape = nullptr);
 uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls);
+// reverse of one taped step (after enqueue_step with a tape, which stops after the sweeps)
+cudaError_t enqueue_adjoint_step(const StepArgs &a, const AdjArgs &d, uint32_t k_local, cudaStream_t st);
+uint32_t adjoint_blocks(uint32_t n);
+cudaError_t enqueue_pack3(float4 *dst, const float *src3, uint32_t n, cudaStream_t st);
 cudaError_t enqueue_export_contacts(const StepArgs &a, uint32_t *rows, float *geom, float *lam, float *bgeom,
                                     float *blam, cudaStream_t st);
 cudaError_t enqueue_vel3_to_vel4(float4 *vel_id, const float *vel3, uint32_t n, cudaStream_t st);

@@ -368,7 +368,10 @@ __global__ void __launch_bounds__(256) k_contacts(StepArgs a) {
 // 6. one projected-Jacobi sweep: U[s] -> U[s^1]
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(512) k_pja(StepArgs a, int s) {
+// s: double-buffer index (U[s] -> U[s^1]).  TAPE: also keep this sweep's iterates
+// in tape slot it + 1 (it = iteration number) for the adjoint.
+template <bool TAPE>
+__global__ void __launch_bounds__(512) k_pja(StepArgs a, int s, Tape tp, int it) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const float4 *__restrict__ Uin = a.U[s];
@@ -391,6 +394,12 @@ __global__ void __launch_bounds__(512) k_pja(StepArgs a, int s) {
     a.clam[o] = l.x;
     a.clam[o + KN] = l.y;
     a.clam[o + 2 * KN] = l.z;
+    if (TAPE) {
+      float *h = tp.lamh + (size_t)(it + 1) * 3 * KN;
+      h[o] = l.x;
+      h[o + KN] = l.y;
+      h[o + 2 * KN] = l.z;
+    }
     sx += l.x;
     sy += l.y;
     sz += l.z;
@@ -421,11 +430,19 @@ __global__ void __launch_bounds__(512) k_pja(StepArgs a, int s) {
     a.blam[o] = l.x;
     a.blam[o + KbN] = l.y;
     a.blam[o + 2 * KbN] = l.z;
+    if (TAPE) {
+      float *h = tp.blamh + (size_t)(it + 1) * 3 * KbN;
+      h[o] = l.x;
+      h[o + KbN] = l.y;
+      h[o + 2 * KbN] = l.z;
+    }
     sx += l.x;
     sy += l.y;
     sz += l.z;
   }
-  a.U[s ^ 1][i] = make_float4(base.x + base.w * sx, base.y + base.w * sy, base.z + base.w * sz, ui.w);
+  const float4 un = make_float4(base.x + base.w * sx, base.y + base.w * sy, base.z + base.w * sz, ui.w);
+  a.U[s ^ 1][i] = un;
+  if (TAPE) tp.Uh[(size_t)(it + 1) * n + i] = un;
 }
 
 // ---------------------------------------------------------------------------
@@ -795,6 +812,12 @@ __global__ void k_vel3_to_vel4(float4 *vel_id, const float *vel3, uint32_t n) {
   vel_id[i] = make_float4(vel3[3 * i], vel3[3 * i + 1], vel3[3 * i + 2], v.w);
 }
 
+__global__ void k_pack3(float4 *dst, const float *src3, uint32_t n) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  dst[i] = src3 ? make_float4(src3[3 * i], src3[3 * i + 1], src3[3 * i + 2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 __global__ void k_vel4_to_vel3(const float4 *vel_id, float *vel3, uint32_t n) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -834,7 +857,7 @@ uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls) {
   return k;
 }
 
-cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st, cudaEvent_t *ev) {
+cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st, cudaEvent_t *ev, const Tape *tp) {
   cudaError_t e;
   const uint32_t nbt = a.n_envs * a.maxb;
   const uint32_t nk = a.n > nbt ? a.n : nbt;
@@ -852,10 +875,22 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
   if (a.n) k_contacts<<<grid_for(a.n, 256), 256, 0, st>>>(a);
   if (a.F) k_free_prep<<<a.F, 1024, 0, st>>>(a);
   if ((e = mark(ev, 2, st)) != cudaSuccess) return e;
+  if (tp && a.n) {  // U^0 and lambda^0 = 0 open the tape
+    if ((e = cudaMemcpyAsync(tp->Uh, a.U[0], sizeof(float4) * a.n, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(tp->lamh, 0, sizeof(float) * 3 * (size_t)a.K * a.n, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(tp->blamh, 0, sizeof(float) * 3 * (size_t)a.Kb * a.n, st)) != cudaSuccess) return e;
+  }
+  const Tape none{};
   for (uint32_t it = 0; it < ls.iters; ++it) {
-    if (a.n) k_pja<<<grid_for(a.n, ls.pja_block), ls.pja_block, 0, st>>>(a, it & 1);
+    if (a.n) {
+      if (tp)
+        k_pja<true><<<grid_for(a.n, ls.pja_block), ls.pja_block, 0, st>>>(a, it & 1, *tp, (int)it);
+      else
+        k_pja<false><<<grid_for(a.n, ls.pja_block), ls.pja_block, 0, st>>>(a, it & 1, none, (int)it);
+    }
     if (a.F) k_free_update<<<a.F, 256, 0, st>>>(a);
   }
+  if (tp) return cudaGetLastError();
   if ((e = mark(ev, 3, st)) != cudaSuccess) return e;
   if (a.n) k_integrate<<<grid_for(a.n, 256), 256, 0, st>>>(a, ls.iters & 1);
   if (a.n_chunks) {
@@ -876,6 +911,11 @@ cudaError_t enqueue_export_contacts(const StepArgs &a, uint32_t *rows, float *ge
 
 cudaError_t enqueue_vel3_to_vel4(float4 *vel_id, const float *vel3, uint32_t n, cudaStream_t st) {
   if (n) k_vel3_to_vel4<<<grid_for(n, 256), 256, 0, st>>>(vel_id, vel3, n);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_pack3(float4 *dst, const float *src3, uint32_t n, cudaStream_t st) {
+  if (n) k_pack3<<<grid_for(n, 256), 256, 0, st>>>(dst, src3, n);
   return cudaGetLastError();
 }
 

@@ -46,6 +46,9 @@ SIGNATURES = {
     "gg_last_error": (C.c_char_p, [_P]),
     "gg_destroy": (None, [_P]),
     "gg_bin_sort_noalloc": (C.c_int, [_P, C.c_uint32, C.c_float, C.c_uint32, _P, _P, _P, _P]),
+    "gg_tape_reserve": (C.c_int, [_P, C.c_uint32, C.c_uint32]),
+    "gg_step_taped": (C.c_int, [_P, C.c_uint32, C.c_uint32, _P]),
+    "gg_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, _P]),
 }
 
 
@@ -314,6 +317,39 @@ class Sim:
         return {"pp_off": pp_off, "pp_j": rows[:, 2:2 + self.K][mpp], "pp_geom": geom[mpp], "pp_lam": lam[mpp],
                 "bc_off": bc_off, "bc_b": rows[:, 2 + self.K:][mb], "bc_geom": bgeom[mb][:, :7],
                 "bc_lam": blam[mb]}
+
+    # ------------------------------------------------------------------ adjoint
+    def tape_reserve(self, n_steps, checkpoint_every):
+        self._check(self._L.gg_tape_reserve(self.h, n_steps, checkpoint_every), "gg_tape_reserve")
+
+    def step_taped(self, tool_body, n_steps, stream=None):
+        self._check(self._L.gg_step_taped(self.h, tool_body, n_steps, _stream(stream)), "gg_step_taped")
+        self._taped = n_steps
+
+    def backward(self, dpos, dvel=None, dpose=None, stream=None):
+        """Gradients (dL/dtwist float32 (T, 6), dL/dmu float) of a loss whose gradient
+        w.r.t. the final positions (n, 3), velocities (n, 3) and tool pose (7,) is given.
+        numpy in -> numpy out; CUDA tensors in -> CUDA tensors out."""
+        if _is_torch(dpos):
+            import torch
+            dev = dpos.device
+            dtw = torch.empty((self._taped, 6), dtype=torch.float32, device=dev)
+            dmu = torch.empty((1,), dtype=torch.float32, device=dev)
+            args = [t.contiguous() if t is not None else None for t in (dpos, dvel, dpose)]   # keep alive
+            ptrs = [C.c_void_p(t.data_ptr()) if t is not None else None for t in args]
+            st = self._L.gg_backward(self.h, ptrs[0], ptrs[1], ptrs[2], C.c_void_p(dtw.data_ptr()),
+                                     C.c_void_p(dmu.data_ptr()), 1, _stream(stream))
+            self._check(st, "gg_backward")
+            return dtw, dmu
+        dpos = np.ascontiguousarray(dpos, np.float32)
+        dvel = None if dvel is None else np.ascontiguousarray(dvel, np.float32)
+        dpose = None if dpose is None else np.ascontiguousarray(dpose, np.float32)
+        dtw = np.empty((self._taped, 6), np.float32)
+        dmu = np.empty(1, np.float32)
+        st = self._L.gg_backward(self.h, _ptr(dpos)[0], _ptr(dvel)[0], _ptr(dpose)[0], C.c_void_p(dtw.ctypes.data),
+                                 C.c_void_p(dmu.ctypes.data), 0, _stream(stream))
+        self._check(st, "gg_backward")
+        return dtw, float(dmu[0])
 
     def stats(self):
         s = GGStats()

@@ -278,6 +278,45 @@ def scoop_bed(n=32768, seed=1004, n_steps=200, dims=None):
                  Params(dt=1e-4, mu=0.5, pja_iters=20), n_steps, twist={1: tw}, info=info)
 
 
+def diff_scene(n=32768, seed=1004, n_steps=200):
+    """Differentiable workload: a bed of n spheres (r = 2 mm +-10 %, cubic lattice
+    footprint) in a container with a scoop (box minus box) embedded in it: the
+    scoop's cavity floor sits at a third of the bed's height, and lattice sites whose
+    sphere would cut the scoop's walls or floor are left empty, so the cavity starts
+    full of particles and nothing overlaps the tool.  The scoop follows a seeded
+    6-waypoint path (slow: 0.2 s per segment); dt = 1e-4 s, 20 PJA iterations."""
+    r0, jit = 2e-3, 0.10
+    side = max(4, int(round(n ** (1.0 / 3.0))))
+    pitch = 2.0 * r0 * (1 + jit) * 1.02
+    foot = side * pitch
+    layers_total = -(-n // (side * side)) + side      # spare sites for the ones inside the walls
+    cand, _ = jittered_lattice((side, side, layers_total), side * side * layers_total, r0, jit, seed,
+                               origin=(-0.5 * foot, -0.5 * foot, 0.0), pitch=pitch)
+    scale = 0.5 * foot / 0.12
+    scoop0 = scoop_body(scale)
+    ha = np.array(scoop0.shape[0:3]); hb = np.array(scoop0.shape[3:6]); cb = np.array(scoop0.shape[6:9])
+    height = (-(-n // (side * side))) * pitch
+    zfloor = height / 3.0                       # world height of the cavity floor
+    pz = zfloor - (cb[2] - hb[2])               # scoop origin so that its cavity floor is at zfloor
+    x = cand[:, :3].astype(np.float64) - np.array([0.0, 0.0, pz])
+    r = cand[:, 3:4].astype(np.float64)
+    in_a = np.all(np.abs(x) < ha + r, axis=1)                 # touches the outer box ...
+    in_b = np.all(np.abs(x - cb) < hb - r, axis=1)            # ... but not well inside the cavity
+    keep = ~(in_a & ~in_b)
+    pr = cand[keep][:n].copy()
+    assert pr.shape[0] == n
+    half = 0.5 * foot + 0.005
+    container = Body(kind=OPEN_BOX, shape=(half, half, 0.0), pos=(0.0, 0.0, 0.0))
+    tw, rv0, p0 = waypoint_twists(seed * 7 + 3, n_steps, 1e-4, (0.0, 0.0, pz), dig_depth=-0.3 * height,
+                                  span=0.3 * foot, pos_jit=0.1 * foot, rot_range=0.15)
+    scoop = scoop_body(scale, pos=p0, rotvec=(0.0, 0.0, 0.0))
+    tw = tw.copy()
+    return Scene(f"diff_scene_{n}", pr, np.zeros((n, 3), np.float32), sphere_mass(pr[:, 3]), [container, scoop],
+                 Params(dt=1e-4, mu=0.5, pja_iters=20), n_steps, twist={1: tw},
+                 info={"side": side, "pitch": pitch, "scoop_scale": scale, "eps": 0.5 * r0,
+                       "cavity_floor_z": zfloor})
+
+
 def batched_beds(n_envs=256, seed=1003, n_steps=500, n_min=8192, n_max=65536):
     """n_envs independent beds with n_e = round(exp(U(ln n_min, ln n_max))) spheres,
     radius r_e ~ U(2, 4) mm (+-10 %), 16 layers, each with its own container and a

@@ -1,0 +1,122 @@
+"""Gradients of a task loss w.r.t. the tool's per-step twists and mu (hand-written
+adjoint behind torch.autograd.Function; beyond the paper, Sec. V future work).
+
+Scene: 512 spheres settled by the FP64 oracle around a stationary scoop (the
+oracle's FP32-rounded state is the common input), then 10 steps with the scoop
+on its seeded path.  Loss: the smooth mass inside the scoop's cavity.  The oracle
+gradient is the central finite difference of the FP64 oracle's loss (contact and
+active sets do not change under steps this small).
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from gpu_helpers import F32, need_gpu
+from paper_2306_01369_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+T_STEPS = 10
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return need_gpu()
+
+
+@pytest.fixture(scope="module")
+def scene():
+    import oracle
+    sc = S.diff_scene(n=512, n_steps=T_STEPS)
+    o = oracle.Sim(sc.pos_r, sc.vel, sc.mass, sc.bodies, sc.params, twist={}, n_threads=8)
+    o.step(600)   # settle around the stationary scoop
+    pos_r = np.empty_like(sc.pos_r)
+    pos_r[:, :3] = o.x
+    pos_r[:, 3] = sc.pos_r[:, 3]
+    return S.Scene("diff_settled_512", pos_r, o.v.astype(F32), sc.mass, sc.bodies, sc.params, T_STEPS,
+                   twist={1: sc.twist[1]}, info=sc.info)
+
+
+def oracle_loss(scene, tw, mu):
+    import oracle
+    p = dataclasses.replace(scene.params, mu=mu)
+    o = oracle.Sim(scene.pos_r, scene.vel, scene.mass, scene.bodies, p, twist={1: tw}, n_threads=4)
+    o.step(tw.shape[0])
+    return o.scoop_loss(1, scene.info["eps"])
+
+
+def gpu_grad(torch, scene, checkpoint_every=4):
+    from paper_2306_01369_gb300.autograd import rollout, scoop_mass
+    dev = torch.device("cuda", 0)
+    tw = torch.tensor(scene.twist[1], device=dev, requires_grad=True)
+    mu = torch.tensor(float(scene.params.mu), device=dev, requires_grad=True)
+    pos, vel, pose = rollout(tw, mu, scene, 1, checkpoint_every)
+    L = scoop_mass(pos, torch.tensor(scene.mass, device=dev), pose, scene.bodies[1].shape12(), scene.info["eps"])
+    L.backward()
+    return float(L.detach()), tw.grad.cpu().numpy().astype(np.float64), float(mu.grad)
+
+
+def fd(f, x32, h):
+    """Central difference of f at float32 x32 (the step actually taken after rounding)."""
+    xp, xm = F32(float(x32) + h), F32(float(x32) - h)
+    return (f(xp) - f(xm)) / (float(xp) - float(xm))
+
+
+def test_adjoint_matches_oracle_gradient(torch, scene):
+    L, g_tw, g_mu = gpu_grad(torch, scene)
+    tw0 = scene.twist[1].astype(F32)
+    mu0 = F32(scene.params.mu)
+    L_orc = oracle_loss(scene, tw0, float(mu0))
+    assert abs(L - L_orc) < 1e-4 * L_orc
+    want = np.zeros_like(g_tw)
+    for k in range(T_STEPS):
+        for c in range(6):
+            def f(v, k=k, c=c):
+                t = tw0.copy()
+                t[k, c] = v
+                return oracle_loss(scene, t, float(mu0))
+            want[k, c] = fd(f, tw0[k, c], 1e-5 if c < 3 else 1e-4)
+    want_mu = fd(lambda v: oracle_loss(scene, tw0, float(v)), mu0, 1e-4)
+    assert np.abs(want).max() > 0
+    cos = float((g_tw * want).sum() / (np.linalg.norm(g_tw) * np.linalg.norm(want)))
+    rel = float(np.abs(g_tw - want).max() / np.abs(want).max())
+    assert cos > 0.999, (cos, rel)
+    assert rel < 1e-2, (cos, rel)
+    assert abs(g_mu - want_mu) <= 1e-2 * max(abs(want_mu), 1e-3 * np.abs(want).max()), (g_mu, want_mu)
+
+
+def test_adjoint_invariant_to_checkpoint_interval(torch, scene):
+    ref = gpu_grad(torch, scene, checkpoint_every=1)
+    for K in (3, 10):
+        got = gpu_grad(torch, scene, checkpoint_every=K)
+        assert got[0] == ref[0]
+        assert np.array_equal(got[1], ref[1]) and got[2] == ref[2]
+
+
+def test_adjoint_matches_gpu_finite_differences(torch, scene):
+    """Central differences of the GPU's own FP32 forward on the largest components."""
+    from paper_2306_01369_gb300.autograd import rollout, scoop_mass
+    L, g_tw, _ = gpu_grad(torch, scene)
+    dev = torch.device("cuda", 0)
+    mass = torch.tensor(scene.mass, device=dev)
+
+    def loss(tw):
+        with torch.no_grad():
+            pos, vel, pose = rollout(torch.tensor(tw, device=dev), torch.tensor(float(scene.params.mu), device=dev),
+                                     scene, 1, 10)
+            return float(scoop_mass(pos.double(), mass.double(), pose.double(), scene.bodies[1].shape12(),
+                                    scene.info["eps"]))
+
+    tw0 = scene.twist[1].astype(F32)
+    gmax = np.abs(g_tw).max()
+    idx = [i for i in np.argsort(-np.abs(g_tw).ravel())[:4] if abs(g_tw.ravel()[i]) >= 0.1 * gmax]
+    assert idx
+    for flat in idx:
+        k, c = divmod(int(flat), 6)
+        h = 1e-3 if c < 3 else 1e-2
+        tp, tm = tw0.copy(), tw0.copy()
+        tp[k, c] += h
+        tm[k, c] -= h
+        g = (loss(tp) - loss(tm)) / (float(tp[k, c]) - float(tm[k, c]))
+        assert abs(g - g_tw[k, c]) < 0.1 * abs(g_tw[k, c]), (k, c, g, g_tw[k, c])
