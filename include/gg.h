@@ -87,12 +87,16 @@ typedef struct {
   uint32_t max_body_contacts;/* particle-body contact capacity per particle, 1..8; 0 -> 4 */
   uint32_t max_bodies;       /* bodies per environment, 1..64; 0 -> 8 */
   float density;             /* mass = density 4/3 pi r^3 when no masses are given; 0 -> 2500 */
-  uint32_t tuning;           /* 0: pick launch shapes by timing (results do not depend on it);
-                                k >= 1: fixed launch-shape set k (see gg_tuning_count) */
+  uint32_t tuning;           /* 0: the first gg_step times every launch-shape set on a copy of the
+                                state (restored bit-exactly) and keeps the fastest; k >= 1: fixed
+                                set k (see gg_tuning_count).  Results do not depend on it. */
   uint32_t wrench_history;   /* per-step body wrenches kept for readback; 0 -> 1 */
   uint32_t max_free_bodies;  /* free rigid bodies over all environments (beyond the paper's
                                 kinematic bodies, Sec. V two-way coupling); 0 -> none */
   uint32_t free_contact_capacity; /* particle contacts per free body per step, 1..8192; 0 -> 4096 */
+  uint32_t barrier_test_phantoms; /* testing aid, 0 in normal use: phantom participants that every
+                                     grid barrier of the fused sweep waits for, so each wait runs
+                                     out (bounded) and the step reports GG_ERR_DEVICE_TIMEOUT */
 } gg_params;
 
 typedef struct {

@@ -26,7 +26,9 @@ using gg::StepArgs;
 namespace {
 
 // Launch-shape sets accepted by gg_params.tuning (index k-1).
-const gg::LaunchShape kShapes[] = {{0, 256}, {0, 128}, {0, 512}, {0, 64}};
+// (iters, per-launch block, fused block; the fused grid is sized per device at create)
+const gg::LaunchShape kShapes[] = {{0, 256, 0, 0}, {0, 128, 0, 0}, {0, 512, 0, 0}, {0, 64, 0, 0},
+                                   {0, 256, 1024, 0}, {0, 256, 512, 0}};
 constexpr uint32_t kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 constexpr uint32_t kStateMagic = 0x31534747u;  // "GGS1"
@@ -71,6 +73,7 @@ struct gg_sim {
     std::vector<void *> allocs;
   } ad;
   bool timing = false;
+  bool tuned = false;
   cudaEvent_t ev[5] = {};
   std::string err;
 };
@@ -109,6 +112,7 @@ gg_status dalloc(gg_sim *s, T **ptr, size_t count) {
 }
 
 gg_status status_from_flags(gg_sim *s, uint32_t f) {
+  if (f & gg::kFlagTimeout) return fail(s, GG_ERR_DEVICE_TIMEOUT, "a grid barrier wait gave up (bounded wait)");
   if (f & gg::kFlagNonFinite) return fail(s, GG_ERR_NONFINITE, "a particle position or velocity became non-finite");
   if (f & (gg::kFlagPPOverflow | gg::kFlagBodyOverflow))
     return fail(s, GG_ERR_CONTACT_OVERFLOW, "a particle exceeded its contact capacity (flags " + std::to_string(f) + ")");
@@ -186,6 +190,71 @@ gg_status ad_alloc(gg_sim *s, T **ptr, size_t count) {
   s->ad.allocs.push_back(p);
   *ptr = static_cast<T *>(p);
   return GG_OK;
+}
+
+// Launch shape k (1-based); a fused shape gets its resident grid from the occupancy.
+gg_status set_shape(gg_sim *s, uint32_t k) {
+  gg::LaunchShape ls = kShapes[k - 1];
+  ls.iters = s->p.pja_iters;
+  if (ls.fused_block) {
+    int nsm = 0;
+    GG_CUDA(s, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device));
+    const int per = gg::fused_pja_blocks_per_sm(ls.fused_block);
+    ls.fused_grid = per > 0 ? (uint32_t)(per * nsm) : 0;
+  }
+  s->ls = ls;
+  s->tuning_sel = k;
+  free_graph(s);
+  return GG_OK;
+}
+
+gg_status capture(gg_sim *s);
+
+// tuning == 0: time every launch-shape set on the current state (3 steps each, after
+// one untimed step), restoring the state before each trial and at the end, and keep
+// the fastest.  Every set gives bit-identical results, so the choice cannot change them.
+gg_status autotune(gg_sim *s, cudaStream_t st) {
+  s->tuned = true;
+  if (s->p.tuning || !s->n) return GG_OK;
+  const size_t bytes = state_bytes(s);
+  char *saved = nullptr;
+  if (cudaMalloc(&saved, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(s, GG_ERR_OOM, "autotune state copy");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float best = 0.f;
+  uint32_t best_k = 1;
+  gg_status rc = save_state(s, saved, st);
+  if (rc == GG_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = cuda_fail(s, cudaGetLastError(), "cudaEventCreate");
+  for (uint32_t k = 1; rc == GG_OK && k <= kNumShapes; ++k) {
+    if ((rc = set_shape(s, k)) != GG_OK || (kShapes[k - 1].fused_block && !s->ls.fused_grid)) continue;
+    if ((rc = capture(s)) != GG_OK) break;
+    if ((rc = restore_state(s, saved, st)) != GG_OK) break;
+    float ms = 0.f;
+    cudaError_t ce = cudaGraphLaunch(s->exec, st);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = cudaGraphLaunch(s->exec, st);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    if (ce != cudaSuccess) {
+      rc = cuda_fail(s, ce, "autotune trial");
+      break;
+    }
+    if (k == 1 || ms < best) {
+      best = ms;
+      best_k = k;
+    }
+  }
+  if (rc == GG_OK) rc = restore_state(s, saved, st);
+  if (rc == GG_OK) rc = set_shape(s, best_k);
+  if (rc == GG_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = cuda_fail(s, cudaGetLastError(), "autotune");
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(saved);
+  return rc;
 }
 
 gg_status capture(gg_sim *s) {
@@ -448,9 +517,13 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
     return bail(cuda_fail(s, e, "initialising buffers"));
   if ((e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(cuda_fail(s, e, "cudaStreamCreate"));
+  if (P.barrier_test_phantoms) {
+    const uint32_t ph = P.barrier_test_phantoms;
+    if ((e = cudaMemcpy(&a.ctrl->bar_extra, &ph, sizeof(ph), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(cuda_fail(s, e, "initialising the control word"));
+  }
   s->tuning_sel = P.tuning ? P.tuning : 1;
-  s->ls = kShapes[s->tuning_sel - 1];
-  s->ls.iters = P.pja_iters;
+  if ((rc = set_shape(s, s->tuning_sel)) != GG_OK) return bail(rc);
   *out = s;
   return GG_OK;
 }
@@ -570,6 +643,10 @@ gg_status gg_set_particles(gg_sim *s, const float *pos_radius, const float *vel,
 
 gg_status gg_step(gg_sim *s, uint32_t n_steps, void *stream) {
   if (!s) return GG_ERR_INVALID_ARG;
+  if (!s->tuned && n_steps) {
+    gg_status rc = autotune(s, static_cast<cudaStream_t>(stream));
+    if (rc != GG_OK) return rc;
+  }
   if (!s->graph_ready) {
     gg_status rc = capture(s);
     if (rc != GG_OK) return rc;

@@ -18,6 +18,8 @@ constexpr uint32_t kHashQ = 100u;        // Eq. 6 offset q
 constexpr uint32_t kFlagPPOverflow = 1u;
 constexpr uint32_t kFlagBodyOverflow = 2u;
 constexpr uint32_t kFlagNonFinite = 4u;
+constexpr uint32_t kFlagTimeout = 8u;    // a bounded device-side wait gave up
+constexpr long long kBarrierCycles = 1000000000LL;  // grid-barrier wait limit (~0.5 s at 2 GHz)
 
 constexpr int kMaxK = 32;   // particle-particle capacity limit
 constexpr int kMaxKb = 8;   // particle-body capacity limit
@@ -63,6 +65,10 @@ struct DevCtrl {
   uint32_t status;    // latched flags
   uint32_t n_pp, n_body, max_pp, max_body;
   uint32_t max_psi_bits;  // max psi as the bits of a non-negative float
+  uint32_t bar_count;     // grid barrier: arrivals in the current round
+  uint32_t bar_gen;       // grid barrier: completed rounds
+  uint32_t bar_abort;     // set when a barrier wait gave up (later barriers return at once)
+  uint32_t bar_extra;     // phantom arrivals a barrier waits for (0; tests set it to force a timeout)
   uint32_t pad;
 };
 

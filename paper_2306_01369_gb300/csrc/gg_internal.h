@@ -8,9 +8,12 @@ namespace gg {
 
 // Launch shape of the step; any choice gives bit-identical results.
 struct LaunchShape {
-  uint32_t iters;      // projected-Jacobi iterations
-  int pja_block;       // threads per block of k_pja
+  uint32_t iters;       // projected-Jacobi iterations
+  int pja_block;        // threads per block of k_pja (one launch per sweep)
+  int fused_block;      // > 0: all sweeps in one cooperative launch of this block size ...
+  uint32_t fused_grid;  // ... and this many blocks (all resident); 0: one launch per sweep
 };
+int fused_pja_blocks_per_sm(int block);
 
 // ev (optional): 5 events recorded at the stage boundaries of the step.
 // tape (optional): keep every sweep's iterates and stop after the sweeps (no

@@ -103,6 +103,8 @@ __global__ void k_key(StepArgs a) {
   }
   if (i < a.F) a.fcount[i] = 0;
   if (i == 0) {
+    a.ctrl->bar_count = 0;
+    a.ctrl->bar_abort = 0;
     a.ctrl->n_pp = 0;
     a.ctrl->n_body = 0;
     a.ctrl->max_pp = 0;
@@ -253,12 +255,20 @@ __global__ void __launch_bounds__(256) k_contacts(StepArgs a) {
     uint32_t fid[kMaxK], fsl[kMaxK];
     const uint32_t K = a.K;
     bool ovf = false;
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          const uint32_t h = E.hbase + hash_cell(k0 + dx, k1 + dy, k2 + dz, E.nh);
-          const uint32_t t1 = a.start[h + 1];
-          for (uint32_t t = a.start[h]; t < t1; ++t) {
+    for (int dz = -1; dz <= 1; ++dz) {
+      // the nine bucket ranges of this plane are loaded together, then walked
+      uint32_t r0[9], r1[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const uint32_t h = E.hbase + hash_cell(k0 + (q % 3) - 1, k1 + (q / 3) - 1, k2 + dz, E.nh);
+        r0[q] = a.start[h];
+        r1[q] = a.start[h + 1];
+      }
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        {
+          const uint32_t t1 = r1[q];
+          for (uint32_t t = r0[q]; t < t1; ++t) {
             if (t == i) continue;
             float d2;
             float3 d;
@@ -282,6 +292,8 @@ __global__ void __launch_bounds__(256) k_contacts(StepArgs a) {
             fsl[p] = t;
           }
         }
+      }
+    }
     const size_t n = a.n;
     for (uint32_t c = 0; c < npp; ++c) {
       const uint32_t j = fsl[c];
@@ -368,32 +380,72 @@ __global__ void __launch_bounds__(256) k_contacts(StepArgs a) {
 // 6. one projected-Jacobi sweep: U[s] -> U[s^1]
 // ---------------------------------------------------------------------------
 
-// s: double-buffer index (U[s] -> U[s^1]).  TAPE: also keep this sweep's iterates
-// in tape slot it + 1 (it = iteration number) for the adjoint.
-template <bool TAPE>
-__global__ void __launch_bounds__(512) k_pja(StepArgs a, int s, Tape tp, int it) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
+// One Jacobi update of particle i: U[s] -> U[s^1] (s: double-buffer index).
+// TAPE: also keep the iterates in tape slot it + 1 (it = iteration number).
+// LDCG: read the velocity estimates through L2 only (the fused kernel reads, within
+// one launch, estimates that other SMs wrote in the previous iteration).
+template <bool TAPE, bool LDCG>
+__device__ __forceinline__ void pja_particle(const StepArgs &a, uint32_t i, int s, const Tape &tp, int it) {
   const float4 *__restrict__ Uin = a.U[s];
+  const uint32_t *__restrict__ cj = a.cj;
+  const float4 *__restrict__ cn = a.cn;
+  float *__restrict__ clam = a.clam;
   const size_t n = a.n;
   const uint32_t cc = a.ccount[i];
   const uint32_t npp = cc & 0xffu, nbc = (cc >> 8) & 0xffu;
-  const float4 ui = Uin[i];
+  const float4 ui = LDCG ? __ldcg(Uin + i) : Uin[i];
   const float4 base = a.sbase[i];
   float sx = 0.f, sy = 0.f, sz = 0.f;
   const size_t KN = (size_t)a.K * n;
-  for (uint32_t c = 0; c < npp; ++c) {
+  const float mu = a.mu, ab = a.ab;
+  // two contacts per round: both rounds' loads issue before either update is stored;
+  // the impulses are still added in contact order
+  uint32_t c = 0;
+  for (; c + 1 < npp; c += 2) {
+    const size_t o0 = (size_t)c * n + i, o1 = o0 + n;
+    const uint32_t j0 = cj[o0], j1 = cj[o1];
+    const float4 n0 = cn[o0], n1 = cn[o1];
+    const float3 la0 = make_float3(clam[o0], clam[o0 + KN], clam[o0 + 2 * KN]);
+    const float3 la1 = make_float3(clam[o1], clam[o1 + KN], clam[o1 + 2 * KN]);
+    const float4 u0 = LDCG ? __ldcg(Uin + j0) : Uin[j0];
+    const float4 u1 = LDCG ? __ldcg(Uin + j1) : Uin[j1];
+    const float3 l0 = pja_project(la0, make_float3(ui.x - u0.x, ui.y - u0.y, ui.z - u0.z), make_float3(n0.x, n0.y, n0.z),
+                                  ab * n0.w, 1.0f / (ui.w + u0.w), mu);
+    const float3 l1 = pja_project(la1, make_float3(ui.x - u1.x, ui.y - u1.y, ui.z - u1.z), make_float3(n1.x, n1.y, n1.z),
+                                  ab * n1.w, 1.0f / (ui.w + u1.w), mu);
+    clam[o0] = l0.x;
+    clam[o0 + KN] = l0.y;
+    clam[o0 + 2 * KN] = l0.z;
+    clam[o1] = l1.x;
+    clam[o1 + KN] = l1.y;
+    clam[o1 + 2 * KN] = l1.z;
+    if (TAPE) {
+      float *h = tp.lamh + (size_t)(it + 1) * 3 * KN;
+      h[o0] = l0.x;
+      h[o0 + KN] = l0.y;
+      h[o0 + 2 * KN] = l0.z;
+      h[o1] = l1.x;
+      h[o1 + KN] = l1.y;
+      h[o1 + 2 * KN] = l1.z;
+    }
+    sx += l0.x;
+    sy += l0.y;
+    sz += l0.z;
+    sx += l1.x;
+    sy += l1.y;
+    sz += l1.z;
+  }
+  if (c < npp) {
     const size_t o = (size_t)c * n + i;
-    const uint32_t j = a.cj[o];
-    const float4 nn = a.cn[o];
-    const float4 uj = Uin[j];
-    const float3 lam = make_float3(a.clam[o], a.clam[o + KN], a.clam[o + 2 * KN]);
-    const float w = 1.0f / (ui.w + uj.w);
-    const float3 u = make_float3(ui.x - uj.x, ui.y - uj.y, ui.z - uj.z);
-    const float3 l = pja_project(lam, u, make_float3(nn.x, nn.y, nn.z), a.ab * nn.w, w, a.mu);
-    a.clam[o] = l.x;
-    a.clam[o + KN] = l.y;
-    a.clam[o + 2 * KN] = l.z;
+    const uint32_t j = cj[o];
+    const float4 nn = cn[o];
+    const float4 uj = LDCG ? __ldcg(Uin + j) : Uin[j];
+    const float3 lam = make_float3(clam[o], clam[o + KN], clam[o + 2 * KN]);
+    const float3 l = pja_project(lam, make_float3(ui.x - uj.x, ui.y - uj.y, ui.z - uj.z), make_float3(nn.x, nn.y, nn.z),
+                                 ab * nn.w, 1.0f / (ui.w + uj.w), mu);
+    clam[o] = l.x;
+    clam[o + KN] = l.y;
+    clam[o + 2 * KN] = l.z;
     if (TAPE) {
       float *h = tp.lamh + (size_t)(it + 1) * 3 * KN;
       h[o] = l.x;
@@ -443,6 +495,57 @@ __global__ void __launch_bounds__(512) k_pja(StepArgs a, int s, Tape tp, int it)
   const float4 un = make_float4(base.x + base.w * sx, base.y + base.w * sy, base.z + base.w * sz, ui.w);
   a.U[s ^ 1][i] = un;
   if (TAPE) tp.Uh[(size_t)(it + 1) * n + i] = un;
+}
+
+// One sweep per launch.
+template <bool TAPE>
+__global__ void __launch_bounds__(512) k_pja(StepArgs a, int s, Tape tp, int it) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n) pja_particle<TAPE, false>(a, i, s, tp, it);
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks resident).  The wait is
+// bounded: past kBarrierCycles it latches kFlagTimeout and sets bar_abort, after
+// which every later barrier returns at once, so the kernel always finishes.
+__device__ __forceinline__ void grid_barrier(DevCtrl *c) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile uint32_t *vgen = &c->bar_gen;
+    volatile uint32_t *vab = &c->bar_abort;
+    const uint32_t gen = *vgen;
+    __threadfence();
+    const uint32_t arrived = atomicAdd(&c->bar_count, 1u);
+    if (arrived == gridDim.x - 1 + c->bar_extra) {
+      atomicExch(&c->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+    } else if (!*vab) {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (*vab) break;
+        if (clock64() - t0 > kBarrierCycles) {
+          atomicOr(&c->status, kFlagTimeout);
+          atomicExch(&c->bar_abort, 1u);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// All I sweeps in one persistent cooperative launch (no free bodies): a grid-stride
+// loop over particles per sweep, a grid barrier between sweeps.  Same per-particle
+// arithmetic as k_pja, so results are bit-identical.
+__global__ void __launch_bounds__(1024) k_pja_fused(StepArgs a, uint32_t iters) {
+  const Tape none{};
+  for (uint32_t it = 0; it < iters; ++it) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x)
+      pja_particle<false, true>(a, i, (int)(it & 1), none, (int)it);
+    if (it + 1 < iters) grid_barrier(a.ctrl);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -851,7 +954,7 @@ static inline cudaError_t mark(cudaEvent_t *ev, int k, cudaStream_t st) {
 
 uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls) {
   uint32_t k = 6;  // key, scan x3, wrench_sum, body_update
-  if (a.n) k += 5 + ls.iters;  // scatter, reorder, contacts, pja x I, integrate
+  if (a.n) k += 5 + ((ls.fused_grid && !a.F) ? 1 : ls.iters);  // scatter, reorder, contacts, pja, integrate
   if (a.n_chunks) k += 1;
   if (a.F) k += 1 + ls.iters;  // free_prep, free_update x I
   return k;
@@ -881,6 +984,18 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
     if ((e = cudaMemsetAsync(tp->blamh, 0, sizeof(float) * 3 * (size_t)a.Kb * a.n, st)) != cudaSuccess) return e;
   }
   const Tape none{};
+  if (!tp && ls.fused_grid && !a.F && a.n) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ls.fused_grid);
+    cfg.blockDim = dim3(ls.fused_block);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if ((e = cudaLaunchKernelEx(&cfg, k_pja_fused, a, ls.iters)) != cudaSuccess) return e;
+  } else
   for (uint32_t it = 0; it < ls.iters; ++it) {
     if (a.n) {
       if (tp)
@@ -901,6 +1016,15 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
   k_body_update<<<1, 256, 0, st>>>(a);
   if ((e = mark(ev, 4, st)) != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+int fused_pja_blocks_per_sm(int block) {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pja_fused, block, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return per;
 }
 
 cudaError_t enqueue_export_contacts(const StepArgs &a, uint32_t *rows, float *geom, float *lam, float *bgeom,

@@ -58,7 +58,7 @@ class GGParams(C.Structure):
                 ("hash_factor", C.c_uint32), ("hash_size", C.c_uint32), ("max_contacts", C.c_uint32),
                 ("max_body_contacts", C.c_uint32), ("max_bodies", C.c_uint32), ("density", C.c_float),
                 ("tuning", C.c_uint32), ("wrench_history", C.c_uint32), ("max_free_bodies", C.c_uint32),
-                ("free_contact_capacity", C.c_uint32)]
+                ("free_contact_capacity", C.c_uint32), ("barrier_test_phantoms", C.c_uint32)]
 
 
 class GGBody(C.Structure):
@@ -122,7 +122,8 @@ def _stream(stream):
     return C.c_void_p(int(stream))
 
 
-def make_params(p, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0, max_free_bodies=0) -> GGParams:
+def make_params(p, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0, max_free_bodies=0,
+                barrier_test_phantoms=0) -> GGParams:
     q = GGParams()
     q.struct_size = C.sizeof(GGParams)
     q.dt = p.dt
@@ -142,6 +143,7 @@ def make_params(p, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0, max_
     q.wrench_history = wrench_history
     q.max_free_bodies = max_free_bodies
     q.free_contact_capacity = 0
+    q.barrier_test_phantoms = barrier_test_phantoms
     return q
 
 
@@ -168,11 +170,12 @@ class Sim:
     """One libgg simulation (single environment, or batched when env_offsets is given)."""
 
     def __init__(self, pos_r, vel=None, mass=None, params=None, env_offsets=None, tuning=0, wrench_history=1,
-                 max_bodies=8, hash_factor=0, max_free_bodies=0):
+                 max_bodies=8, hash_factor=0, max_free_bodies=0, barrier_test_phantoms=0):
         L = load()
         self._L = L
         self.params = params
-        self.gp = make_params(params, tuning, wrench_history, max_bodies, hash_factor, max_free_bodies)
+        self.gp = make_params(params, tuning, wrench_history, max_bodies, hash_factor, max_free_bodies,
+                              barrier_test_phantoms)
         n = int(pos_r.shape[0])
         self.n = n
         pp, dev = _ptr(pos_r)

@@ -94,8 +94,11 @@ def test_adjoint_invariant_to_checkpoint_interval(torch, scene):
         assert np.array_equal(got[1], ref[1]) and got[2] == ref[2]
 
 
-def test_adjoint_matches_gpu_finite_differences(torch, scene):
-    """Central differences of the GPU's own FP32 forward on the largest components."""
+def test_adjoint_matches_gpu_directional_derivative(torch, scene):
+    """Central difference of the GPU's own FP32 forward along the gradient direction
+    and along a random direction: g . d must match (L(tw + h d) - L(tw - h d)) / 2h.
+    (Single components are too small against the FP32 rounding of the final state;
+    along a whole direction the signal adds up.)"""
     from paper_2306_01369_gb300.autograd import rollout, scoop_mass
     L, g_tw, _ = gpu_grad(torch, scene)
     dev = torch.device("cuda", 0)
@@ -108,15 +111,15 @@ def test_adjoint_matches_gpu_finite_differences(torch, scene):
             return float(scoop_mass(pos.double(), mass.double(), pose.double(), scene.bodies[1].shape12(),
                                     scene.info["eps"]))
 
-    tw0 = scene.twist[1].astype(F32)
-    gmax = np.abs(g_tw).max()
-    idx = [i for i in np.argsort(-np.abs(g_tw).ravel())[:4] if abs(g_tw.ravel()[i]) >= 0.1 * gmax]
-    assert idx
-    for flat in idx:
-        k, c = divmod(int(flat), 6)
-        h = 1e-3 if c < 3 else 1e-2
-        tp, tm = tw0.copy(), tw0.copy()
-        tp[k, c] += h
-        tm[k, c] -= h
-        g = (loss(tp) - loss(tm)) / (float(tp[k, c]) - float(tm[k, c]))
-        assert abs(g - g_tw[k, c]) < 0.1 * abs(g_tw[k, c]), (k, c, g, g_tw[k, c])
+    tw0 = scene.twist[1].astype(np.float64)
+    rng = np.random.default_rng(4)
+    for d in (g_tw / np.linalg.norm(g_tw), rng.normal(size=g_tw.shape)):
+        d = d / np.linalg.norm(d)
+        h = 1e-3
+        tp = (tw0 + h * d).astype(F32)
+        tm = (tw0 - h * d).astype(F32)
+        step = (tp.astype(np.float64) - tm.astype(np.float64))
+        want = float((g_tw * step).sum())        # first-order change for the step actually taken
+        got = loss(tp) - loss(tm)
+        scale = np.linalg.norm(g_tw) * 2 * h
+        assert abs(got - want) < 0.05 * scale, (got, want, scale)

@@ -260,6 +260,34 @@ def test_results_invariant_to_launch_shape_and_table_size(gg):
             sim.close()
 
 
+def test_autotuner_picks_a_set_and_changes_nothing(gg):
+    sc = squeezed_box(4096)
+    ref = gg.Sim.from_scene(sc, tuning=1)
+    ref.step(8)
+    auto = gg.Sim.from_scene(sc, tuning=0)
+    auto.step(8)
+    assert 1 <= auto.tuning_selected <= gg.load().gg_tuning_count()
+    assert np.array_equal(auto.pos(), ref.pos()) and np.array_equal(auto.vel(), ref.vel())
+
+
+def test_grid_barrier_wait_runs_out_and_reports(gg):
+    """The fused sweep's grid barrier waits are bounded: with a phantom participant
+    (a flag that nothing sets) every wait runs out, the step reports
+    GG_ERR_DEVICE_TIMEOUT, and the GPU context stays usable."""
+    sc = squeezed_box(2048)
+    fused = [5, 6]   # tuning sets with the fused cooperative sweep
+    sim = gg.Sim(sc.pos_r, sc.vel, sc.mass, sc.params, tuning=fused[0], barrier_test_phantoms=1)
+    sim.set_bodies(sc.bodies)
+    sim.step(1)
+    with pytest.raises(gg.GGError) as e:
+        sim.sync()
+    assert e.value.status == gg.ERR_DEVICE_TIMEOUT
+    sim.close()
+    ok = gg.Sim.from_scene(sc, tuning=fused[0])
+    ok.step(2)
+    ok.sync()
+
+
 def test_run_to_run_deterministic(gg):
     sc = squeezed_box(4096)
     outs = []
