@@ -249,6 +249,108 @@ def run_reference(args):
     return 0
 
 
+def _timed_steps(sim, steps, stream, torch):
+    """Device ms of `steps` steps (events on the library's stream)."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=120.0):
+    """The other figures of the headline metric, one GPU: batched env-steps/s against
+    a loop of the plain single-environment path, backward/forward time of the
+    differentiable workload, and the 1M-sphere excavation throughput."""
+    from paper_2306_01369_gb300 import gg, scenes
+    from paper_2306_01369_gb300.autograd import rollout, scoop_mass
+    out = {}
+    t_start = time.perf_counter()
+    # batched: 256 environments, 8k-64k spheres each
+    sc = scenes.batched_beds(n_envs=256, n_steps=steps_batched + 10)
+    sim = gg.Sim.from_scene(sc)
+    sim.step(3, stream=stream)
+    ms = _timed_steps(sim, steps_batched, stream, torch)
+    sim.sync(stream)
+    E = len(sc.env_offsets) - 1
+    batched = E * steps_batched / (ms * 1e-3)
+    kps = sim.kernels_per_step
+    sim.close()
+    # the same environments, each stepped alone (a sample of 16, scaled to all 256)
+    per_env_ms, sample = [], list(range(0, E, E // 16))[:16]
+    for e in sample:
+        o0, o1 = int(sc.env_offsets[e]), int(sc.env_offsets[e + 1])
+        b0, b1 = int(sc.body_offsets[e]), int(sc.body_offsets[e + 1])
+        es = scenes.Scene("env", sc.pos_r[o0:o1], sc.vel[o0:o1], sc.mass[o0:o1], sc.bodies[b0:b1], sc.params,
+                          sc.n_steps, twist={gb - b0: t for gb, t in sc.twist.items() if b0 <= gb < b1})
+        one = gg.Sim.from_scene(es)
+        one.step(3, stream=stream)
+        per_env_ms.append(_timed_steps(one, 20, stream, torch) / 20)
+        one.close()
+    loop = 1.0 / (statistics.mean(per_env_ms) * 1e-3)
+    out["batched"] = {"workload": f"{E} environments, {sc.n} spheres (8k-64k each), I=20", "env_steps_per_s": batched,
+                      "particle_steps_per_s": sc.n * steps_batched / (ms * 1e-3),
+                      "loop_of_plain_env_steps_per_s": loop, "speedup_vs_loop": batched / loop,
+                      "timed_steps": steps_batched, "kernels_per_step": kps,
+                      "loop_sample": f"{len(sample)} of {E} environments stepped alone, 20 steps each"}
+    # differentiable: 32,768 spheres, 200 steps, checkpoint every 20
+    if time.perf_counter() - t_start < seconds_cap:
+        ds = scenes.diff_scene(n=32768, n_steps=200)
+        settle = gg.Sim(ds.pos_r, ds.vel, ds.mass, ds.params)
+        settle.set_bodies(ds.bodies)
+        settle.step(600, stream=stream)
+        pos, vel = settle.pos(), settle.vel()
+        settle.close()
+        s32 = scenes.Scene("diff32k", pos, vel, ds.mass, ds.bodies, ds.params, 200, twist=ds.twist, info=ds.info)
+        plain = gg.Sim.from_scene(s32)
+        plain.step(2, stream=stream)
+        plain.set_particles(pos, vel, stream=stream)
+        fwd_ms = _timed_steps(plain, 200, stream, torch)
+        plain.close()
+        mass = torch.tensor(ds.mass, device=dev)
+        for _ in range(2):   # the first pass is untimed: torch JIT-compiles the loss kernels on first use
+            tw = torch.tensor(ds.twist[1], device=dev, requires_grad=True)
+            mu = torch.tensor(float(ds.params.mu), device=dev, requires_grad=True)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            p, v, pose = rollout(tw, mu, s32, 1, 20)
+            L = scoop_mass(p, mass, pose, ds.bodies[1].shape12(), ds.info["eps"])
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            L.backward()
+            torch.cuda.synchronize(dev)
+            t2 = time.perf_counter()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        tw = torch.tensor(ds.twist[1], device=dev, requires_grad=True)
+        mu = torch.tensor(float(ds.params.mu), device=dev, requires_grad=True)
+        p, v, pose = rollout(tw, mu, s32, 1, 20)
+        L = scoop_mass(p, mass, pose, ds.bodies[1].shape12(), ds.info["eps"])
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        L.backward()
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+        out["differentiable"] = {"workload": "32,768 spheres + scoop, 200 steps, I=20, checkpoint every 20",
+                                 "forward_ms": fwd_ms, "taped_forward_ms": 1e3 * (t1 - t0),
+                                 "backward_ms": 1e3 * (t2 - t1), "bwd_over_fwd": 1e3 * (t2 - t1) / fwd_ms,
+                                 "grad_norm_twist": float(tw.grad.norm()), "dL_dmu": float(mu.grad)}
+    # excavation: 1,048,576 spheres, scoop, two free cubes, I = 30
+    if time.perf_counter() - t_start < seconds_cap:
+        ex = scenes.excavation(n=1048576, n_steps=steps_exc + 20)
+        sim = gg.Sim.from_scene(ex, wrench_history=steps_exc)
+        sim.step(10, stream=stream)
+        ms = _timed_steps(sim, steps_exc, stream, torch)
+        sim.sync(stream)
+        st = sim.stats()
+        out["excavation"] = {"workload": "1,048,576 spheres, scoop + 2 free cubes + container, I=30",
+                             "particle_steps_per_s": ex.n * steps_exc / (ms * 1e-3), "ms_per_step": ms / steps_exc,
+                             "timed_steps": [10, 10 + steps_exc], "n_pp_last": st["n_pp"], "n_body_last": st["n_body"]}
+        sim.close()
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -339,6 +441,9 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(sc, sim.pos(), sim.vel(), seconds=args.cpu_seconds)
+    xtra = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        xtra = extras(torch, dev, stream)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -352,7 +457,8 @@ def run_gpu(args):
                 "gpu_launches": sim.kernels_per_step * args.steps, "clocks": clk,
                 "stage_ms_last_step": sim.stage_ms(),
                 "contacts_last_step": {"n_pp": stats["n_pp"], "n_body": stats["n_body"],
-                                       "mean_pp_per_particle": stats["n_pp"] / sc.n}}
+                                       "mean_pp_per_particle": stats["n_pp"] / sc.n},
+                "extras": xtra}
         print(json.dumps(line), flush=True)
     sim.close()
     if world > 1:
@@ -371,6 +477,7 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched / adjoint / excavation figures")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -437,6 +437,7 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
     if (nh == 0) nh = 1;
     E.hbase = (uint32_t)hb;
     E.nh = (uint32_t)nh;
+    E.nh_magic = gg::remainder_magic(E.nh);
     hb += nh;
     if (hb > 0xF0000000ull) return bail(fail(s, GG_ERR_INVALID_ARG, "hash tables exceed 2^32 buckets"));
     E.nbodies = 0;

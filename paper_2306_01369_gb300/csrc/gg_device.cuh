@@ -34,7 +34,17 @@ struct DevEnv {
   float inv_cell;         // float(1 / c)
   uint32_t nbodies;       // active bodies (slots [e * maxb, e * maxb + nbodies))
   uint32_t chunk0, nchunks;  // wrench partial chunks of this environment
+  uint64_t nh_magic;      // floor((2^64 - 1) / nh) + 1, for the exact remainder below
 };
+
+// x mod d without a division: Lemire, Kaser & Kurz, "Faster remainder by direct
+// computation" (Software: Practice and Experience, 2019); exact for all 32-bit x and d
+// >= 1 with magic = floor((2^64 - 1) / d) + 1 (wrapping to 0 for d = 1).
+__host__ __device__ __forceinline__ uint64_t remainder_magic(uint32_t d) { return ~0ull / d + 1ull; }
+__device__ __forceinline__ uint32_t fast_mod(uint32_t x, uint64_t magic, uint32_t d) {
+  const uint64_t low = magic * (uint64_t)x;
+  return (uint32_t)__umul64hi(low, (uint64_t)d);
+}
 
 struct DevBody {
   uint32_t kind, is_free;
@@ -130,6 +140,14 @@ __device__ __forceinline__ uint32_t hash_cell(int32_t k0, int32_t k1, int32_t k2
   uint32_t b = ((uint32_t)k1 - kHashQ) * kHashP2;
   uint32_t c = ((uint32_t)k2 - kHashQ) * kHashP3;
   return (a ^ b ^ c) % nh;
+}
+
+// Eq. 6 with the exact fast remainder; same value as hash_cell.
+__device__ __forceinline__ uint32_t hash_cell_fm(int32_t k0, int32_t k1, int32_t k2, const DevEnv &E) {
+  const uint32_t a = ((uint32_t)k0 - kHashQ) * kHashP1;
+  const uint32_t b = ((uint32_t)k1 - kHashQ) * kHashP2;
+  const uint32_t c = ((uint32_t)k2 - kHashQ) * kHashP3;
+  return fast_mod(a ^ b ^ c, E.nh_magic, E.nh);
 }
 
 // squared distance ((dx dx + dy dy) + dz dz) and the sum of radii squared

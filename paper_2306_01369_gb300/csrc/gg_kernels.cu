@@ -93,7 +93,7 @@ __global__ void k_key(StepArgs a) {
     float4 p = a.pos_id[i];
     const DevEnv &E = a.envs[a.env_of[i]];
     int32_t k0 = cell_of(p.x, E.inv_cell), k1 = cell_of(p.y, E.inv_cell), k2 = cell_of(p.z, E.inv_cell);
-    uint32_t key = E.hbase + hash_cell(k0, k1, k2, E.nh);
+    uint32_t key = E.hbase + hash_cell_fm(k0, k1, k2, E);
     a.key_id[i] = key;
     atomicAdd(&a.cnt[key], 1u);
   }
@@ -255,12 +255,20 @@ __global__ void __launch_bounds__(256) k_contacts(StepArgs a) {
     uint32_t fid[kMaxK], fsl[kMaxK];
     const uint32_t K = a.K;
     bool ovf = false;
+    // Eq. 6 terms of the three cells along each axis, combined 27 ways below
+    uint32_t hx[3], hy[3], hz[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      hx[q] = ((uint32_t)(k0 + q - 1) - kHashQ) * kHashP1;
+      hy[q] = ((uint32_t)(k1 + q - 1) - kHashQ) * kHashP2;
+      hz[q] = ((uint32_t)(k2 + q - 1) - kHashQ) * kHashP3;
+    }
     for (int dz = -1; dz <= 1; ++dz) {
       // the nine bucket ranges of this plane are loaded together, then walked
       uint32_t r0[9], r1[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
-        const uint32_t h = E.hbase + hash_cell(k0 + (q % 3) - 1, k1 + (q / 3) - 1, k2 + dz, E.nh);
+        const uint32_t h = E.hbase + fast_mod(hx[q % 3] ^ hy[q / 3] ^ hz[dz + 1], E.nh_magic, E.nh);
         r0[q] = a.start[h];
         r1[q] = a.start[h + 1];
       }

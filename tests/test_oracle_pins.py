@@ -485,3 +485,18 @@ def test_free_box_rests_on_plane(orc):
     assert s.stats.n_corner == 4
     assert np.abs(s.body_twist(1)).max() < 1e-9 * g
     assert abs(s.wrench[0, 2] + float(F32(M)) * g) < 1e-9 * M * g
+
+
+def test_fast_remainder_identity():
+    """The step kernels compute Eq. 6's `mod n_h` without a division (Lemire, Kaser &
+    Kurz 2019): low = magic * x mod 2^64, result = high 64 bits of low * d, with
+    magic = floor((2^64 - 1) / d) + 1.  The identity is exact for all 32-bit x, d."""
+    rng = np.random.default_rng(11)
+    M64 = (1 << 64) - 1
+    for d in [1, 2, 3, 7, 97, 4096, 524288, 1000003, 14_000_000, (1 << 31) + 11, (1 << 32) - 1] + \
+            [int(v) for v in rng.integers(1, 1 << 32, 200)]:
+        magic = (M64 // d + 1) & M64
+        for x in [0, 1, d - 1, d, (1 << 32) - 1] + [int(v) for v in rng.integers(0, 1 << 32, 50)]:
+            x &= (1 << 32) - 1
+            low = (magic * x) & M64
+            assert (low * d) >> 64 == x % d, (x, d)
