@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_begin(StepArgs a, AdjArgs d
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.n) return;
   const size_t n = a.n, KN = (size_t)a.K * n, KbN = (size_t)a.Kb * n;
-  const uint32_t id = a.sid[s];
+  const uint32_t id = s;
   const float4 xb = d.xbar[id], vb = d.vbar[id];
   d.xbar_s[s] = xb;
   const float4 ub = make_float4(vb.x + a.dt * xb.x, vb.y + a.dt * xb.y, vb.z + a.dt * xb.z, 0.f);
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_iter(StepArgs a, AdjArgs d,
   if (i < a.n) {
     const size_t n = a.n, KN = (size_t)a.K * n, KbN = (size_t)a.Kb * n;
     const float4 Un = d.Ubar[cur][i];
-    const float invm = a.sbase[i].w;
+    const float invm = a.vel_id[i].w;
     const float4 Ui = d.tp.Uh[(size_t)s * n + i];
     const float *lh = d.tp.lamh + (size_t)s * 3 * KN;
     const float *blh = d.tp.blamh + (size_t)s * 3 * KbN;
@@ -280,14 +280,14 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_geom(StepArgs a, AdjArgs d)
   float part[kPart] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (i < a.n) {
     const size_t n = a.n, KN = (size_t)a.K * n, KbN = (size_t)a.Kb * n;
-    const float4 pi = a.spos[i];
+    const float4 pi = a.pos_id[i];
     float3 X = f3(d.xbar_s[i]);
     const uint32_t cc = a.ccount[i];
     const uint32_t npp = cc & 0xffu, nbc = (cc >> 8) & 0xffu;
     for (uint32_t c = 0; c < npp; ++c) {
       const size_t o = (size_t)c * n + i;
       const uint32_t j = a.cj[o];
-      const float dist = pi.w + a.spos[j].w - a.cn[o].w;
+      const float dist = pi.w + a.pos_id[j].w - a.cn[o].w;
       const size_t ot = (size_t)d.twin[o] * n + j;
       X = add(X, sub(pair_geom_grad(d, a, o, KN, dist), pair_geom_grad(d, a, ot, KN, dist)));
     }
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_geom(StepArgs a, AdjArgs d)
         part[5] += rb.z;
       }
     }
-    const uint32_t id = a.sid[i];
+    const uint32_t id = i;
     d.xbar[id] = make_float4(X.x, X.y, X.z, 0.f);
     const float4 b = d.basebar[i];
     d.vbar[id] = make_float4(b.x, b.y, b.z, 0.f);

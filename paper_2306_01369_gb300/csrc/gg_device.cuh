@@ -26,7 +26,7 @@ constexpr int kMaxKb = 8;   // particle-body capacity limit
 constexpr int kScanItems = 16;          // counts per thread in the bucket scan
 constexpr int kScanThreads = 256;
 constexpr int kScanTile = kScanItems * kScanThreads;
-constexpr int kWrenchChunk = 1024;      // slots per wrench partial
+constexpr int kWrenchChunk = 1024;      // particles per wrench partial
 
 struct DevEnv {
   uint32_t off, n;        // particle range [off, off + n)
@@ -96,13 +96,12 @@ struct StepArgs {
   uint32_t *cnt;    // nh_pad entries, zero between steps
   uint32_t *start;  // nh_pad + 1
   uint32_t *bsum;   // scan block sums
-  // slot order
-  uint32_t *sid_tmp, *sid, *slot_of;
-  float4 *spos;     // x, y, z, r
-  float4 *sbase;    // v + dt g, 1/m
+  // sorted slots: particle id of each slot, ascending (bucket, id)
+  uint32_t *sid_tmp, *sid;
+  // per particle (id order)
   float4 *U[2];     // velocity estimate, w = n_contacts / m
   uint32_t *ccount; // pp | body << 8
-  uint32_t *cj;     // [K][n] partner slot
+  uint32_t *cj;     // [K][n] partner id
   float4 *cn;       // [K][n] normal (partner -> particle), psi
   float *clam;      // [3][K][n]
   uint32_t *bj;     // [Kb][n] global body index
@@ -120,7 +119,7 @@ struct StepArgs {
   uint32_t F, Lcap;       // free-body slots, contact-list capacity per free body
   uint32_t *ncb;          // [n_envs * maxb] contacts per body this step
   uint32_t *fcount;       // [F] particle contacts of each free body
-  uint32_t *flist;        // [F][Lcap] (slot * Kb + k), sorted ascending
+  uint32_t *flist;        // [F][Lcap] (particle * Kb + k), sorted ascending
   uint32_t *fgb;          // [F] global body index of each free slot (or ~0u)
   CornerContact *fcc;     // [F][8 * maxb]
 };
@@ -291,12 +290,12 @@ struct Tape {
   float *blamh;  // [I + 1][3][Kb][n] body-contact impulses
 };
 
-// Adjoint state of one reversed step (slot order unless noted).
+// Adjoint state of one reversed step (particle order unless noted).
 struct AdjArgs {
   Tape tp;
   uint32_t I;              // sweeps per step
   uint32_t tool;           // global body index whose twists are differentiated (~0u: none)
-  uint32_t nblk;           // blocks of the per-slot adjoint kernels
+  uint32_t nblk;           // blocks of the per-particle adjoint kernels
   uint32_t *twin;          // [K][n] position of contact (j -> i) in j's list
   float4 *Ubar[2];         // adjoint of U^{s+1} / U^s
   float *ubar;             // [3][K][n] adjoint of each pair contact's relative velocity
@@ -304,7 +303,7 @@ struct AdjArgs {
   float *psibar, *nbar;    // [K][n], [3][K][n]
   float *bpsibar, *bnbar, *bxcbar;  // [Kb][n], [3][Kb][n], [3][Kb][n]
   float4 *basebar;         // adjoint of v + dt g
-  float4 *xbar_s;          // adjoint of x_{k+1} in slot order
+  float4 *xbar_s;          // adjoint of x_{k+1} (working copy)
   float4 *xbar, *vbar;     // id order: in dL/dx_{k+1}, dL/dv_{k+1}; out dL/dx_k, dL/dv_k
   float *part;             // [I + 1][nblk][10] fixed-order partial sums
   float *pose_bar;         // [6] adjoint of the tool pose (p, rotation), updated per step

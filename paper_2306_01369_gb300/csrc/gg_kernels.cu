@@ -5,13 +5,15 @@
 //   k_key            bucket of every particle (Eq. 6), bucket histogram, body prep
 //   k_scan_*         exclusive scan of the histogram -> bucket start table
 //   k_scatter        counting-sort scatter (returns the histogram to zero)
-//   k_reorder        stable order inside each bucket (ascending id) + gather of
-//                    positions / velocities into sorted slots
+//   k_reorder        stable order inside each bucket (ascending id)
 //   k_contacts       27-cell bucket walk, sphere test, SDF tests (Sec. II-B, II-C)
 //   k_free_prep      (free bodies) sorted contact lists, box-corner contacts
 //   k_pja  x I       projected-Jacobi sweeps (Alg. 1), one launch per iteration,
 //   k_free_update    each followed (free bodies) by the bodies' twist update
-//   k_integrate      symplectic Euler (Eq. 4-5), back to particle-id order
+//   k_integrate      symplectic Euler (Eq. 4-5), in place
+// Contacts, sweeps and integration run over particles in the caller's order (their
+// storage order); the bucket table is only walked, so spatially ordered inputs keep
+// neighbours' data in nearby cache lines.
 //   k_wrench_partial per-body impulse sums over fixed slot chunks (deterministic)
 //   k_wrench_sum     per-body sums over chunks into the wrench readback ring
 //   k_body_update    kinematic body poses, step counter
@@ -60,6 +62,11 @@ __device__ __forceinline__ void block_sum6(float v[6]) {
 }
 
 __device__ __forceinline__ void flag(DevCtrl *c, uint32_t f) { atomicOr(&c->status, f); }
+
+// v + dt g (the velocity before contact impulses), with 1/m in w
+__device__ __forceinline__ float4 base_velocity(const StepArgs &a, float4 v) {
+  return make_float4(v.x + a.dt * a.g[0], v.y + a.dt * a.g[1], v.z + a.dt * a.g[2], v.w);
+}
 
 // ---------------------------------------------------------------------------
 // 1. bucket keys + histogram; body pose/twist for this step
@@ -230,12 +237,7 @@ __global__ void k_reorder(StepArgs a) {
   const uint32_t b0 = a.start[key], b1 = a.start[key + 1];
   uint32_t rank = 0;
   for (uint32_t t = b0; t < b1; ++t) rank += (a.sid_tmp[t] < id) ? 1u : 0u;
-  const uint32_t dst = b0 + rank;
-  a.sid[dst] = id;
-  a.slot_of[id] = dst;
-  a.spos[dst] = a.pos_id[id];
-  float4 v = a.vel_id[id];
-  a.sbase[dst] = make_float4(v.x + a.dt * a.g[0], v.y + a.dt * a.g[1], v.z + a.dt * a.g[2], v.w);
+  a.sid[b0 + rank] = id;
 }
 
 // ---------------------------------------------------------------------------
@@ -247,12 +249,11 @@ __global__ void __launch_bounds__(256) k_contacts(StepArgs a) {
   uint32_t npp = 0, nbc = 0;
   float psi_max = 0.f;
   if (i < a.n) {
-    const float4 pi = a.spos[i];
-    const uint32_t idi = a.sid[i];
-    const uint32_t e = a.env_of[idi];
+    const float4 pi = a.pos_id[i];
+    const uint32_t e = a.env_of[i];
     const DevEnv E = a.envs[e];
     const int32_t k0 = cell_of(pi.x, E.inv_cell), k1 = cell_of(pi.y, E.inv_cell), k2 = cell_of(pi.z, E.inv_cell);
-    uint32_t fid[kMaxK], fsl[kMaxK];
+    uint32_t fid[kMaxK];
     const uint32_t K = a.K;
     bool ovf = false;
     // Eq. 6 terms of the three cells along each axis, combined 27 ways below
@@ -274,47 +275,41 @@ __global__ void __launch_bounds__(256) k_contacts(StepArgs a) {
       }
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
-        {
-          const uint32_t t1 = r1[q];
-          for (uint32_t t = r0[q]; t < t1; ++t) {
-            if (t == i) continue;
-            float d2;
-            float3 d;
-            if (!sphere_hit(pi, a.spos[t], &d2, &d)) continue;
-            const uint32_t jid = a.sid[t];
-            // insert by ascending id; a bucket reached twice yields the same id: skip it
-            uint32_t p = 0;
-            while (p < npp && fid[p] < jid) ++p;
-            if (p < npp && fid[p] == jid) continue;
-            if (npp == K) {
-              ovf = true;
-              if (p == K) continue;
-            } else {
-              ++npp;
-            }
-            for (uint32_t q = npp - 1; q > p; --q) {
-              fid[q] = fid[q - 1];
-              fsl[q] = fsl[q - 1];
-            }
-            fid[p] = jid;
-            fsl[p] = t;
+        const uint32_t t1 = r1[q];
+        for (uint32_t t = r0[q]; t < t1; ++t) {
+          const uint32_t jid = a.sid[t];
+          if (jid == i) continue;
+          float d2;
+          float3 d;
+          if (!sphere_hit(pi, a.pos_id[jid], &d2, &d)) continue;
+          // insert by ascending id; a bucket reached twice yields the same id: skip it
+          uint32_t p = 0;
+          while (p < npp && fid[p] < jid) ++p;
+          if (p < npp && fid[p] == jid) continue;
+          if (npp == K) {
+            ovf = true;
+            if (p == K) continue;
+          } else {
+            ++npp;
           }
+          for (uint32_t q2 = npp - 1; q2 > p; --q2) fid[q2] = fid[q2 - 1];
+          fid[p] = jid;
         }
       }
     }
     const size_t n = a.n;
     for (uint32_t c = 0; c < npp; ++c) {
-      const uint32_t j = fsl[c];
+      const uint32_t j = fid[c];
       float d2;
       float3 d;
-      const float4 pj = a.spos[j];
+      const float4 pj = a.pos_id[j];
       sphere_hit(pi, pj, &d2, &d);
       const float dist = __fsqrt_rn(d2);
       float3 nn;
       if (dist > 0.f) {
         nn = make_float3(__fdiv_rn(d.x, dist), __fdiv_rn(d.y, dist), __fdiv_rn(d.z, dist));
       } else {
-        nn = make_float3(0.f, 0.f, idi > fid[c] ? 1.f : -1.f);
+        nn = make_float3(0.f, 0.f, i > j ? 1.f : -1.f);
       }
       const float psi = __fsub_rn(__fadd_rn(pi.w, pj.w), dist);
       psi_max = fmaxf(psi_max, psi);
@@ -361,7 +356,7 @@ __global__ void __launch_bounds__(256) k_contacts(StepArgs a) {
     }
     if (ovf) flag(a.ctrl, kFlagPPOverflow);
     a.ccount[i] = npp | (nbc << 8);
-    const float4 sb = a.sbase[i];
+    const float4 sb = base_velocity(a, a.vel_id[i]);
     a.U[0][i] = make_float4(sb.x, sb.y, sb.z, (float)(npp + nbc) * sb.w);
   }
   // per-step statistics (integer atomics: order-independent)
@@ -402,7 +397,7 @@ __device__ __forceinline__ void pja_particle(const StepArgs &a, uint32_t i, int 
   const uint32_t cc = a.ccount[i];
   const uint32_t npp = cc & 0xffu, nbc = (cc >> 8) & 0xffu;
   const float4 ui = LDCG ? __ldcg(Uin + i) : Uin[i];
-  const float4 base = a.sbase[i];
+  const float4 base = base_velocity(a, a.vel_id[i]);
   float sx = 0.f, sy = 0.f, sz = 0.f;
   const size_t KN = (size_t)a.K * n;
   const float mu = a.mu, ab = a.ab;
@@ -713,14 +708,13 @@ __global__ void k_integrate(StepArgs a, int s) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const float4 u = a.U[s][i];
-  const float4 p = a.spos[i];
-  const float4 b = a.sbase[i];
-  const uint32_t id = a.sid[i];
+  const float4 p = a.pos_id[i];
+  const float invm = a.vel_id[i].w;
   const float x = p.x + a.dt * u.x, y = p.y + a.dt * u.y, z = p.z + a.dt * u.z;
   if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(u.x) && isfinite(u.y) && isfinite(u.z)))
     flag(a.ctrl, kFlagNonFinite);
-  a.pos_id[id] = make_float4(x, y, z, p.w);
-  a.vel_id[id] = make_float4(u.x, u.y, u.z, b.w);
+  a.pos_id[i] = make_float4(x, y, z, p.w);
+  a.vel_id[i] = make_float4(u.x, u.y, u.z, invm);
 }
 
 // ---------------------------------------------------------------------------
@@ -860,7 +854,7 @@ __global__ void __launch_bounds__(256) k_body_update(StepArgs a) {
 __global__ void k_export_contacts(StepArgs a, uint32_t *rows, float *geom, float *lam, float *bgeom, float *blam) {
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.n) return;
-  const uint32_t id = a.sid[s];
+  const uint32_t id = s;
   const uint32_t K = a.K, Kb = a.Kb, W = 2 + K + Kb;
   const size_t n = a.n;
   const uint32_t cc = a.ccount[s];
@@ -869,7 +863,7 @@ __global__ void k_export_contacts(StepArgs a, uint32_t *rows, float *geom, float
     uint32_t *r = rows + (size_t)id * W;
     r[0] = npp;
     r[1] = nbc;
-    for (uint32_t c = 0; c < K; ++c) r[2 + c] = c < npp ? a.sid[a.cj[(size_t)c * n + s]] : 0xffffffffu;
+    for (uint32_t c = 0; c < K; ++c) r[2 + c] = c < npp ? a.cj[(size_t)c * n + s] : 0xffffffffu;
     for (uint32_t c = 0; c < Kb; ++c) r[2 + K + c] = c < nbc ? a.bj[(size_t)c * n + s] % a.maxb : 0xffffffffu;
   }
   for (uint32_t c = 0; c < K; ++c) {
