@@ -26,7 +26,7 @@ using gg::StepArgs;
 namespace {
 
 // Launch-shape sets accepted by gg_params.tuning (index k-1).
-// (iters, per-launch block, fused block; the fused grid is sized per device at create)
+// (iters, per-launch sweep block, fused sweep block, fused grid)
 const gg::LaunchShape kShapes[] = {{0, 256, 0, 0}, {0, 128, 0, 0}, {0, 512, 0, 0}, {0, 64, 0, 0},
                                    {0, 256, 1024, 0}, {0, 256, 512, 0}};
 constexpr uint32_t kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);

@@ -307,7 +307,8 @@ __global__ void __launch_bounds__(256) k_contacts(StepArgs a) {
       const float dist = __fsqrt_rn(d2);
       float3 nn;
       if (dist > 0.f) {
-        nn = make_float3(__fdiv_rn(d.x, dist), __fdiv_rn(d.y, dist), __fdiv_rn(d.z, dist));
+        const float id = __frcp_rn(dist);
+        nn = make_float3(d.x * id, d.y * id, d.z * id);
       } else {
         nn = make_float3(0.f, 0.f, i > j ? 1.f : -1.f);
       }
