@@ -147,10 +147,20 @@ class ClockSampler:
 
 def pja_bytes(n: int, n_pp: int, n_body: int) -> int:
     """Algorithmic DRAM bytes of one k_pja launch (each array read or written once):
-    per particle: velocity estimate in 16 + base velocity 16 + counts 4 + estimate out 16;
+    per particle: velocity estimate in 16 + velocity (base) 16 + counts 4 + estimate out 16;
     per particle-particle contact: partner 4 + normal/psi 16 + impulse in 12 + out 12;
     per particle-body contact: body 4 + normal/psi 16 + contact point 16 + impulse 24."""
     return 52 * n + 44 * n_pp + 60 * n_body
+
+
+def contacts_bytes(n: int, n_pp: int, n_body: int, n_h: int) -> int:
+    """Algorithmic DRAM bytes of one k_contacts launch: per particle position 16 (read
+    once, though the kernel reads its own row from the id-ordered copy and candidates
+    from the bucket-ordered one), environment 4, velocity 16, counts out 4, first
+    velocity estimate out 16, its id in the sorted slot list 4; the bucket table 4 per
+    bucket; per pair contact partner 4 + normal/psi 16 + zeroed impulse 12; per body
+    contact body 4 + normal/psi 16 + contact point 16 + zeroed impulse 12."""
+    return 60 * n + 4 * n_h + 32 * n_pp + 48 * n_body
 
 
 def measured_peaks():
@@ -162,10 +172,10 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def profile_traffic(kernel_digest: str):
-    """ncu DRAM bytes per launch of k_pja from the committed profile summary
+def profile_traffic(kernel: str, kernel_digest: str):
+    """ncu DRAM bytes per launch of `kernel` from its committed profile summary
     ("key: value" lines), if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_pja_column_collapse.txt")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_column_collapse.txt")
     try:
         kv = {}
         with open(path) as f:
@@ -386,7 +396,7 @@ def run_gpu(args):
     clocks.start()
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    step_ms, pja_ms, pja_bytes_tot = [], 0.0, 0
+    step_ms, pja_ms, pja_bytes_tot, con_ms, con_bytes_tot = [], 0.0, 0, 0.0, 0
     barrier(world)
     torch.cuda.synchronize(dev)
     torch.cuda.nvtx.range_push("timed")     # lets ncu --nvtx-include "timed/" select the timed steps
@@ -397,8 +407,10 @@ def run_gpu(args):
         ev1[k].record(stream)
         st = sim.stage_ms()                       # waits for this step
         pja_ms += st["pja"]
+        con_ms += st["contacts"]
         s = sim.stats()
         pja_bytes_tot += sc.params.pja_iters * pja_bytes(sc.n, s["n_pp"], s["n_body"])
+        con_bytes_tot += contacts_bytes(sc.n, s["n_pp"], s["n_body"], 2 * sc.n)
     torch.cuda.synchronize(dev)
     torch.cuda.nvtx.range_pop()
     barrier(world)
@@ -410,16 +422,23 @@ def run_gpu(args):
     stats = sim.stats()
     value = sum_over_ranks(float(sc.n * args.steps), world, dev) / (total_ms * 1e-3)
 
-    # roofline of the dominant kernel: k_pja, I launches per step
-    launches = args.steps * sc.params.pja_iters
-    avg_launch_s = pja_ms * 1e-3 / launches
-    bytes_per_launch = pja_bytes_tot / launches
+    # roofline of the dominant kernel (largest share of the timed steps), the other beside it
     peak, peak_kind = measured_peaks()
-    achieved = bytes_per_launch / avg_launch_s / 1e9
-    roof = {"bound": "hbm", "kernel": "k_pja", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-            "traffic": profile_traffic(kernel_digest()), "bytes_per_launch": bytes_per_launch,
-            "avg_launch_us": avg_launch_s * 1e6, "share_of_step": pja_ms / sum(step_ms)}
+    digest = kernel_digest()
+
+    def roof(kernel, total_ms, total_bytes, launches):
+        avg_s = total_ms * 1e-3 / launches
+        per_launch = total_bytes / launches
+        achieved = per_launch / avg_s / 1e9
+        return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy), burst",
+                "traffic": profile_traffic(kernel, digest), "bytes_per_launch": per_launch,
+                "avg_launch_us": avg_s * 1e6, "share_of_step": total_ms / sum(step_ms)}
+
+    roofs = [roof("k_pja", pja_ms, pja_bytes_tot, args.steps * sc.params.pja_iters),
+             roof("k_contacts", con_ms, con_bytes_tot, args.steps)]
+    roofs.sort(key=lambda r: -r["share_of_step"])
+    roof_main, roof_other = roofs
 
     # end to end through the public API with host buffers: H2D of the state, one
     # step, D2H of the new state, every step
@@ -451,7 +470,7 @@ def run_gpu(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {**workload_config(sc), "replicas": world, "tuning_set": sim.tuning_selected,
                            "timed_steps": window},
-                "roofline": roof, "cpu_baseline": cpu,
+                "roofline": roof_main, "roofline_next": roof_other, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "steps": e2e_steps,
                         "h2d_bytes_per_step": sc.n * (16 + 12), "d2h_bytes_per_step": sc.n * (16 + 12)},
                 "gpu_launches": sim.kernels_per_step * args.steps, "clocks": clk,

@@ -471,8 +471,8 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
   const size_t nK = (size_t)n * s->K, nKb = (size_t)n * s->Kb;
   if ((rc = dalloc(s, &a.pos_id, n)) || (rc = dalloc(s, &a.vel_id, n)) || (rc = dalloc(s, &a.env_of, n)) ||
       (rc = dalloc(s, &a.key_id, n)) || (rc = dalloc(s, &a.cnt, s->nh_pad)) ||
-      (rc = dalloc(s, &a.start, (size_t)s->nh_pad + 4)) || (rc = dalloc(s, &a.bsum, s->nh_pad / gg::kScanTile)) ||
-      (rc = dalloc(s, &a.sid_tmp, n)) || (rc = dalloc(s, &a.sid, n)) || (rc = dalloc(s, &a.U[0], n)) ||
+      (rc = dalloc(s, &a.start, (size_t)s->nh_pad + 4)) || (rc = dalloc(s, &a.range, s->nh_pad)) || (rc = dalloc(s, &a.bsum, s->nh_pad / gg::kScanTile)) ||
+      (rc = dalloc(s, &a.sid_tmp, n)) || (rc = dalloc(s, &a.sid, n)) || (rc = dalloc(s, &a.pos_s, n)) || (rc = dalloc(s, &a.U[0], n)) ||
       (rc = dalloc(s, &a.U[1], n)) || (rc = dalloc(s, &a.ccount, n)) || (rc = dalloc(s, &a.cj, nK)) ||
       (rc = dalloc(s, &a.cn, nK)) || (rc = dalloc(s, &a.clam, 3 * nK)) || (rc = dalloc(s, &a.bj, nKb)) ||
       (rc = dalloc(s, &a.bn, nKb)) || (rc = dalloc(s, &a.bxc, nKb)) || (rc = dalloc(s, &a.blam, 3 * nKb)) ||

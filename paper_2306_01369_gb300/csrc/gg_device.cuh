@@ -62,6 +62,16 @@ struct DevBody {
   uint32_t fid;         // free bodies: index into the free-body arrays
 };
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with programmatic
+// stream serialization may be scheduled while its predecessor in the stream drains; it
+// touches no memory before griddepcontrol.wait, which returns once the predecessor grid
+// has completed and its writes are visible.  launch_dependents, issued right after,
+// lets the successor's blocks be scheduled once every block of this grid has issued
+// it.  For a normal launch both are no-ops.  Every kernel of the step calls this first.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // A corner of a free box touching a non-free body of its environment.
 struct CornerContact {
   uint32_t o, valid;
@@ -95,9 +105,12 @@ struct StepArgs {
   // buckets
   uint32_t *cnt;    // nh_pad entries, zero between steps
   uint32_t *start;  // nh_pad + 1
+  uint2 *range;     // nh_pad: (start, end) of every bucket, one load in the bucket walk
   uint32_t *bsum;   // scan block sums
-  // sorted slots: particle id of each slot, ascending (bucket, id)
+  // sorted slots: particle id of each slot, ascending (bucket, id), and that
+  // particle's position (the bucket walk reads candidates without an id hop)
   uint32_t *sid_tmp, *sid;
+  float4 *pos_s;
   // per particle (id order)
   float4 *U[2];     // velocity estimate, w = n_contacts / m
   uint32_t *ccount; // pp | body << 8

@@ -5,7 +5,7 @@
 //   k_key            bucket of every particle (Eq. 6), bucket histogram, body prep
 //   k_scan_*         exclusive scan of the histogram -> bucket start table
 //   k_scatter        counting-sort scatter (returns the histogram to zero)
-//   k_reorder        stable order inside each bucket (ascending id)
+//   k_reorder        stable order inside each bucket (ascending id), positions in slot order
 //   k_contacts       27-cell bucket walk, sphere test, SDF tests (Sec. II-B, II-C)
 //   k_free_prep      (free bodies) sorted contact lists, box-corner contacts
 //   k_pja  x I       projected-Jacobi sweeps (Alg. 1), one launch per iteration,
@@ -95,6 +95,7 @@ __device__ void prep_body(const StepArgs &a, uint32_t gb) {
 }
 
 __global__ void k_key(StepArgs a) {
+  pdl_enter();
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < a.n) {
     float4 p = a.pos_id[i];
@@ -125,6 +126,7 @@ __global__ void k_key(StepArgs a) {
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(StepArgs a) {
+  pdl_enter();
   const uint4 *c4 = reinterpret_cast<const uint4 *>(a.cnt + (size_t)blockIdx.x * kScanTile +
                                                      (size_t)threadIdx.x * kScanItems);
   uint32_t s = 0;
@@ -147,6 +149,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(StepArgs a) {
 
 // Single block: exclusive scan of the block sums in place; start[nh_pad] = total.
 __global__ void __launch_bounds__(1024) k_scan_top(StepArgs a, uint32_t nblk) {
+  pdl_enter();
   __shared__ uint32_t carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
@@ -175,6 +178,7 @@ __global__ void __launch_bounds__(1024) k_scan_top(StepArgs a, uint32_t nblk) {
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(StepArgs a) {
+  pdl_enter();
   const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
   const uint4 *c4 = reinterpret_cast<const uint4 *>(a.cnt + base);
   uint32_t v[kScanItems];
@@ -202,18 +206,17 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(StepArgs a) {
   __syncthreads();
   uint32_t run = a.bsum[blockIdx.x] + ws[wid] + inc - tsum;
   uint4 *s4 = reinterpret_cast<uint4 *>(a.start + base);
+  uint4 *r4 = reinterpret_cast<uint4 *>(a.range + base);  // two (start, end) pairs per uint4
 #pragma unroll
   for (int k = 0; k < kScanItems / 4; ++k) {
-    uint4 o;
-    o.x = run;
-    run += v[4 * k];
-    o.y = run;
-    run += v[4 * k + 1];
-    o.z = run;
-    run += v[4 * k + 2];
-    o.w = run;
-    run += v[4 * k + 3];
-    s4[k] = o;
+    uint32_t b[5];
+    b[0] = run;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) b[m + 1] = b[m] + v[4 * k + m];
+    run = b[4];
+    s4[k] = make_uint4(b[0], b[1], b[2], b[3]);
+    r4[2 * k] = make_uint4(b[0], b[1], b[1], b[2]);
+    r4[2 * k + 1] = make_uint4(b[2], b[3], b[3], b[4]);
   }
 }
 
@@ -222,6 +225,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(StepArgs a) {
 // ---------------------------------------------------------------------------
 
 __global__ void k_scatter(StepArgs a) {
+  pdl_enter();
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const uint32_t key = a.key_id[i];
@@ -230,21 +234,33 @@ __global__ void k_scatter(StepArgs a) {
 }
 
 __global__ void k_reorder(StepArgs a) {
+  pdl_enter();
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.n) return;
   const uint32_t id = a.sid_tmp[s];
   const uint32_t key = a.key_id[id];
-  const uint32_t b0 = a.start[key], b1 = a.start[key + 1];
+  const uint2 rg = a.range[key];
+  const uint32_t b0 = rg.x, b1 = rg.y;
   uint32_t rank = 0;
   for (uint32_t t = b0; t < b1; ++t) rank += (a.sid_tmp[t] < id) ? 1u : 0u;
   a.sid[b0 + rank] = id;
+  a.pos_s[b0 + rank] = a.pos_id[id];
 }
 
 // ---------------------------------------------------------------------------
 // 5. contacts: particle-particle (27 buckets) and particle-body (SDF)
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_contacts(StepArgs a) {
+constexpr int kWalkGroup = 3;       // buckets of a row (dx = -1, 0, 1), walked together
+constexpr int kContactsBlock = 128;  // threads per block of k_contacts
+
+// The partner list of a thread, kept sorted by id while the buckets are walked, lives
+// in shared memory, slot p of thread t at [p * blockDim.x + t] (conflict-free): an
+// array indexed at run time in registers would go to local memory, which at full
+// occupancy does not fit in L1.  Dynamic shared memory: K * blockDim.x words.
+__global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
+  pdl_enter();
+  extern __shared__ uint32_t s_fid[];
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t npp = 0, nbc = 0;
   float psi_max = 0.f;
@@ -253,7 +269,8 @@ __global__ void __launch_bounds__(256) k_contacts(StepArgs a) {
     const uint32_t e = a.env_of[i];
     const DevEnv E = a.envs[e];
     const int32_t k0 = cell_of(pi.x, E.inv_cell), k1 = cell_of(pi.y, E.inv_cell), k2 = cell_of(pi.z, E.inv_cell);
-    uint32_t fid[kMaxK];
+    uint32_t *fid = s_fid + threadIdx.x;
+    const uint32_t S = blockDim.x;
     const uint32_t K = a.K;
     bool ovf = false;
     // Eq. 6 terms of the three cells along each axis, combined 27 ways below
@@ -264,42 +281,79 @@ __global__ void __launch_bounds__(256) k_contacts(StepArgs a) {
       hy[q] = ((uint32_t)(k1 + q - 1) - kHashQ) * kHashP2;
       hz[q] = ((uint32_t)(k2 + q - 1) - kHashQ) * kHashP3;
     }
-    for (int dz = -1; dz <= 1; ++dz) {
-      // the nine bucket ranges of this plane are loaded together, then walked
-      uint32_t r0[9], r1[9];
+    // The 27 buckets are walked as nine rows of three (dx = -1, 0, 1 at fixed dy, dz).
+    // A row's three ranges are loaded while the previous row is walked; within a row
+    // the walk takes one candidate from every non-empty bucket per round, so the
+    // position loads of a round, and the id loads of its hits, are independent.
+    uint32_t n0[kWalkGroup], n1[kWalkGroup];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        const uint32_t h = E.hbase + fast_mod(hx[q % 3] ^ hy[q / 3] ^ hz[dz + 1], E.nh_magic, E.nh);
-        r0[q] = a.start[h];
-        r1[q] = a.start[h + 1];
+    for (int q = 0; q < kWalkGroup; ++q) {
+      const uint2 rg = a.range[E.hbase + fast_mod(hx[q] ^ hy[0] ^ hz[0], E.nh_magic, E.nh)];
+      n0[q] = rg.x;
+      n1[q] = rg.y;
+    }
+#pragma unroll 1
+    for (int row = 0; row < 9; ++row) {
+      uint32_t r0[kWalkGroup], r1[kWalkGroup];
+#pragma unroll
+      for (int q = 0; q < kWalkGroup; ++q) {
+        r0[q] = n0[q];
+        r1[q] = n1[q];
       }
+      if (row < 8) {
+        const uint32_t hyz = hy[(row + 1) % 3] ^ hz[(row + 1) / 3];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        const uint32_t t1 = r1[q];
-        for (uint32_t t = r0[q]; t < t1; ++t) {
-          const uint32_t jid = a.sid[t];
-          if (jid == i) continue;
+        for (int q = 0; q < kWalkGroup; ++q) {
+          const uint2 rg = a.range[E.hbase + fast_mod(hx[q] ^ hyz, E.nh_magic, E.nh)];
+          n0[q] = rg.x;
+          n1[q] = rg.y;
+        }
+      }
+      for (;;) {
+        float4 pc[kWalkGroup];
+        uint32_t live = 0;
+#pragma unroll
+        for (int q = 0; q < kWalkGroup; ++q)
+          if (r0[q] < r1[q]) {
+            live |= 1u << q;
+            pc[q] = a.pos_s[r0[q]];
+          }
+        if (!live) break;
+        uint32_t hit = 0;
+#pragma unroll
+        for (int q = 0; q < kWalkGroup; ++q) {
           float d2;
           float3 d;
-          if (!sphere_hit(pi, a.pos_id[jid], &d2, &d)) continue;
+          if (((live >> q) & 1u) && sphere_hit(pi, pc[q], &d2, &d)) hit |= 1u << q;
+        }
+        uint32_t jc[kWalkGroup];
+#pragma unroll
+        for (int q = 0; q < kWalkGroup; ++q)
+          if ((hit >> q) & 1u) jc[q] = a.sid[r0[q]];
+#pragma unroll
+        for (int q = 0; q < kWalkGroup; ++q) {
+          r0[q] += (live >> q) & 1u;
+          if (!((hit >> q) & 1u)) continue;
+          const uint32_t jid = jc[q];
+          if (jid == i) continue;
           // insert by ascending id; a bucket reached twice yields the same id: skip it
           uint32_t p = 0;
-          while (p < npp && fid[p] < jid) ++p;
-          if (p < npp && fid[p] == jid) continue;
+          while (p < npp && fid[p * S] < jid) ++p;
+          if (p < npp && fid[p * S] == jid) continue;
           if (npp == K) {
             ovf = true;
             if (p == K) continue;
           } else {
             ++npp;
           }
-          for (uint32_t q2 = npp - 1; q2 > p; --q2) fid[q2] = fid[q2 - 1];
-          fid[p] = jid;
+          for (uint32_t q2 = npp - 1; q2 > p; --q2) fid[q2 * S] = fid[(q2 - 1) * S];
+          fid[p * S] = jid;
         }
       }
     }
     const size_t n = a.n;
     for (uint32_t c = 0; c < npp; ++c) {
-      const uint32_t j = fid[c];
+      const uint32_t j = fid[c * S];
       float d2;
       float3 d;
       const float4 pj = a.pos_id[j];
@@ -504,6 +558,7 @@ __device__ __forceinline__ void pja_particle(const StepArgs &a, uint32_t i, int 
 // One sweep per launch.
 template <bool TAPE>
 __global__ void __launch_bounds__(512) k_pja(StepArgs a, int s, Tape tp, int it) {
+  pdl_enter();
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < a.n) pja_particle<TAPE, false>(a, i, s, tp, it);
 }
@@ -544,6 +599,7 @@ __device__ __forceinline__ void grid_barrier(DevCtrl *c) {
 // loop over particles per sweep, a grid barrier between sweeps.  Same per-particle
 // arithmetic as k_pja, so results are bit-identical.
 __global__ void __launch_bounds__(1024) k_pja_fused(StepArgs a, uint32_t iters) {
+  pdl_enter();
   const Tape none{};
   for (uint32_t it = 0; it < iters; ++it) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x)
@@ -561,6 +617,7 @@ constexpr int kFreeSortMax = 8192;  // contact-list capacity limit (shared-memor
 // One block per free body: sort its contact list (bitonic, ascending), then find
 // its box corners touching the environment's non-free bodies (FP32 decision).
 __global__ void __launch_bounds__(1024) k_free_prep(StepArgs a) {
+  pdl_enter();
   __shared__ uint32_t sk[kFreeSortMax];
   const uint32_t fid = blockIdx.x;
   const uint32_t gb = a.fgb[fid];
@@ -637,6 +694,7 @@ __device__ __forceinline__ float free_inv_mass(const DevBody &B, float3 r, float
 // the twist of this iteration), sum every impulse it received in a fixed order,
 // and set its twist for the next iteration (Newton-Euler, gyroscopic term dropped).
 __global__ void __launch_bounds__(256) k_free_update(StepArgs a) {
+  pdl_enter();
   const uint32_t fid = blockIdx.x;
   const uint32_t gb = a.fgb[fid];
   if (gb == 0xffffffffu) return;
@@ -706,6 +764,7 @@ __global__ void __launch_bounds__(256) k_free_update(StepArgs a) {
 // ---------------------------------------------------------------------------
 
 __global__ void k_integrate(StepArgs a, int s) {
+  pdl_enter();
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const float4 u = a.U[s][i];
@@ -723,6 +782,7 @@ __global__ void k_integrate(StepArgs a, int s) {
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_wrench_partial(StepArgs a) {
+  pdl_enter();
   const uint32_t c = blockIdx.x, lb = blockIdx.y;
   const uint32_t e = a.chunk_env[c];
   const DevEnv &E = a.envs[e];
@@ -761,6 +821,7 @@ __global__ void __launch_bounds__(256) k_wrench_partial(StepArgs a) {
 // One warp per body: sum its environment's chunk partials in a fixed order
 // (lane-strided, then a fixed butterfly) into the wrench ring.
 __global__ void __launch_bounds__(256) k_wrench_sum(StepArgs a) {
+  pdl_enter();
   const uint32_t gb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const uint32_t nbt = a.n_envs * a.maxb;
@@ -811,6 +872,7 @@ __global__ void __launch_bounds__(256) k_wrench_sum(StepArgs a) {
 
 // Body poses after the step (p += dt v, q <- exp(dt w / 2) q), then the step counter.
 __global__ void __launch_bounds__(256) k_body_update(StepArgs a) {
+  pdl_enter();
   const uint32_t step = a.ctrl->step;
   const uint32_t nbt = a.n_envs * a.maxb;
   for (uint32_t gb = threadIdx.x; gb < nbt; gb += blockDim.x) {
@@ -963,24 +1025,64 @@ uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls) {
   return k;
 }
 
+// One kernel launch of the step.  With `pdl` the launch asks for programmatic
+// serialization with the stream's previous kernel (every step kernel begins with
+// pdl_enter, so it still waits for that kernel's completion before touching memory;
+// what overlaps is its launch and the predecessor's tail).
+template <typename... P, typename... A>
+static cudaError_t launch(bool pdl, void (*k)(P...), dim3 grid, unsigned block, size_t smem, cudaStream_t st,
+                          A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st, cudaEvent_t *ev, const Tape *tp) {
   cudaError_t e;
   const uint32_t nbt = a.n_envs * a.maxb;
   const uint32_t nk = a.n > nbt ? a.n : nbt;
-  if ((e = mark(ev, 0, st)) != cudaSuccess) return e;
-  k_key<<<grid_for(nk, 256), 256, 0, st>>>(a);
+  // Programmatic launches chain the kernels of the step; the first kernel after an
+  // event record, a copy or the previous step is launched normally.  The taped
+  // forward keeps plain launches (copies sit between its stages).
+  const bool allow_pdl = !tp;
+  bool after_kernel = false;
+#define GG_LAUNCH(kern, grid, block, smem, ...)                                                       \
+  do {                                                                                                \
+    if ((e = launch(allow_pdl && after_kernel, kern, grid, block, smem, st, __VA_ARGS__)) != cudaSuccess) \
+      return e;                                                                                       \
+    after_kernel = true;                                                                              \
+  } while (0)
+#define GG_MARK(k)                                             \
+  do {                                                         \
+    if (ev) {                                                  \
+      if ((e = mark(ev, k, st)) != cudaSuccess) return e;      \
+      after_kernel = false;                                    \
+    }                                                          \
+  } while (0)
+  GG_MARK(0);
+  GG_LAUNCH(k_key, dim3(grid_for(nk, 256)), 256, 0, a);
   const uint32_t nblk = a.nh_pad / kScanTile;
-  k_scan_reduce<<<nblk, kScanThreads, 0, st>>>(a);
-  k_scan_top<<<1, 1024, 0, st>>>(a, nblk);
-  k_scan_down<<<nblk, kScanThreads, 0, st>>>(a);
+  GG_LAUNCH(k_scan_reduce, dim3(nblk), kScanThreads, 0, a);
+  GG_LAUNCH(k_scan_top, dim3(1), 1024, 0, a, nblk);
+  GG_LAUNCH(k_scan_down, dim3(nblk), kScanThreads, 0, a);
   if (a.n) {
-    k_scatter<<<grid_for(a.n, 256), 256, 0, st>>>(a);
-    k_reorder<<<grid_for(a.n, 256), 256, 0, st>>>(a);
+    GG_LAUNCH(k_scatter, dim3(grid_for(a.n, 256)), 256, 0, a);
+    GG_LAUNCH(k_reorder, dim3(grid_for(a.n, 256)), 256, 0, a);
   }
-  if ((e = mark(ev, 1, st)) != cudaSuccess) return e;
-  if (a.n) k_contacts<<<grid_for(a.n, 256), 256, 0, st>>>(a);
-  if (a.F) k_free_prep<<<a.F, 1024, 0, st>>>(a);
-  if ((e = mark(ev, 2, st)) != cudaSuccess) return e;
+  GG_MARK(1);
+  if (a.n)
+    GG_LAUNCH(k_contacts, dim3(grid_for(a.n, kContactsBlock)), kContactsBlock,
+              (size_t)a.K * kContactsBlock * sizeof(uint32_t), a);
+  if (a.F) GG_LAUNCH(k_free_prep, dim3(a.F), 1024, 0, a);
+  GG_MARK(2);
   if (tp && a.n) {  // U^0 and lambda^0 = 0 open the tape
     if ((e = cudaMemcpyAsync(tp->Uh, a.U[0], sizeof(float4) * a.n, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(tp->lamh, 0, sizeof(float) * 3 * (size_t)a.K * a.n, st)) != cudaSuccess) return e;
@@ -998,26 +1100,26 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     if ((e = cudaLaunchKernelEx(&cfg, k_pja_fused, a, ls.iters)) != cudaSuccess) return e;
+    after_kernel = true;
   } else
   for (uint32_t it = 0; it < ls.iters; ++it) {
     if (a.n) {
       if (tp)
-        k_pja<true><<<grid_for(a.n, ls.pja_block), ls.pja_block, 0, st>>>(a, it & 1, *tp, (int)it);
+        GG_LAUNCH(k_pja<true>, dim3(grid_for(a.n, ls.pja_block)), ls.pja_block, 0, a, (int)(it & 1), *tp, (int)it);
       else
-        k_pja<false><<<grid_for(a.n, ls.pja_block), ls.pja_block, 0, st>>>(a, it & 1, none, (int)it);
+        GG_LAUNCH(k_pja<false>, dim3(grid_for(a.n, ls.pja_block)), ls.pja_block, 0, a, (int)(it & 1), none, (int)it);
     }
-    if (a.F) k_free_update<<<a.F, 256, 0, st>>>(a);
+    if (a.F) GG_LAUNCH(k_free_update, dim3(a.F), 256, 0, a);
   }
   if (tp) return cudaGetLastError();
-  if ((e = mark(ev, 3, st)) != cudaSuccess) return e;
-  if (a.n) k_integrate<<<grid_for(a.n, 256), 256, 0, st>>>(a, ls.iters & 1);
-  if (a.n_chunks) {
-    dim3 g(a.n_chunks, a.maxb);
-    k_wrench_partial<<<g, 256, 0, st>>>(a);
-  }
-  k_wrench_sum<<<grid_for(nbt * 32, 256), 256, 0, st>>>(a);
-  k_body_update<<<1, 256, 0, st>>>(a);
-  if ((e = mark(ev, 4, st)) != cudaSuccess) return e;
+  GG_MARK(3);
+  if (a.n) GG_LAUNCH(k_integrate, dim3(grid_for(a.n, 256)), 256, 0, a, (int)(ls.iters & 1));
+  if (a.n_chunks) GG_LAUNCH(k_wrench_partial, dim3(a.n_chunks, a.maxb), 256, 0, a);
+  GG_LAUNCH(k_wrench_sum, dim3(grid_for(nbt * 32, 256)), 256, 0, a);
+  GG_LAUNCH(k_body_update, dim3(1), 256, 0, a);
+  GG_MARK(4);
+#undef GG_LAUNCH
+#undef GG_MARK
   return cudaGetLastError();
 }
 

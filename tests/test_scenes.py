@@ -1,4 +1,6 @@
 """Seeded input generators: shapes and recipes of the workloads (no GPU)."""
+import os
+
 import numpy as np
 
 from paper_2306_01369_gb300 import scenes as S
@@ -33,3 +35,24 @@ def test_column_recipe():
     assert sc.n == 262144 and sc.info["dims"] == (40, 40, 164)
     assert abs(sc.info["pitch"] - 4.488e-3) < 1e-9
     assert sc.params.dt == 5e-5 and sc.params.pja_iters == 20 and sc.params.mu == 0.6
+
+
+def test_pile_statistics_recovers_a_cone():
+    """The repose-angle measure of the long-run statistics test, on a solid cone of
+    known base angle filled uniformly with points.  Below a surface of height H(r) the
+    95th percentile of z is 0.95 H(r), so the measure must return atan(0.95 tan(angle));
+    the centre of mass must sit h/4 above the base (closed form)."""
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from gpu_helpers import pile_statistics
+    rng = np.random.default_rng(7)
+    for deg in (10.0, 25.0, 35.0):
+        R = 0.2
+        h = R * np.tan(np.radians(deg))
+        p = rng.uniform([-R, -R, 0], [R, R, h], (400000, 3))
+        p = p[p[:, 2] <= h * (1 - np.hypot(p[:, 0], p[:, 1]) / R)]
+        angle, com, nb = pile_statistics(p, np.ones(len(p)), 0.002)
+        assert nb >= 10
+        want = np.degrees(np.arctan(0.95 * np.tan(np.radians(deg))))
+        assert abs(angle - want) < 0.3, (angle, want)
+        assert abs(com[2] - h / 4) < 0.01 * h
