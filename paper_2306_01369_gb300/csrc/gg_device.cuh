@@ -155,11 +155,17 @@ __device__ __forceinline__ uint32_t hash_cell(int32_t k0, int32_t k1, int32_t k2
 }
 
 // Eq. 6 with the exact fast remainder; same value as hash_cell.
+// Eq. 6's "mod n_h" of a hash value: a mask when n_h is a power of two (the paper's
+// 2n heuristic gives one for power-of-two n), else the exact remainder above.
+__device__ __forceinline__ uint32_t mod_nh(uint32_t h, const DevEnv &E) {
+  return (E.nh & (E.nh - 1u)) == 0u ? (h & (E.nh - 1u)) : fast_mod(h, E.nh_magic, E.nh);
+}
+
 __device__ __forceinline__ uint32_t hash_cell_fm(int32_t k0, int32_t k1, int32_t k2, const DevEnv &E) {
   const uint32_t a = ((uint32_t)k0 - kHashQ) * kHashP1;
   const uint32_t b = ((uint32_t)k1 - kHashQ) * kHashP2;
   const uint32_t c = ((uint32_t)k2 - kHashQ) * kHashP3;
-  return fast_mod(a ^ b ^ c, E.nh_magic, E.nh);
+  return mod_nh(a ^ b ^ c, E);
 }
 
 // squared distance ((dx dx + dy dy) + dz dz) and the sum of radii squared

@@ -3,20 +3,21 @@
 // One time step = the launches below, in this order (captured once into a CUDA
 // graph and replayed):
 //   k_key            bucket of every particle (Eq. 6), bucket histogram, body prep
-//   k_scan_*         exclusive scan of the histogram -> bucket start table
+//   k_scan_*         exclusive scan of the histogram (tile sums, their scan, down-sweep)
+//                    -> bucket start table and (start, end) ranges
 //   k_scatter        counting-sort scatter (returns the histogram to zero)
 //   k_reorder        stable order inside each bucket (ascending id), positions in slot order
 //   k_contacts       27-cell bucket walk, sphere test, SDF tests (Sec. II-B, II-C)
 //   k_free_prep      (free bodies) sorted contact lists, box-corner contacts
 //   k_pja  x I       projected-Jacobi sweeps (Alg. 1), one launch per iteration,
 //   k_free_update    each followed (free bodies) by the bodies' twist update
-//   k_integrate      symplectic Euler (Eq. 4-5), in place
+//   k_integrate_wrench  symplectic Euler (Eq. 4-5) in place, and per-body impulse
+//                    sums over fixed chunks of particles (deterministic)
+//   k_wrench_sum     per-body sums over chunks into the wrench readback ring
+//   k_body_update    kinematic body poses, step counter
 // Contacts, sweeps and integration run over particles in the caller's order (their
 // storage order); the bucket table is only walked, so spatially ordered inputs keep
 // neighbours' data in nearby cache lines.
-//   k_wrench_partial per-body impulse sums over fixed slot chunks (deterministic)
-//   k_wrench_sum     per-body sums over chunks into the wrench readback ring
-//   k_body_update    kinematic body poses, step counter
 // Detection and impulse computation are separate launches, the split the paper
 // finds fastest (Sec. II-D).
 #include "gg_device.cuh"
@@ -281,6 +282,32 @@ __global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
       hy[q] = ((uint32_t)(k1 + q - 1) - kHashQ) * kHashP2;
       hz[q] = ((uint32_t)(k2 + q - 1) - kHashQ) * kHashP3;
     }
+    // Neighbour cells that cannot hold a partner are not walked.  In cell units
+    // (u = x inv_c, cell k spans [k - 1/2, k + 1/2)) the gap from u_i to the cell
+    // at offset d along an axis is 0 for d = 0 and 1/2 -+ f for d = -+1, f = u_i - k_i.
+    // A partner j has |x_i - x_j| <= r_i + r_j <= r_i + c/2 (c >= 2 r_max is checked
+    // at creation), so a cell whose gap vector is longer than r_i inv_c + 1/2 plus a
+    // margin (float32 rounding of u and of the cell assignment: 2^-10 cells plus
+    // four ulps of |u|) is skipped.  A bucket shared with a nearer cell is still
+    // walked for that cell, so the contact set is exactly the 27-cell one.
+    float g2x[3], g2y[3], g2z[3];
+    {
+      const float ux = __fmul_rn(pi.x, E.inv_cell), uy = __fmul_rn(pi.y, E.inv_cell), uz = __fmul_rn(pi.z, E.inv_cell);
+      const float fx = __fsub_rn(ux, (float)k0), fy = __fsub_rn(uy, (float)k1), fz = __fsub_rn(uz, (float)k2);
+      const float lo_x = fmaxf(0.5f + fx, 0.f), hi_x = fmaxf(0.5f - fx, 0.f);
+      const float lo_y = fmaxf(0.5f + fy, 0.f), hi_y = fmaxf(0.5f - fy, 0.f);
+      const float lo_z = fmaxf(0.5f + fz, 0.f), hi_z = fmaxf(0.5f - fz, 0.f);
+      g2x[0] = lo_x * lo_x; g2x[1] = 0.f; g2x[2] = hi_x * hi_x;
+      g2y[0] = lo_y * lo_y; g2y[1] = 0.f; g2y[2] = hi_y * hi_y;
+      g2z[0] = lo_z * lo_z; g2z[1] = 0.f; g2z[2] = hi_z * hi_z;
+    }
+    float reach;
+    {
+      const float um = fabsf(__fmul_rn(pi.x, E.inv_cell)) + fabsf(__fmul_rn(pi.y, E.inv_cell)) +
+                       fabsf(__fmul_rn(pi.z, E.inv_cell));
+      const float rr = pi.w * E.inv_cell + 0.5f + 0.0009765625f + um * 4.76837158203125e-7f;  // 2^-10, 2^-21
+      reach = rr * rr;
+    }
     // The 27 buckets are walked as nine rows of three (dx = -1, 0, 1 at fixed dy, dz).
     // A row's three ranges are loaded while the previous row is walked; within a row
     // the walk takes one candidate from every non-empty bucket per round, so the
@@ -288,9 +315,12 @@ __global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
     uint32_t n0[kWalkGroup], n1[kWalkGroup];
 #pragma unroll
     for (int q = 0; q < kWalkGroup; ++q) {
-      const uint2 rg = a.range[E.hbase + fast_mod(hx[q] ^ hy[0] ^ hz[0], E.nh_magic, E.nh)];
-      n0[q] = rg.x;
-      n1[q] = rg.y;
+      n0[q] = n1[q] = 0u;
+      if (g2x[q] + g2y[0] + g2z[0] <= reach) {
+        const uint2 rg = a.range[E.hbase + mod_nh(hx[q] ^ hy[0] ^ hz[0], E)];
+        n0[q] = rg.x;
+        n1[q] = rg.y;
+      }
     }
 #pragma unroll 1
     for (int row = 0; row < 9; ++row) {
@@ -301,12 +331,18 @@ __global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
         r1[q] = n1[q];
       }
       if (row < 8) {
-        const uint32_t hyz = hy[(row + 1) % 3] ^ hz[(row + 1) / 3];
+        const int ny = (row + 1) % 3, nz = (row + 1) / 3;
+        // selects keep the per-axis terms in registers (run-time indexing would not)
+        const uint32_t hyz = hy[ny] ^ hz[nz];
+        const float g2yz = g2y[ny] + g2z[nz];
 #pragma unroll
         for (int q = 0; q < kWalkGroup; ++q) {
-          const uint2 rg = a.range[E.hbase + fast_mod(hx[q] ^ hyz, E.nh_magic, E.nh)];
-          n0[q] = rg.x;
-          n1[q] = rg.y;
+          n0[q] = n1[q] = 0u;
+          if (g2x[q] + g2yz <= reach) {
+            const uint2 rg = a.range[E.hbase + mod_nh(hx[q] ^ hyz, E)];
+            n0[q] = rg.x;
+            n1[q] = rg.y;
+          }
         }
       }
       for (;;) {
@@ -763,10 +799,8 @@ __global__ void __launch_bounds__(256) k_free_update(StepArgs a) {
 // 7. symplectic Euler back into particle-id order
 // ---------------------------------------------------------------------------
 
-__global__ void k_integrate(StepArgs a, int s) {
-  pdl_enter();
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
+// Euler update of one particle, in place (Eq. 4-5).
+__device__ __forceinline__ void integrate_particle(const StepArgs &a, int s, uint32_t i) {
   const float4 u = a.U[s][i];
   const float4 p = a.pos_id[i];
   const float invm = a.vel_id[i].w;
@@ -778,43 +812,48 @@ __global__ void k_integrate(StepArgs a, int s) {
 }
 
 // ---------------------------------------------------------------------------
-// 8. wrench: per (chunk, body) fixed-order sums, then per body over chunks
+// 7-8. integration and the wrench partials: one block per chunk of kWrenchChunk
+//      particles of one environment; the block integrates its particles, then sums
+//      each body's contact forces and torques over them in a fixed order
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_wrench_partial(StepArgs a) {
+__global__ void __launch_bounds__(256) k_integrate_wrench(StepArgs a, int s) {
   pdl_enter();
-  const uint32_t c = blockIdx.x, lb = blockIdx.y;
+  const uint32_t c = blockIdx.x;
   const uint32_t e = a.chunk_env[c];
   const DevEnv &E = a.envs[e];
-  if (lb >= E.nbodies) return;
-  const uint32_t gb = e * a.maxb + lb;
-  const DevBody &B = a.bodies[gb];
   const uint32_t s0 = E.off + (c - E.chunk0) * kWrenchChunk;
   const uint32_t s1 = min(s0 + kWrenchChunk, E.off + E.n);
+  for (uint32_t i = s0 + threadIdx.x; i < s1; i += 256) integrate_particle(a, s, i);
   const size_t n = a.n, KbN = (size_t)a.Kb * n;
   const float inv_dt = 1.0f / a.dt;
-  float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (uint32_t s = s0 + threadIdx.x; s < s1; s += 256) {
-    const uint32_t nbc = (a.ccount[s] >> 8) & 0xffu;
-    for (uint32_t k = 0; k < nbc; ++k) {
-      const size_t o = (size_t)k * n + s;
-      if (a.bj[o] != gb) continue;
-      const float fx = -a.blam[o] * inv_dt, fy = -a.blam[o + KbN] * inv_dt, fz = -a.blam[o + 2 * KbN] * inv_dt;
-      const float4 xc = a.bxc[o];
-      const float rx = xc.x - B.p[0], ry = xc.y - B.p[1], rz = xc.z - B.p[2];
-      v[0] += fx;
-      v[1] += fy;
-      v[2] += fz;
-      v[3] += ry * fz - rz * fy;
-      v[4] += rz * fx - rx * fz;
-      v[5] += rx * fy - ry * fx;
+  for (uint32_t lb = 0; lb < E.nbodies; ++lb) {
+    const uint32_t gb = e * a.maxb + lb;
+    const DevBody &B = a.bodies[gb];
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (uint32_t i = s0 + threadIdx.x; i < s1; i += 256) {
+      const uint32_t nbc = (a.ccount[i] >> 8) & 0xffu;
+      for (uint32_t k = 0; k < nbc; ++k) {
+        const size_t o = (size_t)k * n + i;
+        if (a.bj[o] != gb) continue;
+        const float fx = -a.blam[o] * inv_dt, fy = -a.blam[o + KbN] * inv_dt, fz = -a.blam[o + 2 * KbN] * inv_dt;
+        const float4 xc = a.bxc[o];
+        const float rx = xc.x - B.p[0], ry = xc.y - B.p[1], rz = xc.z - B.p[2];
+        v[0] += fx;
+        v[1] += fy;
+        v[2] += fz;
+        v[3] += ry * fz - rz * fy;
+        v[4] += rz * fx - rx * fz;
+        v[5] += rx * fy - ry * fx;
+      }
     }
-  }
-  block_sum6<256>(v);
-  if (threadIdx.x == 0) {
-    float *dst = a.wpart + ((size_t)c * a.maxb + lb) * 6;
+    block_sum6<256>(v);
+    if (threadIdx.x == 0) {
+      float *dst = a.wpart + ((size_t)c * a.maxb + lb) * 6;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) dst[k] = v[k];
+      for (int k = 0; k < 6; ++k) dst[k] = v[k];
+    }
+    __syncthreads();  // block_sum6's shared slots are reused by the next body
   }
 }
 
@@ -1019,8 +1058,8 @@ static inline cudaError_t mark(cudaEvent_t *ev, int k, cudaStream_t st) {
 
 uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls) {
   uint32_t k = 6;  // key, scan x3, wrench_sum, body_update
-  if (a.n) k += 5 + ((ls.fused_grid && !a.F) ? 1 : ls.iters);  // scatter, reorder, contacts, pja, integrate
-  if (a.n_chunks) k += 1;
+  if (a.n) k += 3 + ((ls.fused_grid && !a.F) ? 1 : ls.iters);  // scatter, reorder, contacts, pja
+  if (a.n_chunks) k += 1;  // integrate + wrench partials
   if (a.F) k += 1 + ls.iters;  // free_prep, free_update x I
   return k;
 }
@@ -1113,8 +1152,7 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
   }
   if (tp) return cudaGetLastError();
   GG_MARK(3);
-  if (a.n) GG_LAUNCH(k_integrate, dim3(grid_for(a.n, 256)), 256, 0, a, (int)(ls.iters & 1));
-  if (a.n_chunks) GG_LAUNCH(k_wrench_partial, dim3(a.n_chunks, a.maxb), 256, 0, a);
+  if (a.n_chunks) GG_LAUNCH(k_integrate_wrench, dim3(a.n_chunks), 256, 0, a, (int)(ls.iters & 1));
   GG_LAUNCH(k_wrench_sum, dim3(grid_for(nbt * 32, 256)), 256, 0, a);
   GG_LAUNCH(k_body_update, dim3(1), 256, 0, a);
   GG_MARK(4);

@@ -213,6 +213,21 @@ def column_collapse(n=262144, seed=1001, n_steps=2000, dims=None):
                  info={"dims": dims, "pitch": pitch})
 
 
+def pile_column(member=-1, n=32768, dims=(24, 24, 57), mu=0.2, n_steps=20000):
+    """A column collapse that spreads into a low pile and comes to rest within
+    n_steps (mu = 0.2; at mu = 0.6 a column this size stands jammed for thousands of
+    steps).  Member k >= 0 of the ensemble moves the x of every particle with
+    index % 8 == k by one float32 ulp towards +inf; member -1 is the unperturbed
+    column.  The perturbations sample the chaotic spread of the collapse."""
+    sc = column_collapse(n=n, seed=1001, n_steps=n_steps, dims=dims)
+    sc.params.mu = mu
+    if member >= 0:
+        sel = np.arange(sc.n) % 8 == member
+        sc.pos_r[sel, 0] = np.nextafter(sc.pos_r[sel, 0], np.float32(np.inf))
+    sc.name = f"pile_column_{n}_m{member}"
+    return sc
+
+
 def _bed_env(n, r0, jit, seed, side=None, layers=None, n_steps=500, dt=1e-4, scoop_scale=1.0,
              tool_seed=None, margin=0.005):
     """A bed of n spheres in an open container, plus a kinematic scoop on a seeded

@@ -44,7 +44,7 @@ def test_pile_statistics_recovers_a_cone():
     the centre of mass must sit h/4 above the base (closed form)."""
     import sys
     sys.path.insert(0, os.path.dirname(__file__))
-    from gpu_helpers import pile_statistics
+    from pile_stats import pile_statistics
     rng = np.random.default_rng(7)
     for deg in (10.0, 25.0, 35.0):
         R = 0.2
@@ -56,3 +56,14 @@ def test_pile_statistics_recovers_a_cone():
         want = np.degrees(np.arctan(0.95 * np.tan(np.radians(deg))))
         assert abs(angle - want) < 0.3, (angle, want)
         assert abs(com[2] - h / 4) < 0.01 * h
+
+
+def test_pile_column_members_differ_by_one_ulp():
+    base = S.pile_column(-1, n=2048, dims=(8, 8, 32))
+    for k in (0, 5):
+        m = S.pile_column(k, n=2048, dims=(8, 8, 32))
+        sel = np.arange(base.n) % 8 == k
+        assert np.array_equal(m.pos_r[~sel], base.pos_r[~sel])
+        assert np.array_equal(m.pos_r[sel, 1:], base.pos_r[sel, 1:])
+        assert np.array_equal(m.pos_r[sel, 0], np.nextafter(base.pos_r[sel, 0], np.float32(np.inf)))
+    assert base.params.mu == np.float32(0.2) or abs(base.params.mu - 0.2) < 1e-7
