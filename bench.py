@@ -219,9 +219,23 @@ def oracle_sample(sc, state_pos, state_vel, seconds=15.0, max_steps=2000, thread
         if time.perf_counter() - t0 >= seconds:
             break
     el = time.perf_counter() - t0
+    one = _oracle_rate(sc, state_pos, state_vel, 1, threads=1)
     return {"value": sc.n * steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{steps} full time steps of the {sc.n}-sphere column (FP64 C oracle, {threads} OpenMP "
-                      f"threads) from the GPU state at the end of the timed region; {el:.1f} s"}
+                      f"threads) from the GPU state at the end of the timed region; {el:.1f} s",
+            "single_core_value": one["value"], "single_core_sample": one["sample"]}
+
+
+def _oracle_rate(sc, pos, vel, steps, threads=None):
+    """The FP64 oracle's particle-steps/s over `steps` whole steps from (pos, vel)."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    o = oracle.Sim(pos, vel, sc.mass, sc.bodies, sc.params, twist=sc.twist, n_threads=threads)
+    t0 = time.perf_counter()
+    o.step(steps)
+    el = time.perf_counter() - t0
+    return {"value": sc.n * steps / el, "cores": threads,
+            "sample": f"{steps} whole steps of {sc.n} spheres, {threads} OpenMP threads, {el:.2f} s"}
 
 
 def run_reference(args):
@@ -277,6 +291,19 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=120.
     from paper_2306_01369_gb300.autograd import rollout, scoop_mass
     out = {}
     t_start = time.perf_counter()
+    # small settle: 4,096 spheres in an open box, 200 steps (the oracle runs it whole)
+    ss = scenes.settle_box(n=4096, n_steps=200)
+    sim = gg.Sim.from_scene(ss)
+    sim.step(3, stream=stream)
+    sim.set_particles(ss.pos_r, ss.vel, stream=stream)
+    ms = _timed_steps(sim, 200, stream, torch)
+    sim.sync(stream)
+    sim.close()
+    orc = _oracle_rate(ss, ss.pos_r, ss.vel, 200)
+    out["small_settle"] = {"workload": "4,096 spheres settling in a 0.2 m open box, 200 steps, I=20",
+                           "particle_steps_per_s": ss.n * 200 / (ms * 1e-3), "ms_per_step": ms / 200,
+                           "oracle_particle_steps_per_s": orc["value"], "oracle_threads": orc["cores"],
+                           "oracle_sample": orc["sample"]}
     # batched: 256 environments, 8k-64k spheres each
     sc = scenes.batched_beds(n_envs=256, n_steps=steps_batched + 10)
     sim = gg.Sim.from_scene(sc)
@@ -357,7 +384,14 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=120.
         out["excavation"] = {"workload": "1,048,576 spheres, scoop + 2 free cubes + container, I=30",
                              "particle_steps_per_s": ex.n * steps_exc / (ms * 1e-3), "ms_per_step": ms / steps_exc,
                              "timed_steps": [10, 10 + steps_exc], "n_pp_last": st["n_pp"], "n_body_last": st["n_body"]}
+        pos, vel = sim.pos(), sim.vel()
         sim.close()
+        if time.perf_counter() - t_start < seconds_cap:
+            tw = {b: t[10 + steps_exc:] for b, t in ex.twist.items()}
+            ex_now = scenes.Scene(ex.name, pos, vel, ex.mass, ex.bodies, ex.params, 2, twist=tw)
+            orc = _oracle_rate(ex_now, pos, vel, 2)
+            out["excavation"].update({"oracle_particle_steps_per_s": orc["value"], "oracle_threads": orc["cores"],
+                                      "oracle_sample": orc["sample"]})
     return out
 
 
@@ -443,16 +477,16 @@ def run_gpu(args):
     # end to end through the public API with host buffers: H2D of the state, one
     # step, D2H of the new state, every step
     e2e_steps = min(args.steps, args.e2e_steps)
-    pos_h = torch.from_numpy(sim.pos()).pin_memory()
-    vel_h = torch.from_numpy(sim.vel()).pin_memory()
+    state_h = torch.empty(7 * sc.n, dtype=torch.float32).pin_memory()   # positions (n, 4), velocities (n, 3)
+    sim.read("POS_VEL", out=state_h, stream=stream)
+    pos_h, vel_h = state_h[:4 * sc.n].view(sc.n, 4), state_h[4 * sc.n:].view(sc.n, 3)
     torch.cuda.synchronize(dev)
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         sim.set_particles(pos_h, vel_h, stream=stream)
         sim.step(1, stream=stream)
-        sim.read("POS", out=pos_h.numpy(), stream=stream)
-        sim.read("VEL", out=vel_h.numpy(), stream=stream)
+        sim.read("POS_VEL", out=state_h, stream=stream)
     torch.cuda.synchronize(dev)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e_val = sum_over_ranks(float(sc.n * e2e_steps), world, dev) / e2e_s

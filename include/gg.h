@@ -17,7 +17,8 @@
  * Conventions
  *  - All arithmetic on the device is FP32.  Arrays are row-major, little-endian.
  *  - Particle arrays passed in or read back are in the caller's particle order
- *    ("id" order).  Internally the library stores particles in sorted-bucket order.
+ *    ("id" order), which is also the library's storage order; the bucket sort
+ *    produces a list of slots, not a reordered copy of the particles.
  *  - Host pointers are borrowed for the duration of the call only; the library
  *    copies what it needs.  Device pointers (flag *_on_device != 0) must be
  *    cudaMalloc'ed memory of the current device; they too are read only during the
@@ -135,7 +136,9 @@ typedef enum {
   GG_FIELD_BODY_CONTACT_GEOM = 10, /* float[n][Kb][8]: normal (body into particle), psi, contact point, 0 */
   GG_FIELD_BODY_CONTACT_IMPULSE = 11, /* float[n][Kb][3] */
   GG_FIELD_STATS = 12,         /* gg_stats */
-  GG_FIELD_STATE = 13          /* opaque checkpoint for gg_set_state (bit-exact resume) */
+  GG_FIELD_STATE = 13,         /* opaque checkpoint for gg_set_state (bit-exact resume) */
+  GG_FIELD_POS_VEL = 14        /* float[n][4] as GG_FIELD_POS, then float[n][3] as GG_FIELD_VEL: both
+                                  in one copy and, to the host, one wait */
 } gg_field;
 
 typedef struct {

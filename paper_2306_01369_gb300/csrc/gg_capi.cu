@@ -683,6 +683,7 @@ size_t gg_field_bytes(const gg_sim *s, gg_field f) {
   case GG_FIELD_BODY_CONTACT_IMPULSE: return n * s->Kb * 12;
   case GG_FIELD_STATS: return sizeof(gg_stats);
   case GG_FIELD_STATE: return sizeof(StateHeader) + n * 32 + nbt * 16 * 4;
+  case GG_FIELD_POS_VEL: return n * 28;
   }
   return 0;
 }
@@ -714,6 +715,14 @@ gg_status gg_readback(gg_sim *s, gg_field f, void *dst, size_t bytes, int dst_on
     if ((rc = target(need, &t)) != GG_OK) return rc;
     GG_CUDA(s, gg::enqueue_vel4_to_vel3(s->a.vel_id, static_cast<float *>(t), s->n, st));
     if (!dst_on_device && n) GG_CUDA(s, cudaMemcpyAsync(dst, t, need, cudaMemcpyDeviceToHost, st));
+    break;
+  case GG_FIELD_POS_VEL:
+    if (!n) break;
+    if ((rc = target(need, &t)) != GG_OK) return rc;
+    GG_CUDA(s, cudaMemcpyAsync(t, s->a.pos_id, n * 16, cudaMemcpyDeviceToDevice, st));
+    GG_CUDA(s, gg::enqueue_vel4_to_vel3(s->a.vel_id, reinterpret_cast<float *>(static_cast<char *>(t) + n * 16),
+                                        s->n, st));
+    if (!dst_on_device) GG_CUDA(s, cudaMemcpyAsync(dst, t, need, cudaMemcpyDeviceToHost, st));
     break;
   case GG_FIELD_BODY_STATE:
     if ((rc = target(need, &t)) != GG_OK) return rc;

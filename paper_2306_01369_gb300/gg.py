@@ -21,7 +21,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_CONTACT_OVERFLOW, ERR_DEVICE_TIMEOUT
 
 FIELD = {"POS": 0, "VEL": 1, "BODY_STATE": 2, "BODY_WRENCH": 3, "CELL_KEY": 4, "SORT_PERM": 5, "CELL_START": 6,
          "CONTACTS": 7, "CONTACT_GEOM": 8, "CONTACT_IMPULSE": 9, "BODY_CONTACT_GEOM": 10,
-         "BODY_CONTACT_IMPULSE": 11, "STATS": 12, "STATE": 13}
+         "BODY_CONTACT_IMPULSE": 11, "STATS": 12, "STATE": 13, "POS_VEL": 14}
 
 # exported functions: name -> (restype, argtypes)
 _P = C.c_void_p
@@ -111,7 +111,7 @@ def _ptr(x):
         assert x.is_contiguous()
         return C.c_void_p(x.data_ptr()), int(x.is_cuda)
     assert isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"]
-    return C.c_void_p(x.ctypes.data), 0
+    return C.c_void_p(x.__array_interface__["data"][0]), 0   # (ndarray.ctypes is slow to build)
 
 
 def _stream(stream):
@@ -195,6 +195,7 @@ class Sim:
         if st != OK:
             raise GGError(st, "gg_create failed")
         self.h = h
+        self._field_bytes = {}
         self.max_bodies = max_bodies
         self.K = self.gp.max_contacts or 16
         self.Kb = self.gp.max_body_contacts or 4
@@ -268,7 +269,10 @@ class Sim:
 
     # ------------------------------------------------------------------ readback
     def field_bytes(self, field):
-        return self._L.gg_field_bytes(self.h, FIELD[field])
+        nb = self._field_bytes.get(field)   # fixed for the simulation's lifetime
+        if nb is None:
+            nb = self._field_bytes[field] = self._L.gg_field_bytes(self.h, FIELD[field])
+        return nb
 
     def read(self, field, dtype=np.float32, shape=None, out=None, stream=None, check=True):
         nb = self.field_bytes(field)
@@ -287,6 +291,13 @@ class Sim:
 
     def vel(self):
         return self.read("VEL", shape=(self.n, 3))
+
+    def pos_vel(self, out=None, stream=None):
+        """Positions (n, 4) and velocities (n, 3) in one copy (and one wait, to the host):
+        `out` holds 7 n floats, positions first."""
+        buf = self.read("POS_VEL", out=out, stream=stream)
+        flat = buf.reshape(-1)
+        return flat[:4 * self.n].reshape(self.n, 4), flat[4 * self.n:].reshape(self.n, 3)
 
     def body_state(self):
         return self.read("BODY_STATE", shape=(self.n_envs * self.max_bodies, 16))

@@ -312,6 +312,30 @@ def test_checkpoint_resume_bit_exact(gg):
     assert np.array_equal(a.body_state(), b.body_state())
 
 
+def test_host_buffer_round_trip(gg, torch):
+    """POS_VEL equals POS then VEL, to host and device buffers; set_particles from the
+    same pinned buffer restores the state the step reads (the end-to-end loop)."""
+    sc = squeezed_box(3001)
+    sim = gg.Sim.from_scene(sc)
+    sim.step(7)
+    pos, vel = sim.pos(), sim.vel()
+    p2, v2 = sim.pos_vel()
+    assert np.array_equal(p2, pos) and np.array_equal(v2, vel)
+    pinned = torch.empty(7 * sc.n, dtype=torch.float32).pin_memory()
+    sim.read("POS_VEL", out=pinned)
+    assert np.array_equal(pinned.numpy()[:4 * sc.n].reshape(-1, 4), pos)
+    d = torch.empty(7 * sc.n, dtype=torch.float32, device="cuda")
+    sim.read("POS_VEL", out=d)
+    assert np.array_equal(d.cpu().numpy(), pinned.numpy())
+    other = gg.Sim.from_scene(sc)
+    other.set_particles(pinned[:4 * sc.n].view(sc.n, 4), pinned[4 * sc.n:].view(sc.n, 3))
+    ref = gg.Sim.from_scene(sc)
+    ref.step(7)
+    for s in (ref, other):
+        s.step(3)
+    assert np.array_equal(ref.pos(), other.pos()) and np.array_equal(ref.vel(), other.vel())
+
+
 # --------------------------------------------------------------------------- #
 # edge cases and errors
 # --------------------------------------------------------------------------- #
