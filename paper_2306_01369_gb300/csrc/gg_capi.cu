@@ -56,9 +56,9 @@ struct gg_sim {
   gg::LaunchShape ls{};
   uint32_t tuning_sel = 1;
   cudaStream_t cap = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  bool graph_ready = false;
+  // the step graph, captured lazily: [0] plain, [1] with the stage-timing events
+  cudaGraph_t graph[2] = {};
+  cudaGraphExec_t exec[2] = {};
   uint64_t steps = 0;
   void *staging = nullptr;
   size_t staging_bytes = 0;
@@ -126,11 +126,12 @@ gg_status read_ctrl(gg_sim *s, DevCtrl *out, cudaStream_t st) {
 }
 
 void free_graph(gg_sim *s) {
-  if (s->exec) cudaGraphExecDestroy(s->exec);
-  if (s->graph) cudaGraphDestroy(s->graph);
-  s->exec = nullptr;
-  s->graph = nullptr;
-  s->graph_ready = false;
+  for (int t = 0; t < 2; ++t) {
+    if (s->exec[t]) cudaGraphExecDestroy(s->exec[t]);
+    if (s->graph[t]) cudaGraphDestroy(s->graph[t]);
+    s->exec[t] = nullptr;
+    s->graph[t] = nullptr;
+  }
 }
 
 gg_status ensure_staging(gg_sim *s, size_t bytes) {
@@ -233,9 +234,9 @@ gg_status autotune(gg_sim *s, cudaStream_t st) {
     if ((rc = capture(s)) != GG_OK) break;
     if ((rc = restore_state(s, saved, st)) != GG_OK) break;
     float ms = 0.f;
-    cudaError_t ce = cudaGraphLaunch(s->exec, st);
+    cudaError_t ce = cudaGraphLaunch(s->exec[s->timing], st);
     if (ce == cudaSuccess) ce = cudaEventRecord(e0, st);
-    for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = cudaGraphLaunch(s->exec, st);
+    for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = cudaGraphLaunch(s->exec[s->timing], st);
     if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
     if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
     if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
@@ -257,8 +258,13 @@ gg_status autotune(gg_sim *s, cudaStream_t st) {
   return rc;
 }
 
+// Capture the step graph of the current timing mode (the other mode's graph stays).
 gg_status capture(gg_sim *s) {
-  free_graph(s);
+  const int t = s->timing ? 1 : 0;
+  if (s->exec[t]) cudaGraphExecDestroy(s->exec[t]);
+  if (s->graph[t]) cudaGraphDestroy(s->graph[t]);
+  s->exec[t] = nullptr;
+  s->graph[t] = nullptr;
   GG_CUDA(s, cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = gg::enqueue_step(s->a, s->ls, s->cap, s->timing ? s->ev : nullptr);
   cudaGraph_t g = nullptr;
@@ -268,9 +274,8 @@ gg_status capture(gg_sim *s) {
     return cuda_fail(s, e, "enqueue_step during capture");
   }
   if (e2 != cudaSuccess) return cuda_fail(s, e2, "cudaStreamEndCapture");
-  s->graph = g;
-  GG_CUDA(s, cudaGraphInstantiate(&s->exec, g, 0));
-  s->graph_ready = true;
+  s->graph[t] = g;
+  GG_CUDA(s, cudaGraphInstantiate(&s->exec[t], g, 0));
   return GG_OK;
 }
 
@@ -305,11 +310,7 @@ gg_status gg_enable_timing(gg_sim *s, int on) {
   if (!s) return GG_ERR_INVALID_ARG;
   if (on && !s->ev[0])
     for (cudaEvent_t &ev : s->ev) GG_CUDA(s, cudaEventCreate(&ev));
-  if ((bool)on != s->timing) {
-    GG_CUDA(s, cudaDeviceSynchronize());
-    s->timing = on != 0;
-    free_graph(s);
-  }
+  s->timing = on != 0;  // selects the step graph; each mode's graph is captured once
   return GG_OK;
 }
 
@@ -647,12 +648,12 @@ gg_status gg_step(gg_sim *s, uint32_t n_steps, void *stream) {
     gg_status rc = autotune(s, static_cast<cudaStream_t>(stream));
     if (rc != GG_OK) return rc;
   }
-  if (!s->graph_ready) {
+  if (!s->exec[s->timing]) {
     gg_status rc = capture(s);
     if (rc != GG_OK) return rc;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  for (uint32_t k = 0; k < n_steps; ++k) GG_CUDA(s, cudaGraphLaunch(s->exec, st));
+  for (uint32_t k = 0; k < n_steps; ++k) GG_CUDA(s, cudaGraphLaunch(s->exec[s->timing], st));
   s->steps += n_steps;
   return GG_OK;
 }
@@ -956,7 +957,7 @@ gg_status gg_backward(gg_sim *s, const float *dL_dpos, const float *dL_dvel, con
   GG_CUDA(s, cudaMemcpyAsync(d.pose_bar, pose6, sizeof(pose6), cudaMemcpyHostToDevice, st));
   GG_CUDA(s, cudaMemsetAsync(d.mubar, 0, sizeof(double), st));
   GG_CUDA(s, cudaStreamSynchronize(st));  // pose6 lives on this stack frame
-  if (!s->graph_ready) {
+  if (!s->exec[s->timing]) {
     gg_status rc = capture(s);
     if (rc != GG_OK) return rc;
   }
@@ -967,7 +968,7 @@ gg_status gg_backward(gg_sim *s, const float *dL_dpos, const float *dL_dvel, con
     if (rc != GG_OK) return rc;
     for (uint32_t k = k0; k < k1; ++k) {  // recompute the segment's step-start states
       if ((rc = save_state(s, s->ad.seg + (size_t)(k - k0) * s->ad.state_bytes, st)) != GG_OK) return rc;
-      if (k + 1 < k1) GG_CUDA(s, cudaGraphLaunch(s->exec, st));
+      if (k + 1 < k1) GG_CUDA(s, cudaGraphLaunch(s->exec[s->timing], st));
     }
     for (int k = (int)k1 - 1; k >= (int)k0; --k) {  // reverse the steps
       if ((rc = restore_state(s, s->ad.seg + (size_t)(k - k0) * s->ad.state_bytes, st)) != GG_OK) return rc;

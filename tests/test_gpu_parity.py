@@ -312,6 +312,25 @@ def test_checkpoint_resume_bit_exact(gg):
     assert np.array_equal(a.body_state(), b.body_state())
 
 
+def test_stage_timing_switch_changes_nothing(gg):
+    """Switching between the plain and the instrumented step graph leaves results
+    bit-identical; stage times are positive and cover the step."""
+    sc = squeezed_box(4096)
+    a = gg.Sim.from_scene(sc, tuning=1)
+    b = gg.Sim.from_scene(sc, tuning=1)
+    a.step(12)
+    for k in range(12):
+        b.enable_timing(k % 3 == 1)
+        b.step(1)
+        if k % 3 == 1:
+            st = b.stage_ms()
+            assert all(v > 0 for v in st.values()), st
+    b.enable_timing(False)
+    with pytest.raises(gg.GGError):
+        b.stage_ms()
+    assert np.array_equal(a.pos(), b.pos()) and np.array_equal(a.vel(), b.vel())
+
+
 def test_host_buffer_round_trip(gg, torch):
     """POS_VEL equals POS then VEL, to host and device buffers; set_particles from the
     same pinned buffer restores the state the step reads (the end-to-end loop)."""
