@@ -1,0 +1,65 @@
+"""Long-run statistics.  Trajectories of a collapsing column are chaotic, so after
+thousands of steps FP32 (CUDA path) and FP64 (oracle) agree on what the flow
+produces, not on where each sphere ends up.  The measures are the repose angle of
+the collapsed pile and its centre of mass (pile_stats.pile_statistics).
+
+Case: scenes.pile_column, 32,768 spheres, mu = 0.2, 20,000 steps (1 s), by which the
+pile has come to rest.  One run's angle varies by about 0.3 degrees (one standard
+deviation) under one-ulp perturbations of the input, so both sides are averaged over
+an ensemble of such perturbations of the same column: the oracle over members -1, 0,
+1, 2 (stored in golden/pile_column_32768.txt, written by golden/make_pile_stats.py,
+oracle only), the CUDA path over members -1 .. 6.
+
+Bars: mean repose angle within 1 degree; mean centre of mass within 1 % of the
+initial column height H0 (Euclidean distance)."""
+import os
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from gpu_helpers import need_gpu
+from pile_stats import pile_statistics
+from paper_2306_01369_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+GPU_MEMBERS = tuple(range(-1, 7))
+
+
+def golden():
+    kv = {}
+    with open(os.path.join(ROOT, "tests", "golden", "pile_column_32768.txt")) as f:
+        for line in f:
+            if line.startswith("#") or ":" not in line:
+                continue
+            k, v = line.split(":", 1)
+            kv[k.strip()] = np.array([float(t) for t in v.split()])
+    return kv
+
+
+def test_collapsed_pile_matches_oracle_statistics():
+    need_gpu()
+    from paper_2306_01369_gb300 import gg
+    angles, coms = [], []
+    for member in GPU_MEMBERS:
+        sc = S.pile_column(member)
+        sim = gg.Sim.from_scene(sc)
+        try:
+            sim.step(sc.n_steps)
+            sim.sync()
+            x = sim.pos()[:, :3].astype(np.float64)
+            v = sim.vel().astype(np.float64)
+        finally:
+            sim.close()
+        assert np.linalg.norm(v, axis=1).mean() < 1e-3, f"member {member}: the pile has not come to rest"
+        angle, com, nbins = pile_statistics(x, sc.mass, float(sc.pos_r[:, 3].max()))
+        assert nbins >= 10
+        angles.append(angle)
+        coms.append(com)
+    want = golden()
+    h0 = float(want["h0"][0])
+    angle = float(np.mean(angles))
+    com = np.mean(coms, axis=0)
+    assert abs(angle - want["angle_deg"][0]) < 1.0, (angle, want["angle_deg"][0], angles)
+    assert np.linalg.norm(com - want["com"]) <= 0.01 * h0, (com, want["com"], h0)
