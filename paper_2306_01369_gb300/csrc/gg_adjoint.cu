@@ -7,10 +7,12 @@
 // sweeps (every iterate U^s, lambda^s kept):
 //   k_adj_twins     position of each directed pair contact's twin (j -> i)
 //   k_adj_begin     U-bar^I = v-bar + dt x-bar (integrator), clear accumulators
-//   k_adj_iter  s   per contact: z-bar = J_proj^T (lambda-bar), u-bar = -w z-bar,
-//                   psi-bar, n-bar, mu-bar; tool twist partials
-//   k_adj_gather s  U-bar^s_i = sum over own contacts of (u-bar_c - u-bar_twin(c))
-//   k_adj_geom      positions through psi, normals, SDF branches; tool pose partials
+//   k_adj_iter  s   completes U-bar^{s+1} with the twin contacts' u-bar of sweep s+1
+//                   (U-bar_i = sum over own contacts of u-bar_c - u-bar_twin(c)), then per
+//                   contact: z-bar = J_proj^T (lambda-bar), u-bar = -w z-bar, psi-bar,
+//                   n-bar, mu-bar; tool twist partials
+//   k_adj_geom      completes U-bar^0; positions through psi, normals, SDF branches;
+//                   tool pose partials
 //   k_adj_tool      fixed-order sums, tool pose chain (p, R) -> twist gradient
 // No floating-point atomics: every sum is per particle in contact order, per block
 // in a fixed tree, then over blocks in index order.
@@ -122,6 +124,7 @@ __device__ __forceinline__ void block_partials(float v[kPart], float *dst) {
 }
 
 __global__ void __launch_bounds__(kAdjThreads) k_adj_twins(StepArgs a, AdjArgs d) {
+  pdl_enter();
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const size_t n = a.n;
@@ -141,6 +144,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_twins(StepArgs a, AdjArgs d
 }
 
 __global__ void __launch_bounds__(kAdjThreads) k_adj_begin(StepArgs a, AdjArgs d) {
+  pdl_enter();
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.n) return;
   const size_t n = a.n, KN = (size_t)a.K * n, KbN = (size_t)a.Kb * n;
@@ -168,14 +172,36 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_begin(StepArgs a, AdjArgs d
   }
 }
 
+// Subtracts the twin contacts' u-bar (of the sweep whose u-bar is in `ub`) from U, the
+// own-contact part of a U-bar, and adds the completed U-bar to the base velocity's.
+__device__ __forceinline__ float4 complete_ubar(const StepArgs &a, const AdjArgs &d, uint32_t i, float4 U,
+                                                const float *ub) {
+  const size_t n = a.n, KN = (size_t)a.K * n;
+  const uint32_t npp = a.ccount[i] & 0xffu;
+  for (uint32_t c = 0; c < npp; ++c) {
+    const size_t o = (size_t)c * n + i;
+    const size_t ot = (size_t)d.twin[o] * n + a.cj[o];
+    U.x -= ub[ot];
+    U.y -= ub[ot + KN];
+    U.z -= ub[ot + 2 * KN];
+  }
+  const float4 b = d.basebar[i];
+  d.basebar[i] = make_float4(b.x + U.x, b.y + U.y, b.z + U.z, 0.f);
+  return U;
+}
+
 // Reverse of sweep s (U^s, lambda^s -> lambda^{s+1}, U^{s+1}).  Ubar[cur] holds the
-// adjoint of U^{s+1}; the own-contact part of the adjoint of U^s goes to Ubar[cur ^ 1].
+// own-contact part of the adjoint of U^{s+1} (complete for s + 1 = I); the own-contact
+// part of the adjoint of U^s goes to Ubar[cur ^ 1], this sweep's u-bar to ubar[s & 1].
 __global__ void __launch_bounds__(kAdjThreads) k_adj_iter(StepArgs a, AdjArgs d, uint32_t s, int cur) {
+  pdl_enter();
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   float part[kPart] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (i < a.n) {
     const size_t n = a.n, KN = (size_t)a.K * n, KbN = (size_t)a.Kb * n;
-    const float4 Un = d.Ubar[cur][i];
+    float4 Un = d.Ubar[cur][i];
+    if (s + 1 < d.I) Un = complete_ubar(a, d, i, Un, d.ubar[(s + 1) & 1u]);
+    float *ubar = d.ubar[s & 1u];
     const float invm = a.vel_id[i].w;
     const float4 Ui = d.tp.Uh[(size_t)s * n + i];
     const float *lh = d.tp.lamh + (size_t)s * 3 * KN;
@@ -198,7 +224,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_iter(StepArgs a, AdjArgs d,
       const float3 zb = cone_adjoint(z, nv, a.mu, abar, &nb, &mub);
       st3(d.Lbar, o, KN, zb);
       const float3 ub = mul(-w, zb);
-      st3(d.ubar, o, KN, ub);
+      st3(ubar, o, KN, ub);
       S = add(S, ub);
       d.psibar[o] += w * a.ab * dot(nv, zb);
       acc3(d.nbar, o, KN, add(mul(w * bias, zb), nb));
@@ -245,26 +271,6 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_iter(StepArgs a, AdjArgs d,
   block_partials(part, d.part + ((size_t)s * d.nblk + blockIdx.x) * kPart);
 }
 
-// Adds the twin contacts' u-bar (-u-bar_twin per own contact) to the adjoint of U^s,
-// and accumulates the adjoint of the base velocity v + dt g.
-__global__ void __launch_bounds__(kAdjThreads) k_adj_gather(StepArgs a, AdjArgs d, int nxt) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  const size_t n = a.n, KN = (size_t)a.K * n;
-  float4 U = d.Ubar[nxt][i];
-  const uint32_t npp = a.ccount[i] & 0xffu;
-  for (uint32_t c = 0; c < npp; ++c) {
-    const size_t o = (size_t)c * n + i;
-    const size_t ot = (size_t)d.twin[o] * n + a.cj[o];
-    U.x -= d.ubar[ot];
-    U.y -= d.ubar[ot + KN];
-    U.z -= d.ubar[ot + 2 * KN];
-  }
-  d.Ubar[nxt][i] = U;
-  float4 b = d.basebar[i];
-  d.basebar[i] = make_float4(b.x + U.x, b.y + U.y, b.z + U.z, 0.f);
-}
-
 // gradient of a pair contact's psi and normal w.r.t. the particle's own position
 __device__ __forceinline__ float3 pair_geom_grad(const AdjArgs &d, const StepArgs &a, size_t o, size_t KN, float dist) {
   const float4 nn = a.cn[o];
@@ -275,10 +281,14 @@ __device__ __forceinline__ float3 pair_geom_grad(const AdjArgs &d, const StepArg
   return add(mul(-d.psibar[o], nv), mul(id, sub(nb, mul(nbn, nv))));
 }
 
-__global__ void __launch_bounds__(kAdjThreads) k_adj_geom(StepArgs a, AdjArgs d) {
+// Ubar[cur] holds the own-contact part of the adjoint of U^0 (completed here with
+// sweep 0's twin u-bar); then the adjoint of the step's input positions and velocities.
+__global__ void __launch_bounds__(kAdjThreads) k_adj_geom(StepArgs a, AdjArgs d, int cur) {
+  pdl_enter();
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   float part[kPart] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (i < a.n) {
+    (void)complete_ubar(a, d, i, d.Ubar[cur][i], d.ubar[0]);
     const size_t n = a.n, KN = (size_t)a.K * n, KbN = (size_t)a.Kb * n;
     const float4 pi = a.pos_id[i];
     float3 X = f3(d.xbar_s[i]);
@@ -369,23 +379,42 @@ __device__ void left_jacobian(float3 phi, float J[9]) {
     }
 }
 
-// One warp: sums the partials in a fixed order and runs the tool pose chain of step k.
-__global__ void k_adj_tool(StepArgs a, AdjArgs d, uint32_t k_local) {
-  const int lane = threadIdx.x;
+// Sums the partials in a fixed order (thread-strided over the (sweep, block) vectors,
+// a fixed butterfly in each warp, then the warps in index order), and thread 0 runs
+// the tool pose chain of step k.
+constexpr int kToolThreads = 256;
+__global__ void __launch_bounds__(kToolThreads) k_adj_tool(StepArgs a, AdjArgs d, uint32_t k_local) {
+  pdl_enter();
   double v[16];
+#pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = 0.0;
-  const uint32_t I = d.I;
-  for (uint32_t b = lane; b < d.nblk; b += 32) {
-    for (uint32_t s = 0; s < I; ++s) {
-      const float *p = d.part + ((size_t)s * d.nblk + b) * kPart;
-      for (int q = 0; q < kPart; ++q) v[q] += p[q];
-    }
-    const float *g = d.part + ((size_t)I * d.nblk + b) * kPart;
+  const uint32_t I = d.I, nb = d.nblk;
+  for (uint32_t t = threadIdx.x; t < I * nb; t += kToolThreads) {  // t = s * nblk + b
+    const float *p = d.part + (size_t)t * kPart;
+#pragma unroll
+    for (int q = 0; q < kPart; ++q) v[q] += p[q];
+  }
+  for (uint32_t b = threadIdx.x; b < nb; b += kToolThreads) {
+    const float *g = d.part + ((size_t)I * nb + b) * kPart;
+#pragma unroll
     for (int q = 0; q < 6; ++q) v[10 + q] += g[q];
   }
+#pragma unroll
   for (int q = 0; q < 16; ++q)
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-  if (lane != 0) return;
+  __shared__ double sm[kToolThreads / 32][16];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) sm[wid][q] = v[q];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int q = 0; q < 16; ++q) {
+    double t = sm[0][q];
+    for (int w = 1; w < kToolThreads / 32; ++w) t += sm[w][q];
+    v[q] = t;
+  }
   d.mubar[0] += v[9];
   if (d.tool == 0xffffffffu) return;
   const DevBody &B = a.bodies[d.tool];
@@ -419,21 +448,22 @@ inline unsigned blocks(uint32_t n) { return n ? (n + kAdjThreads - 1) / kAdjThre
 
 uint32_t adjoint_blocks(uint32_t n) { return blocks(n); }
 
+// The step's adjoint kernels, chained with programmatic dependent launch (every one
+// begins with pdl_enter); the first follows the taped forward's last sweep.
 cudaError_t enqueue_adjoint_step(const StepArgs &a, const AdjArgs &d, uint32_t k_local, cudaStream_t st) {
-  const unsigned g = blocks(a.n);
+  const dim3 g(blocks(a.n));
+  cudaError_t e;
   if (a.n) {
-    k_adj_twins<<<g, kAdjThreads, 0, st>>>(a, d);
-    k_adj_begin<<<g, kAdjThreads, 0, st>>>(a, d);
+    if ((e = launch(true, k_adj_twins, g, kAdjThreads, 0, st, a, d)) != cudaSuccess) return e;
+    if ((e = launch(true, k_adj_begin, g, kAdjThreads, 0, st, a, d)) != cudaSuccess) return e;
   }
   int cur = 0;
   for (int s = (int)d.I - 1; s >= 0; --s) {
-    k_adj_iter<<<g, kAdjThreads, 0, st>>>(a, d, (uint32_t)s, cur);
-    if (a.n) k_adj_gather<<<g, kAdjThreads, 0, st>>>(a, d, cur ^ 1);
+    if ((e = launch(true, k_adj_iter, g, kAdjThreads, 0, st, a, d, (uint32_t)s, cur)) != cudaSuccess) return e;
     cur ^= 1;
   }
-  k_adj_geom<<<g, kAdjThreads, 0, st>>>(a, d);
-  k_adj_tool<<<1, 32, 0, st>>>(a, d, k_local);
-  return cudaGetLastError();
+  if ((e = launch(true, k_adj_geom, g, kAdjThreads, 0, st, a, d, cur)) != cudaSuccess) return e;
+  return launch(true, k_adj_tool, dim3(1), kToolThreads, 0, st, a, d, k_local);
 }
 
 }  // namespace gg

@@ -870,7 +870,7 @@ gg_status gg_tape_reserve(gg_sim *s, uint32_t n_steps, uint32_t K) {
       (rc = ad_alloc(s, &s->ad.fin, s->ad.state_bytes)) || (rc = ad_alloc(s, &tp.Uh, (I + 1) * n)) ||
       (rc = ad_alloc(s, &tp.lamh, (I + 1) * 3 * KN)) || (rc = ad_alloc(s, &tp.blamh, (I + 1) * 3 * KbN)) ||
       (rc = ad_alloc(s, &d.twin, KN)) || (rc = ad_alloc(s, &d.Ubar[0], n)) || (rc = ad_alloc(s, &d.Ubar[1], n)) ||
-      (rc = ad_alloc(s, &d.ubar, 3 * KN)) || (rc = ad_alloc(s, &d.Lbar, 3 * KN)) || (rc = ad_alloc(s, &d.bLbar, 3 * KbN)) ||
+      (rc = ad_alloc(s, &d.ubar[0], 3 * KN)) || (rc = ad_alloc(s, &d.ubar[1], 3 * KN)) || (rc = ad_alloc(s, &d.Lbar, 3 * KN)) || (rc = ad_alloc(s, &d.bLbar, 3 * KbN)) ||
       (rc = ad_alloc(s, &d.psibar, KN)) || (rc = ad_alloc(s, &d.nbar, 3 * KN)) || (rc = ad_alloc(s, &d.bpsibar, KbN)) ||
       (rc = ad_alloc(s, &d.bnbar, 3 * KbN)) || (rc = ad_alloc(s, &d.bxcbar, 3 * KbN)) ||
       (rc = ad_alloc(s, &d.basebar, n)) || (rc = ad_alloc(s, &d.xbar_s, n)) || (rc = ad_alloc(s, &d.xbar, n)) ||

@@ -317,7 +317,7 @@ struct AdjArgs {
   uint32_t nblk;           // blocks of the per-particle adjoint kernels
   uint32_t *twin;          // [K][n] position of contact (j -> i) in j's list
   float4 *Ubar[2];         // adjoint of U^{s+1} / U^s
-  float *ubar;             // [3][K][n] adjoint of each pair contact's relative velocity
+  float *ubar[2];          // [3][K][n] adjoint of each pair contact's relative velocity, by sweep parity
   float *Lbar, *bLbar;     // [3][K][n], [3][Kb][n] adjoint of lambda^s (carried down the sweeps)
   float *psibar, *nbar;    // [K][n], [3][K][n]
   float *bpsibar, *bnbar, *bxcbar;  // [Kb][n], [3][Kb][n], [3][Kb][n]

@@ -6,6 +6,26 @@
 
 namespace gg {
 
+// One kernel launch.  With `pdl` the launch asks for programmatic serialization with
+// the stream's previous kernel; the kernel must begin with pdl_enter (it then still
+// waits for that kernel's completion before touching memory; what overlaps is its
+// launch and the predecessor's tail).  Only kernels follow kernels with pdl set.
+template <typename... P, typename... A>
+inline cudaError_t launch(bool pdl, void (*k)(P...), dim3 grid, unsigned block, size_t smem, cudaStream_t st,
+                          A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Launch shape of the step; any choice gives bit-identical results.
 struct LaunchShape {
   uint32_t iters;       // projected-Jacobi iterations

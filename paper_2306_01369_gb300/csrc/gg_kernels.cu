@@ -1064,34 +1064,13 @@ uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls) {
   return k;
 }
 
-// One kernel launch of the step.  With `pdl` the launch asks for programmatic
-// serialization with the stream's previous kernel (every step kernel begins with
-// pdl_enter, so it still waits for that kernel's completion before touching memory;
-// what overlaps is its launch and the predecessor's tail).
-template <typename... P, typename... A>
-static cudaError_t launch(bool pdl, void (*k)(P...), dim3 grid, unsigned block, size_t smem, cudaStream_t st,
-                          A... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, k, args...);
-}
-
 cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st, cudaEvent_t *ev, const Tape *tp) {
   cudaError_t e;
   const uint32_t nbt = a.n_envs * a.maxb;
   const uint32_t nk = a.n > nbt ? a.n : nbt;
   // Programmatic launches chain the kernels of the step; the first kernel after an
-  // event record, a copy or the previous step is launched normally.  The taped
-  // forward keeps plain launches (copies sit between its stages).
-  const bool allow_pdl = !tp;
+  // event record, a copy or the previous step is launched normally.
+  const bool allow_pdl = true;
   bool after_kernel = false;
 #define GG_LAUNCH(kern, grid, block, smem, ...)                                                       \
   do {                                                                                                \
@@ -1126,6 +1105,7 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
     if ((e = cudaMemcpyAsync(tp->Uh, a.U[0], sizeof(float4) * a.n, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(tp->lamh, 0, sizeof(float) * 3 * (size_t)a.K * a.n, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(tp->blamh, 0, sizeof(float) * 3 * (size_t)a.Kb * a.n, st)) != cudaSuccess) return e;
+    after_kernel = false;
   }
   const Tape none{};
   if (!tp && ls.fused_grid && !a.F && a.n) {
