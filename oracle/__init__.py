@@ -46,7 +46,8 @@ class OrcParams(C.Structure):
 class OrcBody(C.Structure):
     _fields_ = [("kind", C.c_int32), ("is_free", C.c_int32), ("shape", C.c_double * 12), ("pos", C.c_double * 3),
                 ("quat", C.c_double * 4), ("lin_vel", C.c_double * 3), ("ang_vel", C.c_double * 3),
-                ("mass", C.c_double), ("inertia", C.c_double * 3)]
+                ("mass", C.c_double), ("inertia", C.c_double * 3), ("grid", C.c_void_p),
+                ("grid_dims", C.c_uint32 * 3)]
 
 
 class OrcStats(C.Structure):
@@ -132,6 +133,12 @@ def make_bodies(bodies) -> C.Array:
         for a in range(4):
             o.quat[a] = _f32(b.quat[a])
         o.mass = _f32(b.mass)
+        g = getattr(b, "grid", None)
+        if g is not None:   # the caller keeps b (and so the samples) alive while arr is used
+            assert g.values.dtype == np.float32 and g.values.flags["C_CONTIGUOUS"]
+            o.grid = g.values.ctypes.data
+            nz, ny, nx = g.values.shape
+            o.grid_dims[0], o.grid_dims[1], o.grid_dims[2] = nx, ny, nz
     return arr
 
 

@@ -78,6 +78,8 @@ typedef struct {
   float s[12];
   float p[3];
   float R[9]; /* row-major, body -> world */
+  const float *grid;
+  uint32_t gn[3];
 } bodyf;
 
 static void rot_f32(const float *q, float *R) {
@@ -103,6 +105,8 @@ static void body_to_f32(const orc_body *b, bodyf *o) {
   for (int k = 0; k < 3; ++k) o->p[k] = (float)b->pos[k];
   for (int k = 0; k < 4; ++k) q[k] = (float)b->quat[k];
   rot_f32(q, o->R);
+  o->grid = b->grid;
+  for (int k = 0; k < 3; ++k) o->gn[k] = b->grid_dims[k];
 }
 
 /* y = R^T (x - p), each row summed left to right. */
@@ -140,6 +144,46 @@ static float box_f32(const float *y, const float *h, int *branch) {
   else
     *branch = 2;
   return f;
+}
+
+/* Gridded SDF (Sec. II-C): trilinear interpolation of the samples around y.
+ * FP32, in this order: u_k = (y_k - o_k) * float(1/h); cell i_k = floor(u_k), at most
+ * n_k - 2; t_k = u_k - i_k; lerp(a, b, t) = a + t (b - a) along x (4 edges), then y,
+ * then z.  Outside the sampled box [0, n_k - 1] (or NaN): no contact (+inf), branch -1;
+ * inside, the branch is the cell's linear index. */
+static float lerp_f32(float a, float b, float t) {
+  float d = b - a;
+  float m = t * d;
+  return a + m;
+}
+
+static float grid_f32(const bodyf *b, const float *y, int *branch) {
+  const float ih = (float)(1.0 / (double)b->s[3]);
+  int32_t i[3];
+  float t[3];
+  for (int k = 0; k < 3; ++k) {
+    float d = y[k] - b->s[k];
+    float u = d * ih;
+    float top = (float)(b->gn[k] - 1);
+    if (!(u >= 0.0f && u <= top)) {
+      *branch = -1;
+      return INFINITY;
+    }
+    int32_t c = (int32_t)floorf(u);
+    if (c > (int32_t)b->gn[k] - 2) c = (int32_t)b->gn[k] - 2;
+    i[k] = c;
+    t[k] = u - (float)c;
+  }
+  const size_t nx = b->gn[0], nxy = (size_t)b->gn[0] * b->gn[1];
+  const float *v = b->grid + (size_t)i[2] * nxy + (size_t)i[1] * nx + (size_t)i[0];
+  float c00 = lerp_f32(v[0], v[1], t[0]);
+  float c10 = lerp_f32(v[nx], v[nx + 1], t[0]);
+  float c01 = lerp_f32(v[nxy], v[nxy + 1], t[0]);
+  float c11 = lerp_f32(v[nxy + nx], v[nxy + nx + 1], t[0]);
+  float c0 = lerp_f32(c00, c10, t[1]);
+  float c1 = lerp_f32(c01, c11, t[1]);
+  *branch = (int)((size_t)i[2] * nxy + (size_t)i[1] * nx + (size_t)i[0]);
+  return lerp_f32(c0, c1, t[2]);
 }
 
 /* SDF of body b at body-frame point y, FP32, with the active branch. */
@@ -180,6 +224,8 @@ static float sdf_f32(const bodyf *b, const float *y, int *branch) {
     *branch = br;
     return f;
   }
+  case ORC_GRID:
+    return grid_f32(b, y, branch);
   default:
     *branch = -1;
     return INFINITY;
@@ -232,6 +278,43 @@ static double box64(const double *y, const double *h, int branch, double *g) {
   return q[branch];
 }
 
+/* Gridded SDF in FP64 on the cell chosen in FP32: the trilinear interpolant of that
+ * cell's eight samples, sum over corners v_abc w_a(t_x) w_b(t_y) w_c(t_z) with
+ * w_0(t) = 1 - t, w_1(t) = t, t_k = (y_k - o_k) / h - i_k, and its unit gradient
+ * (d f / d y_k = (1/h) d f / d t_k); a zero gradient gives +z. */
+static double grid64(const orc_body *b, const double *y, int cell, double *g) {
+  const uint32_t nx = b->grid_dims[0], ny = b->grid_dims[1];
+  const size_t nxy = (size_t)nx * ny;
+  const int32_t i[3] = {(int32_t)((size_t)cell % nx), (int32_t)(((size_t)cell / nx) % ny), (int32_t)((size_t)cell / nxy)};
+  const double h = (double)(float)b->shape[3];
+  double t[3], w[3][2], dw[2] = {-1.0, 1.0};
+  for (int k = 0; k < 3; ++k) {
+    t[k] = (y[k] - (double)(float)b->shape[k]) / h - (double)i[k];
+    w[k][0] = 1.0 - t[k];
+    w[k][1] = t[k];
+  }
+  const float *v = b->grid + (size_t)cell;
+  double f = 0.0, df[3] = {0.0, 0.0, 0.0};
+  for (int c = 0; c < 2; ++c)
+    for (int bb = 0; bb < 2; ++bb)
+      for (int a = 0; a < 2; ++a) {
+        const double s = (double)v[(size_t)c * nxy + (size_t)bb * nx + (size_t)a];
+        f += s * w[0][a] * w[1][bb] * w[2][c];
+        df[0] += s * dw[a] * w[1][bb] * w[2][c];
+        df[1] += s * w[0][a] * dw[bb] * w[2][c];
+        df[2] += s * w[0][a] * w[1][bb] * dw[c];
+      }
+  const double gn = sqrt(dot3(df, df));
+  if (gn > 0.0) {
+    for (int k = 0; k < 3; ++k) g[k] = df[k] / gn;
+  } else {
+    g[0] = 0.0;
+    g[1] = 0.0;
+    g[2] = 1.0;
+  }
+  return f;
+}
+
 static double sdf64_branch(const orc_body *b, const double *y, int branch, double *g) {
   switch (b->kind) {
   case ORC_PLANE:
@@ -258,6 +341,9 @@ static double sdf64_branch(const orc_body *b, const double *y, int branch, doubl
     for (int k = 0; k < 3; ++k) g[k] = gn[branch][k];
     return w[branch];
   }
+  case ORC_GRID:
+    if (branch >= 0) return grid64(b, y, branch, g);
+    break;
   }
   g[0] = g[1] = g[2] = 0;
   return INFINITY;

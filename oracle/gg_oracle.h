@@ -29,18 +29,21 @@ typedef struct {
   uint32_t hash_size; /* n_h of Eq. 6 */
 } orc_params;
 
-enum { ORC_PLANE = 0, ORC_BOX = 1, ORC_BOX_MINUS_BOX = 2, ORC_OPEN_BOX = 3 };
+enum { ORC_PLANE = 0, ORC_BOX = 1, ORC_BOX_MINUS_BOX = 2, ORC_OPEN_BOX = 3, ORC_GRID = 4 };
 
 typedef struct {
   int32_t kind;       /* ORC_* */
   int32_t is_free;    /* 0: kinematic (driven by its twist), 1: free rigid body */
-  double shape[12];   /* BOX/OPEN_BOX: half extents [0..2]; BOX_MINUS_BOX: A half [0..2], B half [3..5], B centre [6..8] */
+  double shape[12];   /* BOX/OPEN_BOX: half extents [0..2]; BOX_MINUS_BOX: A half [0..2], B half [3..5], B centre [6..8];
+                         GRID: body-frame position of sample (0, 0, 0) [0..2], sample spacing h [3] */
   double pos[3];      /* world position of the body origin */
   double quat[4];     /* orientation (w, x, y, z), body -> world */
   double lin_vel[3];  /* world-frame twist: velocity of the origin ... */
   double ang_vel[3];  /* ... and angular velocity */
   double mass;        /* free bodies only */
   double inertia[3];  /* free bodies only: principal moments in the body frame */
+  const float *grid;  /* GRID: SDF samples float[nz][ny][nx], x fastest (Sec. II-C gridded SDF) */
+  uint32_t grid_dims[3]; /* GRID: nx, ny, nz (each >= 2) */
 } orc_body;
 
 typedef struct {

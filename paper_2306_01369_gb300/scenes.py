@@ -26,6 +26,7 @@ PLANE = 0          # half-space below the body's local z = 0 plane
 BOX = 1            # solid box, shape[0:3] = half extents
 BOX_MINUS_BOX = 2  # box A (shape[0:3]) minus box B (half extents shape[3:6], centre shape[6:9])
 OPEN_BOX = 3       # container: inside of a box with no lid, shape[0:3] = half extents
+GRID = 4           # SDF sampled on a regular grid (trilinear), samples in Body.grid
 
 DENSITY = 2500.0   # kg/m^3, used when a scene gives no density
 
@@ -47,6 +48,19 @@ def uniform(seed: int, count: int) -> np.ndarray:
 
 
 @dataclass
+class Grid:
+    """Samples of a signed distance function on a regular grid (body frame):
+    values[k, j, i] = f(origin + h (i, j, k)), float32, x fastest."""
+    values: np.ndarray
+    origin: tuple
+    spacing: float
+
+    def __post_init__(self):
+        self.values = np.ascontiguousarray(self.values, np.float32)
+        assert self.values.ndim == 3 and min(self.values.shape) >= 2
+
+
+@dataclass
 class Body:
     kind: int
     shape: tuple = (0.0,) * 12
@@ -57,8 +71,12 @@ class Body:
     is_free: int = 0
     mass: float = 0.0
     inertia: tuple = (0.0, 0.0, 0.0)     # principal moments in the body frame
+    grid: Grid = None                    # GRID bodies: the sampled SDF
 
     def shape12(self):
+        if self.grid is not None:        # GRID: origin of the samples, spacing
+            o = self.grid.origin
+            return (float(o[0]), float(o[1]), float(o[2]), float(self.grid.spacing)) + (0.0,) * 8
         s = list(self.shape) + [0.0] * (12 - len(self.shape))
         return tuple(float(v) for v in s[:12])
 

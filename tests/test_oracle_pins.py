@@ -500,3 +500,120 @@ def test_fast_remainder_identity():
             x &= (1 << 32) - 1
             low = (magic * x) & M64
             assert (low * d) >> 64 == x % d, (x, d)
+
+
+# --------------------------------------------------------------------------- #
+# gridded SDF (Sec. II-C: samples on a regular grid, trilinear interpolation)
+# --------------------------------------------------------------------------- #
+
+def _grid_body(f, origin, h, dims, pos=(0.0, 0.0, 0.0), quat=(1.0, 0.0, 0.0, 0.0)):
+    """GRID body sampling f (body frame, vectorised over (..., 3)) at origin + h (i, j, k)."""
+    nx, ny, nz = dims
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    y = np.stack([origin[0] + h * i, origin[1] + h * j, origin[2] + h * k], axis=-1)
+    vals = f(y).astype(F32)
+    return S.Body(kind=S.GRID, pos=pos, quat=quat, grid=S.Grid(vals, origin, h))
+
+
+def test_grid_sdf_exact_on_linear_fields(orc):
+    """Trilinear interpolation reproduces a linear function exactly (dyadic samples,
+    exact in float32), and its unit gradient is the field's direction."""
+    rng = np.random.default_rng(11)
+    for a, c in (((0.25, -0.5, 0.75), 0.125), ((0.0, 0.0, 1.0), -0.0625), ((-1.0, 0.5, 0.0), 0.25)):
+        a = np.array(a)
+        body = _grid_body(lambda y: y @ a + c, (-0.5, -0.25, -0.125), 1.0 / 64, (65, 33, 17))
+        for _ in range(40):
+            y = rng.uniform([-0.49, -0.24, -0.12], [0.49, 0.24, 0.124])
+            f, n = orc.sdf(body, y)
+            assert abs(f - (y @ a + c)) < 1e-12, (y, f)
+            assert np.allclose(n, a / np.linalg.norm(a), atol=1e-12)
+
+
+def test_grid_sdf_interpolates_its_samples(orc):
+    """At the sample points the interpolant equals the samples, which for a baked box
+    are the box's closed-form SDF rounded to float32; a rotated, translated body is
+    queried in its own frame."""
+    h = 1.0 / 128
+    half = np.array([0.03, 0.02, 0.01])
+
+    def box(y):
+        q = np.abs(y) - half
+        return np.linalg.norm(np.maximum(q, 0.0), axis=-1) + np.minimum(q.max(axis=-1), 0.0)
+
+    origin = (-0.0625, -0.046875, -0.03125)
+    dims = (17, 13, 9)
+    rv = np.array([0.2, -0.1, 0.3])
+    body = _grid_body(box, origin, h, dims, pos=(0.25, -0.125, 0.5), quat=S._quat_from_rotvec(rv))
+    qq = np.array([F32(v) for v in body.quat], np.float64)
+    qq /= np.linalg.norm(qq)
+    a_, b_, c_, d_ = qq
+    R = np.array([[1 - 2 * (c_ * c_ + d_ * d_), 2 * (b_ * c_ - a_ * d_), 2 * (b_ * d_ + a_ * c_)],
+                  [2 * (b_ * c_ + a_ * d_), 1 - 2 * (b_ * b_ + d_ * d_), 2 * (c_ * d_ - a_ * b_)],
+                  [2 * (b_ * d_ - a_ * c_), 2 * (c_ * d_ + a_ * b_), 1 - 2 * (b_ * b_ + c_ * c_)]])
+    p = np.array([F32(v) for v in body.pos], np.float64)
+    rng = np.random.default_rng(12)
+    for _ in range(30):
+        i, j, k = rng.integers(0, dims[0]), rng.integers(0, dims[1]), rng.integers(0, dims[2])
+        y = np.array([origin[0] + h * i, origin[1] + h * j, origin[2] + h * k])
+        f, _ = orc.sdf(body, p + R @ y)
+        assert abs(f - float(body.grid.values[k, j, i])) < 1e-9
+        assert abs(f - box(y)) < 1e-7
+
+
+def test_grid_sdf_error_within_trilinear_bound(orc):
+    """For f with bounded second derivatives the trilinear interpolant errs by at most
+    (h^2 / 8) (|f_xx| + |f_yy| + |f_zz|); for a sphere's SDF |y| - R that is
+    3 h^2 / (8 rho) at distance rho >= rho_min from the centre.  Halving h must cut the
+    error by about four."""
+    Rs = 0.05
+
+    def sph(y):
+        return np.linalg.norm(y, axis=-1) - Rs
+
+    rng = np.random.default_rng(13)
+    pts = rng.normal(size=(300, 3))
+    pts = pts / np.linalg.norm(pts, axis=1)[:, None] * rng.uniform(0.04, 0.07, (300, 1))
+    errs, nerrs = [], []
+    for h in (1.0 / 64, 1.0 / 128):
+        n = int(round(0.16 / h)) + 1
+        body = _grid_body(sph, (-0.08, -0.08, -0.08), h, (n, n, n))
+        e = ne = 0.0
+        for y in pts:
+            f, nrm = orc.sdf(body, y)
+            rho = np.linalg.norm(y)
+            err = abs(f - sph(y))
+            assert err <= 3 * h * h / (8 * 0.03) + 1e-7, (h, err)   # cell corners within 0.03 of the centre at most
+            e = max(e, err)
+            ne = max(ne, np.linalg.norm(nrm - y / rho))
+        errs.append(e)
+        nerrs.append(ne)
+    assert errs[1] < errs[0] / 3.0          # second order in h
+    assert nerrs[1] < nerrs[0] / 1.7        # the normal: first order
+    assert nerrs[1] < 0.15
+
+
+def test_grid_outside_the_samples_is_not_in_contact(orc):
+    body = _grid_body(lambda y: y[..., 2], (-0.09375, -0.09375, -0.09375), 1.0 / 32, (7, 7, 7))
+    f, _ = orc.sdf(body, np.array([0.0, 0.0, 0.0]))
+    assert abs(f) < 1e-12
+    for y in ([0.2, 0.0, 0.0], [0.0, -0.11, 0.0], [0.0, 0.0, 0.095]):
+        f, _ = orc.sdf(body, np.array(y))
+        assert f == math.inf
+
+
+def test_sphere_rests_on_a_grid_plane(orc):
+    """A sphere resting on a GRID body that samples the plane z = 0 behaves as on the
+    closed-form plane: penetration decays as (1 - alpha)^k (Baumgarte, Sec. II-A)."""
+    r = F32(0.005)
+    ground = _grid_body(lambda y: y[..., 2], (-0.0625, -0.0625, -0.0625), 1.0 / 64, (9, 9, 9))
+    psi0 = 1e-6
+    z0 = F32(float(r) - psi0)
+    pr = np.array([[0.01, -0.02, z0, r]], F32)
+    p = S.Params(dt=1e-4, mu=0.5, alpha=0.2, pja_iters=20)
+    s = orc.Sim(pr, np.zeros((1, 3), F32), np.array([0.01], F32), [ground], p)
+    a = float(F32(0.2))
+    psi = float(r) - float(z0)
+    for k in range(1, 9):
+        s.step(1)
+        want = (1.0 - a) ** k * psi
+        assert abs((float(r) - s.x[0, 2]) - want) < 1e-13, k
