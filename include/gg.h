@@ -62,14 +62,17 @@ typedef enum {
   GG_ERR_NO_DEVICE = 8          /* no usable CUDA device */
 } gg_status;
 
-/* Rigid-body geometry, as closed-form SDFs (Sec. II-C).  Body frame: origin at pos. */
+/* Rigid-body geometry as signed distance functions (Sec. II-C): closed forms, or
+ * samples on a regular grid.  Body frame: origin at pos. */
 typedef enum {
   GG_BODY_PLANE = 0,          /* half-space z_body <= 0; surface z_body = 0, normal +z_body */
   GG_BODY_BOX = 1,            /* solid box; shape[0..2] = half extents */
   GG_BODY_BOX_MINUS_BOX = 2,  /* box A (half extents shape[0..2]) minus box B (half extents
                                  shape[3..5], centre shape[6..8]): an excavation scoop */
-  GG_BODY_OPEN_BOX = 3        /* container: inside of a box with no lid, walls at x = +-shape[0],
+  GG_BODY_OPEN_BOX = 3,       /* container: inside of a box with no lid, walls at x = +-shape[0],
                                  y = +-shape[1], floor at z = -shape[2]; walls are unbounded in +z */
+  GG_BODY_GRID = 4            /* SDF sampled on a regular grid, trilinear interpolation (Sec. II-C);
+                                 samples from gg_set_body_grid (shape ignored).  Kinematic only. */
 } gg_body_kind;
 
 typedef struct {
@@ -178,6 +181,21 @@ GG_API gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const
 /* Replace the bodies of environment env (n_bodies <= max_bodies; host array).
  * Synchronous with respect to previously enqueued steps. */
 GG_API gg_status gg_set_bodies(gg_sim *sim, uint32_t env, uint32_t n_bodies, const gg_body *bodies);
+
+/*
+ * Samples of GG_BODY_GRID body `body` of environment env (Sec. II-C): values =
+ * float[dims[2]][dims[1]][dims[0]], x fastest, values[k][j][i] = f at body-frame point
+ * origin + spacing (i, j, k); dims >= 2 each, spacing > 0.  A particle's SDF value is
+ * the trilinear interpolant of its cell's eight samples, evaluated in FP32 in this
+ * order: u = (y - origin) * float(1 / spacing) per axis, cell = floor(u) (at most
+ * dims - 2), t = u - cell, lerp(a, b, t) = a + t (b - a) along x, then y, then z; the
+ * normal is the interpolant's unit gradient (+z where it vanishes).  Points outside
+ * [origin, origin + spacing (dims - 1)] are not in contact, so the samples must
+ * extend at least r_max beyond the geometry.  The library copies the samples
+ * (allocating device memory outside gg_step); gg_set_bodies drops them.
+ */
+GG_API gg_status gg_set_body_grid(gg_sim *sim, uint32_t env, uint32_t body, const uint32_t dims[3],
+                                  const float origin[3], float spacing, const float *values, int on_device);
 
 /*
  * Prescribe the twist of kinematic body `body` of environment env for the next

@@ -89,7 +89,30 @@ __device__ __forceinline__ float3 box_grad_adj(float3 y, const float *h, int bra
   return make_float3(a0 * (gb.x - g.x * gg) / mn, a1 * (gb.y - g.y * gg) / mn, a2 * (gb.z - g.z * gg) / mn);
 }
 
+// Gridded SDF: the unit gradient n = g / |g| of the trilinear interpolant has
+// dn/dy = (I - n n^T) H / |g|, H the interpolant's Hessian in y (only its mixed terms
+// are non-zero); H is symmetric, so (dn/dy)^T gb = H (I - n n^T) gb / |g|.
+__device__ __forceinline__ float3 grid_grad_adj(const DevBody &b, float3 y, int branch, float3 gb) {
+  float3 hm;
+  const float ih = b.shape[4];
+  const float3 g = mul(ih, grid_dt(b, y, branch, &hm));
+  const float gl = sqrtf(dot(g, g));
+  if (!(gl > 0.f)) return make_float3(0.f, 0.f, 0.f);
+  const float3 n = mul(1.0f / gl, g);
+  const float3 p = sub(gb, mul(dot(n, gb), n));
+  const float s = ih * ih / gl;
+  return make_float3(s * (hm.x * p.y + hm.y * p.z), s * (hm.x * p.x + hm.z * p.z), s * (hm.y * p.x + hm.z * p.y));
+}
+
+// d f / d y (body frame): the unit normal of a true SDF; for samples on a grid, the
+// interpolant's own gradient (not unit length in general).
+__device__ __forceinline__ float3 body_fgrad(const DevBody &b, float3 y, int branch) {
+  if (b.kind == 4) return mul(b.shape[4], grid_dt(b, y, branch, nullptr));
+  return body_grad(b, y, branch);
+}
+
 __device__ __forceinline__ float3 body_grad_adj(const DevBody &b, float3 y, int branch, float3 gb) {
+  if (b.kind == 4) return grid_grad_adj(b, y, branch, gb);
   if (b.kind == 1) return box_grad_adj(y, b.shape, branch, gb);
   if (b.kind == 2) {
     if (branch < 4) return box_grad_adj(y, b.shape, branch, gb);
@@ -320,10 +343,11 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_geom(StepArgs a, AdjArgs d,
       (void)body_sdf(B, y, &br);
       const float3 yb = body_grad_adj(B, y, br, rotT(B.R, nb));
       const float3 Ryb = rot_apply(B.R, yb);
-      X = add(X, add(mul(fb, nv), Ryb));
+      const float3 gw = rot_apply(B.R, body_fgrad(B, y, br));  // d f / d x
+      X = add(X, add(mul(fb, gw), Ryb));
       if (gb == d.tool) {
-        const float3 pb = mul(-1.f, add(mul(fb, nv), Ryb));
-        const float3 rb = add(add(mul(fb, cross(nv, dvec)), cross(nv, nb)), cross(Ryb, dvec));
+        const float3 pb = mul(-1.f, add(mul(fb, gw), Ryb));
+        const float3 rb = add(add(mul(fb, cross(gw, dvec)), cross(nv, nb)), cross(Ryb, dvec));
         part[0] += pb.x;
         part[1] += pb.y;
         part[2] += pb.z;

@@ -1,7 +1,8 @@
 // gg_capi.cu -- host implementation of the C ABI declared in include/gg.h.
 //
 // All device memory is allocated by gg_create / gg_create_batch (and by
-// gg_set_trajectory for its table, and lazily by the first readback that needs a
+// gg_set_trajectory for its table, gg_set_body_grid for its samples, and lazily by
+// the first readback that needs a
 // staging buffer); gg_step allocates nothing.  A time step is captured once into
 // a CUDA graph and replayed on the caller's stream.
 #include <cuda_runtime.h>
@@ -49,6 +50,7 @@ struct gg_sim {
   std::vector<DevEnv> envs;
   std::vector<uint32_t> nbodies;
   std::vector<float *> traj;  // per body slot
+  std::vector<float *> grids; // per body slot: samples of GRID bodies
   std::vector<uint32_t> fgb;  // free-body slot -> global body index (~0u when unused)
   uint32_t F = 0, Lcap = 0;
   std::vector<void *> allocs;
@@ -336,6 +338,8 @@ void gg_destroy(gg_sim *sim) {
   for (void *p : sim->ad.allocs) cudaFree(p);
   for (float *t : sim->traj)
     if (t) cudaFree(t);
+  for (float *g : sim->grids)
+    if (g) cudaFree(g);
   if (sim->staging) cudaFree(sim->staging);
   delete sim;
 }
@@ -453,6 +457,7 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
   const uint32_t nbt = n_envs * s->maxb;
   s->nbodies.assign(n_envs, 0);
   s->traj.assign(nbt, nullptr);
+  s->grids.assign(nbt, nullptr);
 
   // device buffers, all at capacity
   StepArgs &a = s->a;
@@ -544,7 +549,9 @@ gg_status gg_set_bodies(gg_sim *s, uint32_t env, uint32_t n_bodies, const gg_bod
   for (uint32_t b = 0; b < n_bodies; ++b) {
     const gg_body &in = bodies[b];
     DevBody &o = hb[b];
-    if (in.kind > GG_BODY_OPEN_BOX) return fail(s, GG_ERR_INVALID_ARG, "unknown body kind");
+    if (in.kind > GG_BODY_GRID) return fail(s, GG_ERR_INVALID_ARG, "unknown body kind");
+    if (in.kind == GG_BODY_GRID && in.is_free)
+      return fail(s, GG_ERR_UNSUPPORTED, "GRID bodies are kinematic (free bodies are boxes)");
     if (in.is_free && !(in.mass > 0.f && in.inertia[0] > 0.f && in.inertia[1] > 0.f && in.inertia[2] > 0.f))
       return fail(s, GG_ERR_INVALID_ARG, "a free body needs a positive mass and inertia");
     double qn = std::sqrt((double)in.quat[0] * in.quat[0] + (double)in.quat[1] * in.quat[1] +
@@ -586,6 +593,9 @@ gg_status gg_set_bodies(gg_sim *s, uint32_t env, uint32_t n_bodies, const gg_bod
     float *&t = s->traj[env * s->maxb + b];
     if (t) cudaFree(t);
     t = nullptr;
+    float *&g = s->grids[env * s->maxb + b];
+    if (g) cudaFree(g);
+    g = nullptr;
   }
   GG_CUDA(s, cudaMemcpy(s->a.bodies + (size_t)env * s->maxb, hb.data(), sizeof(DevBody) * s->maxb,
                         cudaMemcpyHostToDevice));
@@ -622,6 +632,42 @@ gg_status gg_set_trajectory(gg_sim *s, uint32_t env, uint32_t body, uint32_t n_s
   GG_CUDA(s, cudaMemcpy(&db->traj, &tp, sizeof(tp), cudaMemcpyHostToDevice));
   GG_CUDA(s, cudaMemcpy(&db->traj_len, &n_steps, sizeof(uint32_t), cudaMemcpyHostToDevice));
   GG_CUDA(s, cudaMemcpy(&db->traj_start, &c.step, sizeof(uint32_t), cudaMemcpyHostToDevice));
+  return GG_OK;
+}
+
+gg_status gg_set_body_grid(gg_sim *s, uint32_t env, uint32_t body, const uint32_t dims[3], const float origin[3],
+                           float spacing, const float *values, int on_device) {
+  if (!s) return GG_ERR_INVALID_ARG;
+  if (env >= s->n_envs || body >= s->nbodies[env] || !dims || !origin || !values)
+    return fail(s, GG_ERR_INVALID_ARG, "gg_set_body_grid: bad environment, body or pointer");
+  if (dims[0] < 2 || dims[1] < 2 || dims[2] < 2 || !(spacing > 0.f) || !std::isfinite(spacing) ||
+      !std::isfinite(origin[0]) || !std::isfinite(origin[1]) || !std::isfinite(origin[2]))
+    return fail(s, GG_ERR_INVALID_ARG, "gg_set_body_grid: dims must be >= 2 and spacing > 0");
+  const size_t count = (size_t)dims[0] * dims[1] * dims[2];
+  if (count > ((size_t)1 << 31)) return fail(s, GG_ERR_INVALID_ARG, "gg_set_body_grid: more than 2^31 samples");
+  const uint32_t gb = env * s->maxb + body;
+  GG_CUDA(s, cudaDeviceSynchronize());
+  DevBody hb;
+  GG_CUDA(s, cudaMemcpy(&hb, s->a.bodies + gb, sizeof(DevBody), cudaMemcpyDeviceToHost));
+  if (hb.kind != GG_BODY_GRID) return fail(s, GG_ERR_INVALID_ARG, "gg_set_body_grid: the body is not GG_BODY_GRID");
+  float *&g = s->grids[gb];
+  if (g) cudaFree(g);
+  g = nullptr;
+  cudaError_t e = cudaMalloc(&g, sizeof(float) * count);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    g = nullptr;
+    return fail(s, GG_ERR_OOM, "grid allocation failed");
+  }
+  GG_CUDA(s, cudaMemcpy(g, values, sizeof(float) * count, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+  for (int k = 0; k < 3; ++k) {
+    hb.shape[k] = origin[k];
+    hb.gn[k] = dims[k];
+  }
+  hb.shape[3] = spacing;
+  hb.shape[4] = (float)(1.0 / (double)spacing);
+  hb.grid = g;
+  GG_CUDA(s, cudaMemcpy(s->a.bodies + gb, &hb, sizeof(DevBody), cudaMemcpyHostToDevice));
   return GG_OK;
 }
 

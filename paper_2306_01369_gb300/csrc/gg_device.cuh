@@ -60,6 +60,10 @@ struct DevBody {
   uint32_t traj_start;  // step index at which traj[0] applies
   uint32_t env, active;
   uint32_t fid;         // free bodies: index into the free-body arrays
+  // kind 4 (grid): samples float[gn[2]][gn[1]][gn[0]]; shape[0..2] origin, shape[3]
+  // spacing h, shape[4] float(1 / h)
+  const float *grid;
+  uint32_t gn[3];
 };
 
 // Programmatic dependent launch (sm_90 and later).  A kernel launched with programmatic
@@ -218,6 +222,96 @@ __device__ __forceinline__ float box_sdf(float3 y, const float *h, int *branch) 
   return f;
 }
 
+// Gridded SDF (Sec. II-C): trilinear interpolation of the eight samples of y's cell, in
+// FP32 and in this order: u = (y - o) * float(1/h); cell = floor(u) (at most n - 2);
+// t = u - cell; lerp(a, b, t) = a + t (b - a) along x (four edges), then y, then z.
+// Outside the sampled box (or NaN): +inf, branch -1; inside, branch = the cell index.
+__device__ __forceinline__ float lerp_rn(float a, float b, float t) {
+  return __fadd_rn(a, __fmul_rn(t, __fsub_rn(b, a)));
+}
+
+struct GridCell {
+  int32_t i[3];
+  float t[3];
+};
+
+__device__ __forceinline__ bool grid_cell(const DevBody &b, float3 y, GridCell *c) {
+  const float yy[3] = {y.x, y.y, y.z};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float u = __fmul_rn(__fsub_rn(yy[k], b.shape[k]), b.shape[4]);
+    if (!(u >= 0.0f && u <= (float)(b.gn[k] - 1u))) return false;
+    int32_t ik = (int32_t)floorf(u);
+    if (ik > (int32_t)b.gn[k] - 2) ik = (int32_t)b.gn[k] - 2;
+    c->i[k] = ik;
+    c->t[k] = __fsub_rn(u, (float)ik);
+  }
+  return true;
+}
+
+__device__ __forceinline__ float grid_sdf(const DevBody &b, float3 y, int *branch) {
+  GridCell c;
+  if (!b.grid || !grid_cell(b, y, &c)) {
+    *branch = -1;
+    return __int_as_float(0x7f800000);
+  }
+  const size_t nx = b.gn[0], nxy = (size_t)b.gn[0] * b.gn[1];
+  const size_t base = (size_t)c.i[2] * nxy + (size_t)c.i[1] * nx + (size_t)c.i[0];
+  const float *v = b.grid + base;
+  const float c00 = lerp_rn(v[0], v[1], c.t[0]);
+  const float c10 = lerp_rn(v[nx], v[nx + 1], c.t[0]);
+  const float c01 = lerp_rn(v[nxy], v[nxy + 1], c.t[0]);
+  const float c11 = lerp_rn(v[nxy + nx], v[nxy + nx + 1], c.t[0]);
+  *branch = (int)base;
+  return lerp_rn(lerp_rn(c00, c10, c.t[1]), lerp_rn(c01, c11, c.t[1]), c.t[2]);
+}
+
+// Gradient of the trilinear interpolant of the cell (per unit t, i.e. h times the
+// gradient in y) and, when hess != nullptr, its mixed second derivatives per unit t:
+// hess = (d2f/dtx dty, d2f/dtx dtz, d2f/dty dtz) (the pure ones vanish).
+__device__ __forceinline__ float3 grid_dt(const DevBody &b, float3 y, int branch, float3 *hess) {
+  const size_t nx = b.gn[0], nxy = (size_t)b.gn[0] * b.gn[1];
+  const float *v = b.grid + (size_t)branch;
+  float t[3];
+  const float yy[3] = {y.x, y.y, y.z};
+  const int32_t i[3] = {(int32_t)((size_t)branch % nx), (int32_t)(((size_t)branch / nx) % b.gn[1]),
+                        (int32_t)((size_t)branch / nxy)};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) t[k] = (yy[k] - b.shape[k]) * b.shape[4] - (float)i[k];
+  float s[2][2][2];
+#pragma unroll
+  for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) s[cz][cy][cx] = v[cz * nxy + cy * nx + cx];
+  const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
+  float3 g = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+  for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy) g.x += (s[cz][cy][1] - s[cz][cy][0]) * wy[cy] * wz[cz];
+#pragma unroll
+  for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+    for (int cx = 0; cx < 2; ++cx) g.y += (s[cz][1][cx] - s[cz][0][cx]) * wx[cx] * wz[cz];
+#pragma unroll
+  for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+    for (int cx = 0; cx < 2; ++cx) g.z += (s[1][cy][cx] - s[0][cy][cx]) * wx[cx] * wy[cy];
+  if (hess) {
+    float hxy = 0.f, hxz = 0.f, hyz = 0.f;
+#pragma unroll
+    for (int c2 = 0; c2 < 2; ++c2) {
+      hxy += (s[c2][1][1] - s[c2][1][0] - s[c2][0][1] + s[c2][0][0]) * wz[c2];
+      hxz += (s[1][c2][1] - s[1][c2][0] - s[0][c2][1] + s[0][c2][0]) * wy[c2];
+      hyz += (s[1][1][c2] - s[1][0][c2] - s[0][1][c2] + s[0][0][c2]) * wx[c2];
+    }
+    *hess = make_float3(hxy, hxz, hyz);
+  }
+  return g;
+}
+
 __device__ __forceinline__ float body_sdf(const DevBody &b, float3 y, int *branch) {
   switch (b.kind) {
   case 0:  // plane
@@ -251,6 +345,8 @@ __device__ __forceinline__ float body_sdf(const DevBody &b, float3 y, int *branc
     *branch = br;
     return f;
   }
+  case 4:
+    return grid_sdf(b, y, branch);
   }
   *branch = -1;
   return __int_as_float(0x7f800000);  // +inf: never in contact
@@ -292,6 +388,13 @@ __device__ __forceinline__ float3 body_grad(const DevBody &b, float3 y, int bran
     if (branch == 3) g.y = 1.f;
     if (branch == 4) g.z = 1.f;
     return g;
+  }
+  case 4: {
+    const float3 g = grid_dt(b, y, branch, nullptr);
+    const float gn = sqrtf(g.x * g.x + g.y * g.y + g.z * g.z);
+    if (!(gn > 0.f)) return make_float3(0.f, 0.f, 1.f);
+    const float ig = 1.0f / gn;
+    return make_float3(g.x * ig, g.y * ig, g.z * ig);
   }
   }
   return make_float3(0.f, 0.f, 1.f);

@@ -32,6 +32,7 @@ SIGNATURES = {
     "gg_create_batch": (C.c_int, [_P, C.c_uint32, _P, _P, _P, _P, C.c_int, C.POINTER(C.c_void_p)]),
     "gg_set_bodies": (C.c_int, [_P, C.c_uint32, C.c_uint32, _P]),
     "gg_set_trajectory": (C.c_int, [_P, C.c_uint32, C.c_uint32, C.c_uint32, _P, C.c_int]),
+    "gg_set_body_grid": (C.c_int, [_P, C.c_uint32, C.c_uint32, _P, _P, C.c_float, _P, C.c_int]),
     "gg_set_particles": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "gg_step": (C.c_int, [_P, C.c_uint32, _P]),
     "gg_sync": (C.c_int, [_P, _P]),
@@ -207,8 +208,27 @@ class Sim:
             raise GGError(st, f"{what}: {self._L.gg_last_error(self.h).decode()}")
 
     def set_bodies(self, bodies, env=0):
+        """Bodies of environment env; the samples of GRID bodies (Body.grid) follow."""
         arr = make_bodies(bodies)
         self._check(self._L.gg_set_bodies(self.h, env, len(bodies), arr), "gg_set_bodies")
+        for b, body in enumerate(bodies):
+            if getattr(body, "grid", None) is not None:
+                self.set_body_grid(b, body.grid, env)
+
+    def set_body_grid(self, body, grid, env=0):
+        """Samples of GRID body `body`: grid.values float32 (nz, ny, nx), grid.origin, grid.spacing."""
+        v = grid.values
+        if _is_torch(v):
+            p, dev = _ptr(v.contiguous())
+            nz, ny, nx = v.shape
+        else:
+            v = np.ascontiguousarray(v, np.float32)
+            p, dev = _ptr(v)
+            nz, ny, nx = v.shape
+        dims = (C.c_uint32 * 3)(nx, ny, nz)
+        org = (C.c_float * 3)(*[float(o) for o in grid.origin])
+        self._check(self._L.gg_set_body_grid(self.h, env, body, dims, org, float(grid.spacing), p, dev),
+                    "gg_set_body_grid")
 
     def set_trajectory(self, body, twist, env=0):
         tw = twist if _is_torch(twist) else np.ascontiguousarray(twist, np.float32)

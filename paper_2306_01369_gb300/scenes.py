@@ -391,3 +391,163 @@ def random_cloud(n, seed, box=0.05, r0=2e-3, jitter=0.1, vel_scale=0.0, overlap=
     pr[:, 3] = (r0 * (1.0 + jitter * (2.0 * u[:, 3] - 1.0))).astype(np.float32)
     vel = (vel_scale * (2.0 * u[:, 4:7] - 1.0)).astype(np.float32)
     return pr, vel
+
+
+# --------------------------------------------------------------------------- #
+# sampled SDF bodies (Sec. II-C): geometry baked onto regular grids
+# --------------------------------------------------------------------------- #
+
+def bake_grid(f, lo, hi, h):
+    """Grid of f (a numpy SDF over (..., 3) body-frame points) on the box [lo, hi]
+    with spacing h (the box is grown to a whole number of cells)."""
+    lo = np.asarray(lo, np.float64)
+    n = np.ceil((np.asarray(hi, np.float64) - lo) / h).astype(int) + 1
+    n = np.maximum(n, 2)
+    vals = np.empty((n[2], n[1], n[0]), np.float32)
+    xs = lo[0] + h * np.arange(n[0])
+    ys = lo[1] + h * np.arange(n[1])
+    for k in range(n[2]):
+        yy, xx = np.meshgrid(ys, xs, indexing="ij")
+        pts = np.stack([xx, yy, np.full_like(xx, lo[2] + h * k)], axis=-1)
+        vals[k] = f(pts)
+    return Grid(vals, tuple(float(v) for v in lo), float(h))
+
+
+def box_minus_box_sdf(shape):
+    """numpy SDF of the scoop geometry (box A minus box B), for baking."""
+    ha, hb, cb = np.array(shape[0:3]), np.array(shape[3:6]), np.array(shape[6:9])
+
+    def box(y, half):
+        q = np.abs(y) - half
+        return np.linalg.norm(np.maximum(q, 0.0), axis=-1) + np.minimum(q.max(axis=-1), 0.0)
+
+    return lambda y: np.maximum(box(y, ha), -box(y - cb, hb))
+
+
+def gear_outline(teeth, module, pressure_deg=20.0, n_flank=10, n_arc=3):
+    """Closed outline (counter-clockwise, (N, 2)) of an involute spur gear: pitch
+    radius module * teeth / 2, addendum module, dedendum 1.25 module, involute
+    flanks from the base circle (radial below it), tooth half-thickness pi / (2 teeth)
+    of arc at the pitch circle."""
+    a = math.radians(pressure_deg)
+    rp = 0.5 * module * teeth
+    rb, ra, rf = rp * math.cos(a), rp + module, max(rp - 1.25 * module, 0.2 * rp)
+
+    def inv(r):  # involute polar angle at radius r >= rb
+        al = math.acos(min(1.0, rb / r))
+        return math.tan(al) - al
+
+    half = math.pi / (2 * teeth) + inv(rp)      # flank angle offset at the base circle
+    pts = []
+    for k in range(teeth):
+        c = 2 * math.pi * k / teeth
+        r_lo = max(rb, rf)
+        rr = np.linspace(r_lo, ra, n_flank)
+        # right flank (rising), tip arc, left flank (falling)
+        right = [(r, c - half + inv(r)) for r in rr]
+        left = [(r, c + half - inv(r)) for r in rr[::-1]]
+        tip0, tip1 = right[-1][1], left[0][1]
+        tip = [(ra, t) for t in np.linspace(tip0, tip1, n_arc + 2)[1:-1]]
+        root_a = c + half - inv(r_lo)
+        root_b = c + 2 * math.pi / teeth - half + inv(r_lo)
+        root = [(rf, t) for t in np.linspace(root_a, root_b, n_arc + 2)]
+        seq = ([(rf, right[0][1])] if rf < rb else []) + right + tip + left + ([(rf, root_a)] if rf < rb else []) + root[1:-1]
+        pts.extend(seq)
+    return np.array([(r * math.cos(t), r * math.sin(t)) for r, t in pts])
+
+
+def polygon_sdf2(poly):
+    """numpy signed distance to a closed polygon (negative inside), over (..., 2)."""
+    a = poly
+    b = np.roll(poly, -1, axis=0)
+    e = b - a
+    ee = (e * e).sum(1)
+
+    def f(p):
+        shp = p.shape[:-1]
+        q = p.reshape(-1, 2)
+        out = np.empty(q.shape[0])
+        for s in range(0, q.shape[0], 8192):
+            w = q[s:s + 8192, None, :] - a[None]
+            t = np.clip((w * e[None]).sum(-1) / ee[None], 0.0, 1.0)
+            d = w - t[..., None] * e[None]
+            dist = np.sqrt((d * d).sum(-1).min(1))
+            # winding (crossing) test for the sign
+            y = q[s:s + 8192, 1][:, None]
+            cond = (a[None, :, 1] <= y) != (b[None, :, 1] <= y)
+            xint = a[None, :, 0] + (y - a[None, :, 1]) * (b[None, :, 0] - a[None, :, 0]) / np.where(
+                b[None, :, 1] == a[None, :, 1], 1.0, b[None, :, 1] - a[None, :, 1])
+            inside = (cond & (q[s:s + 8192, 0][:, None] < xint)).sum(1) % 2 == 1
+            out[s:s + 8192] = np.where(inside, -dist, dist)
+        return out.reshape(shp)
+
+    return f
+
+
+def helical_gear_sdf(teeth, module, width, helix_deg=20.0):
+    """numpy SDF (approximate away from the surface) of an involute helical gear about
+    the body z axis: the outline twisted by tan(helix) / r_pitch per unit height,
+    intersected with the slab |z| <= width / 2."""
+    outline = polygon_sdf2(gear_outline(teeth, module))
+    twist = math.tan(math.radians(helix_deg)) / (0.5 * module * teeth)
+
+    def f(y):
+        ang = -twist * y[..., 2]
+        c, s = np.cos(ang), np.sin(ang)
+        p2 = np.stack([c * y[..., 0] - s * y[..., 1], s * y[..., 0] + c * y[..., 1]], axis=-1)
+        return np.maximum(outline(p2), np.abs(y[..., 2]) - 0.5 * width)
+
+    return f
+
+
+def gear_body(teeth=12, module=0.004, width=0.02, h=None, margin=0.006, pos=(0.0, 0.0, 0.0),
+              quat=(1.0, 0.0, 0.0, 0.0), ang_vel=(0.0, 0.0, 0.0)):
+    """A GRID body: helical gear baked with spacing h (default module / 4) on its
+    bounding box grown by `margin` (>= r_max of the spheres it meets)."""
+    h = h or module / 4.0
+    ra = 0.5 * module * teeth + module
+    lo = (-ra - margin, -ra - margin, -0.5 * width - margin)
+    hi = (ra + margin, ra + margin, 0.5 * width + margin)
+    g = bake_grid(helical_gear_sdf(teeth, module, width), lo, hi, h)
+    return Body(kind=GRID, pos=pos, quat=quat, ang_vel=ang_vel, grid=g)
+
+
+def gear_bed(n=4096, seed=1005, n_gears=1, teeth=8, module=0.003, width=0.012, omega=4.0, r0=1.5e-3,
+             n_steps=200, gear=None):
+    """A bed of n spheres (r0 +-10 %) in an open box with n_gears helical gears (GRID
+    bodies, vertical axes, one baked grid shared by all) embedded in it, spinning at
+    +-omega rad/s; lattice sites whose sphere would touch a gear are left empty.
+    dt = 1e-4 s, 20 PJA iterations, mu = 0.5."""
+    jit = 0.10
+    pitch = 2.0 * r0 * (1 + jit) * 1.02
+    ra = 0.5 * module * teeth + module
+    per_row = max(1, int(math.ceil(math.sqrt(n_gears))))
+    side = max(int(math.ceil(math.sqrt(n / 12.0))), int(math.ceil(per_row * 2.6 * ra / pitch)))
+    foot = side * pitch
+    layers = -(-n // (side * side)) + 8
+    cand, _ = jittered_lattice((side, side, layers), side * side * layers, r0, jit, seed,
+                               origin=(-0.5 * foot, -0.5 * foot, 0.0), pitch=pitch)
+    g = gear if gear is not None else gear_body(teeth, module, width, margin=max(0.004, 2.5 * r0))
+    sdf = helical_gear_sdf(teeth, module, width)
+    u = uniform(seed * 31 + 7, 2 * n_gears)
+    bodies = [Body(kind=OPEN_BOX, shape=(0.5 * foot + 0.004, 0.5 * foot + 0.004, 0.0))]
+    keep = np.ones(cand.shape[0], bool)
+    cell = foot / per_row
+    zc = 0.5 * width + 2.0 * pitch
+    for k in range(n_gears):
+        cx = -0.5 * foot + (k % per_row + 0.5) * cell
+        cy = -0.5 * foot + (k // per_row + 0.5) * cell
+        w = omega if u[2 * k] < 0.5 else -omega
+        pos = (cx, cy, zc)
+        y = cand[:, :3].astype(np.float64) - np.array(pos)
+        near = np.linalg.norm(y[:, :2], axis=1) < ra + 2 * r0
+        near &= np.abs(y[:, 2]) < 0.5 * width + 2 * r0
+        if near.any():
+            d = sdf(y[near])
+            idx = np.nonzero(near)[0]
+            keep[idx[d < cand[idx, 3] + 2e-4]] = False
+        bodies.append(Body(kind=GRID, pos=pos, ang_vel=(0.0, 0.0, w), grid=g.grid))
+    pr = cand[keep][:n].copy()
+    assert pr.shape[0] == n
+    return Scene(f"gear_bed_{n}_{n_gears}", pr, np.zeros((n, 3), np.float32), sphere_mass(pr[:, 3]), bodies,
+                 Params(dt=1e-4, mu=0.5, pja_iters=20), n_steps, info={"foot": foot, "ra": ra})

@@ -55,7 +55,8 @@ def fp32_scene(scene, o):
         bodies.append(S.Body(kind=body.kind, shape=body.shape, pos=tuple(float(F32(v)) for v in pose[:3]),
                              quat=tuple(float(F32(v)) for v in pose[3:]),
                              lin_vel=tuple(float(v) for v in tw[:3]), ang_vel=tuple(float(v) for v in tw[3:]),
-                             is_free=body.is_free, mass=body.mass, inertia=body.inertia))
+                             is_free=body.is_free, mass=body.mass, inertia=body.inertia,
+                             grid=getattr(body, "grid", None)))
     twist = {b: t[k:] for b, t in scene.twist.items() if t.shape[0] > k}
     return S.Scene(f"{scene.name}@{k}", pos_r, o.v.astype(F32), scene.mass, bodies, scene.params,
                    max(0, scene.n_steps - k), twist=twist, env_offsets=scene.env_offsets,
