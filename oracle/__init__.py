@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
 class OrcParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("gravity", C.c_double * 3), ("mu", C.c_double), ("alpha", C.c_double),
                 ("pja_iters", C.c_int32), ("n_threads", C.c_int32), ("cell_size", C.c_float),
-                ("hash_size", C.c_uint32)]
+                ("hash_size", C.c_uint32), ("cyclic_z", C.c_double * 2)]
 
 
 class OrcBody(C.Structure):
@@ -114,6 +114,8 @@ def make_params(params, n: int, r_max: float, n_threads: int = 1) -> OrcParams:
     p.n_threads = int(n_threads)
     p.cell_size = params.cell_size if params.cell_size > 0 else default_cell_size(r_max)
     p.hash_size = params.hash_size if params.hash_size > 0 else max(1, 2 * n)
+    cz = getattr(params, "cyclic_z", (0.0, 0.0))
+    p.cyclic_z[0], p.cyclic_z[1] = _f32(cz[0]), _f32(cz[1])
     return p
 
 

@@ -226,6 +226,13 @@ static float sdf_f32(const bodyf *b, const float *y, int *branch) {
   }
   case ORC_GRID:
     return grid_f32(b, y, branch);
+  case ORC_TUBE: { /* inside of a vertical cylinder of radius s[0]: f = R - |(y0, y1)| */
+    float q = y[0] * y[0];
+    float t = y[1] * y[1];
+    q = q + t;
+    *branch = 0;
+    return b->s[0] - sqrtf(q);
+  }
   default:
     *branch = -1;
     return INFINITY;
@@ -344,6 +351,18 @@ static double sdf64_branch(const orc_body *b, const double *y, int branch, doubl
   case ORC_GRID:
     if (branch >= 0) return grid64(b, y, branch, g);
     break;
+  case ORC_TUBE: {
+    const double rho = sqrt(y[0] * y[0] + y[1] * y[1]);
+    if (rho > 0) {
+      g[0] = -y[0] / rho;
+      g[1] = -y[1] / rho;
+    } else {
+      g[0] = -1.0;
+      g[1] = 0.0;
+    }
+    g[2] = 0.0;
+    return b->shape[0] - rho;
+  }
   }
   g[0] = g[1] = g[2] = 0;
   return INFINITY;
@@ -992,12 +1011,17 @@ int orc_step(const orc_params *p, uint32_t n, double *x, double *v, const double
     st->ncp_residual = res / vs;
   }
 
-  /* symplectic Euler (reading of Eq. 4-5): velocity first, then position */
-  for (uint32_t i = 0; i < n; ++i)
+  /* symplectic Euler (reading of Eq. 4-5): velocity first, then position; then the
+     cyclic vertical boundary of the gear tower (the paper's Sec. III: particles leaving
+     through the bottom re-enter at the top with the same velocity) */
+  const int cyclic = p->cyclic_z[1] > p->cyclic_z[0];
+  for (uint32_t i = 0; i < n; ++i) {
     for (int k = 0; k < 3; ++k) {
       v[3 * i + k] = U[3 * i + k];
       x[3 * i + k] += dt * v[3 * i + k];
     }
+    if (cyclic && x[3 * i + 2] < p->cyclic_z[0]) x[3 * i + 2] += p->cyclic_z[1] - p->cyclic_z[0];
+  }
 
   /* wrench on each body = -(impulses it gives) / dt */
   if (wrench) {

@@ -27,15 +27,18 @@ typedef struct {
   int32_t n_threads;  /* OpenMP threads for the per-particle loops (results do not depend on it) */
   float cell_size;    /* grid cell edge c (Eq. 6 uses c = 2r); must be >= 2 r_max */
   uint32_t hash_size; /* n_h of Eq. 6 */
+  double cyclic_z[2]; /* cyclic vertical boundary (gear tower, Sec. III): if cyclic_z[1] > cyclic_z[0], a
+                         particle below cyclic_z[0] after a step moves up by cyclic_z[1] - cyclic_z[0] */
 } orc_params;
 
-enum { ORC_PLANE = 0, ORC_BOX = 1, ORC_BOX_MINUS_BOX = 2, ORC_OPEN_BOX = 3, ORC_GRID = 4 };
+enum { ORC_PLANE = 0, ORC_BOX = 1, ORC_BOX_MINUS_BOX = 2, ORC_OPEN_BOX = 3, ORC_GRID = 4, ORC_TUBE = 5 };
 
 typedef struct {
   int32_t kind;       /* ORC_* */
   int32_t is_free;    /* 0: kinematic (driven by its twist), 1: free rigid body */
   double shape[12];   /* BOX/OPEN_BOX: half extents [0..2]; BOX_MINUS_BOX: A half [0..2], B half [3..5], B centre [6..8];
-                         GRID: body-frame position of sample (0, 0, 0) [0..2], sample spacing h [3] */
+                         GRID: body-frame position of sample (0, 0, 0) [0..2], sample spacing h [3];
+                         TUBE: radius [0] of the inside of a vertical cylinder (no caps) */
   double pos[3];      /* world position of the body origin */
   double quat[4];     /* orientation (w, x, y, z), body -> world */
   double lin_vel[3];  /* world-frame twist: velocity of the origin ... */

@@ -27,6 +27,7 @@ BOX = 1            # solid box, shape[0:3] = half extents
 BOX_MINUS_BOX = 2  # box A (shape[0:3]) minus box B (half extents shape[3:6], centre shape[6:9])
 OPEN_BOX = 3       # container: inside of a box with no lid, shape[0:3] = half extents
 GRID = 4           # SDF sampled on a regular grid (trilinear), samples in Body.grid
+TUBE = 5           # inside of a vertical cylinder (no caps), shape[0] = radius
 
 DENSITY = 2500.0   # kg/m^3, used when a scene gives no density
 
@@ -92,6 +93,7 @@ class Params:
     hash_size: int = 0          # 0 -> 2 n (per environment)
     max_contacts: int = 16      # particle-particle capacity per particle
     max_body_contacts: int = 4  # particle-body capacity per particle
+    cyclic_z: tuple = (0.0, 0.0)  # cyclic vertical boundary (bottom, top); off when equal
 
 
 @dataclass

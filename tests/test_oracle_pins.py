@@ -617,3 +617,41 @@ def test_sphere_rests_on_a_grid_plane(orc):
         s.step(1)
         want = (1.0 - a) ** k * psi
         assert abs((float(r) - s.x[0, 2]) - want) < 1e-13, k
+
+
+def test_cyclic_vertical_boundary_free_fall(orc):
+    """Cyclic boundary of the gear tower (Sec. III): a free-falling sphere leaving
+    through the bottom re-enters at the top with the same velocity.  Symplectic Euler
+    from rest: v_k = -k g dt, z_k = z_0 - g dt^2 k (k + 1) / 2, then wrapped into the
+    period [lo, hi)."""
+    lo, hi = 0.0, 0.0625
+    p = S.Params(dt=1e-3, mu=0.5, pja_iters=5, cyclic_z=(lo, hi))
+    z0 = F32(0.05)
+    s = orc.Sim(np.array([[0.0, 0.0, z0, 0.001]], F32), np.zeros((1, 3), F32), np.array([1e-3], F32), [], p)
+    g, dt = float(F32(9.81)), float(F32(1e-3))
+    wrapped = 0
+    z = float(z0)
+    for k in range(1, 301):
+        s.step(1)
+        v = -k * g * dt
+        z = z + dt * v
+        if z < lo:
+            z += hi - lo
+            wrapped += 1
+        assert abs(s.v[0, 2] - v) < 1e-12
+        assert abs(s.x[0, 2] - z) < 1e-12, (k, s.x[0, 2], z)
+    assert wrapped >= 3
+
+
+def test_tube_sdf_values(orc):
+    """Inside of a vertical cylinder of radius R (the gear tower's wall): f = R - rho,
+    normal towards the axis, independent of height."""
+    tube = S.Body(kind=S.TUBE, shape=(0.0625,), pos=(0.25, -0.125, 0.0))
+    for y, want in (((0.0, 0.0, 0.3), 0.0625), ((0.05, 0.0, -1.0), 0.0125), ((0.0, -0.06, 0.0), 0.0025),
+                    ((0.03, 0.04, 0.7), 0.0125)):
+        x = np.array(y) + np.array([0.25, -0.125, 0.0])
+        f, n = orc.sdf(tube, x)
+        assert abs(f - want) < 1e-12
+        rho = math.hypot(y[0], y[1])
+        if rho > 0:
+            assert np.allclose(n, [-y[0] / rho, -y[1] / rho, 0.0], atol=1e-12)
