@@ -389,27 +389,49 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
                                  "forward_ms": fwd_ms, "taped_forward_ms": 1e3 * (t1 - t0),
                                  "backward_ms": 1e3 * (t2 - t1), "bwd_over_fwd": 1e3 * (t2 - t1) / fwd_ms,
                                  "grad_norm_twist": float(tw.grad.norm()), "dL_dmu": float(mu.grad)}
-    # gridded SDF bodies: helical gears (one baked grid) spinning in a bed of 65,536
-    # spheres, throughput against the number of gears (the paper's claim: the gridded
-    # lookup costs the same whatever the geometry)
+    # the gear tower (Sec. III, Fig. helical-gear-benchmark): 65,536 spheres in a tube
+    # with a cyclic vertical boundary, n helical gears (GRID bodies sharing one baked
+    # grid) on its axis; throughput against the number of gears (the paper's claim:
+    # the gridded lookup costs the same whatever the geometry)
     if time.perf_counter() - t_start < seconds_cap:
-        gear = scenes.gear_body(12, 0.004, 0.02)
+        gear = scenes.gear_body(10, 0.003, 0.012, margin=0.005)
         rates = {}
-        for nb in (0, 4, 9, 16):
-            gs = scenes.gear_bed(n=65536, n_gears=max(nb, 1), teeth=12, module=0.004, width=0.02, r0=2e-3,
-                                 gear=gear)
-            if nb == 0:
-                gs.bodies = gs.bodies[:1]
-            sim = gg.Sim.from_scene(gs, max_bodies=17)
-            sim.step(300, stream=stream)       # let the bed settle around the gears
-            ms = _timed_steps(sim, 50, stream, torch)
+        for nb in (0, 5, 10, 20):
+            ts = scenes.gear_tower(n=65536, n_gears=nb, gear=gear)
+            sim = gg.Sim.from_scene(ts, max_bodies=21)
+            sim.step(300, stream=stream)
+            ms = _timed_steps(sim, 100, stream, torch)
             sim.sync(stream)
             st = sim.stats()
-            rates[str(nb)] = {"particle_steps_per_s": gs.n * 50 / (ms * 1e-3), "n_body_contacts": st["n_body"]}
+            rates[str(nb)] = {"particle_steps_per_s": ts.n * 100 / (ms * 1e-3), "ms_per_step": ms / 100,
+                              "n_pp": st["n_pp"], "n_body": st["n_body"]}
             sim.close()
-        out["gears"] = {"workload": "65,536 spheres in a box with n helical gears (GRID bodies, 12 teeth, "
-                                    "module 4 mm, 1 mm samples), I=20", "by_gear_count": rates,
-                        "grid_samples": int(gear.grid.values.size)}
+        out["gear_tower"] = {"workload": "65,536 spheres in a 6 cm tube with a cyclic vertical boundary and n "
+                                         "helical gears (GRID bodies: 10 teeth, module 3 mm, 0.75 mm samples) "
+                                         "spinning at U(-4, 4) rad/s, I=20; timed steps 300-400",
+                             "by_gear_count": rates, "grid_samples": int(gear.grid.values.size)}
+    # ablations of the paper's design choices on the column (262,144 spheres, 1,000
+    # steps into the collapse): binning by counting sort vs the paper's per-bucket
+    # linked lists (Alg. 2), and the hash table size n_h (Fig. hashtable-benchmark,
+    # whose heuristic is n_h = 2n)
+    if time.perf_counter() - t_start < seconds_cap:
+        col = scenes.column_collapse()
+        abl = {}
+        for name, kw in (("sort_nh2n", dict(tuning=1, hash_factor=2)), ("lists_nh2n", dict(tuning=7, hash_factor=2)),
+                         ("sort_nh1n", dict(tuning=1, hash_factor=1)), ("lists_nh1n", dict(tuning=7, hash_factor=1)),
+                         ("sort_nh4n", dict(tuning=1, hash_factor=4)), ("lists_nh4n", dict(tuning=7, hash_factor=4)),
+                         ("sort_nh8n", dict(tuning=1, hash_factor=8)), ("lists_nh8n", dict(tuning=7, hash_factor=8))):
+            sim = gg.Sim.from_scene(col, **kw)
+            sim.step(1000, stream=stream)
+            ms = _timed_steps(sim, 100, stream, torch)
+            sim.enable_timing(True)
+            sim.step(1, stream=stream)
+            stg = sim.stage_ms()
+            sim.close()
+            abl[name] = {"ms_per_step": ms / 100, "binning_us": 1e3 * stg["bin_sort"],
+                         "contacts_us": 1e3 * stg["contacts"]}
+        out["ablations"] = {"workload": "column collapse 262,144, steps 1000-1100; stage times from one "
+                                        "instrumented step after the timed ones", "configs": abl}
     # excavation: 1,048,576 spheres, scoop, two free cubes, I = 30
     if time.perf_counter() - t_start < seconds_cap:
         ex = scenes.excavation(n=1048576, n_steps=steps_exc + 20)

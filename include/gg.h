@@ -71,8 +71,10 @@ typedef enum {
                                  shape[3..5], centre shape[6..8]): an excavation scoop */
   GG_BODY_OPEN_BOX = 3,       /* container: inside of a box with no lid, walls at x = +-shape[0],
                                  y = +-shape[1], floor at z = -shape[2]; walls are unbounded in +z */
-  GG_BODY_GRID = 4            /* SDF sampled on a regular grid, trilinear interpolation (Sec. II-C);
+  GG_BODY_GRID = 4,           /* SDF sampled on a regular grid, trilinear interpolation (Sec. II-C);
                                  samples from gg_set_body_grid (shape ignored).  Kinematic only. */
+  GG_BODY_TUBE = 5            /* inside of a vertical cylinder of radius shape[0], no caps (the wall
+                                 of the gear tower, Sec. III): f = shape[0] - |(y_x, y_y)| */
 } gg_body_kind;
 
 typedef struct {
@@ -91,9 +93,10 @@ typedef struct {
   uint32_t max_body_contacts;/* particle-body contact capacity per particle, 1..8; 0 -> 4 */
   uint32_t max_bodies;       /* bodies per environment, 1..64; 0 -> 8 */
   float density;             /* mass = density 4/3 pi r^3 when no masses are given; 0 -> 2500 */
-  uint32_t tuning;           /* 0: the first gg_step times every launch-shape set on a copy of the
-                                state (restored bit-exactly) and keeps the fastest; k >= 1: fixed
-                                set k (see gg_tuning_count).  Results do not depend on it. */
+  uint32_t tuning;           /* 0: the first gg_step times every launch-shape set (binning
+                                included) on a copy of the state (restored bit-exactly) and keeps
+                                the fastest; k >= 1: fixed set k (see gg_tuning_count; sets 7-8 bin
+                                by linked lists).  Results do not depend on it. */
   uint32_t wrench_history;   /* per-step body wrenches kept for readback; 0 -> 1 */
   uint32_t max_free_bodies;  /* free rigid bodies over all environments (beyond the paper's
                                 kinematic bodies, Sec. V two-way coupling); 0 -> none */
@@ -101,6 +104,15 @@ typedef struct {
   uint32_t barrier_test_phantoms; /* testing aid, 0 in normal use: phantom participants that every
                                      grid barrier of the fused sweep waits for, so each wait runs
                                      out (bounded) and the step reports GG_ERR_DEVICE_TIMEOUT */
+  uint32_t binning;          /* 1: counting sort of (bucket, id), contiguous buckets; 2: a lock-free
+                                linked list per bucket, the paper's Alg. 2 (pushed with an atomic
+                                exchange); 0: either, as the tuning set says (tuning = 0: the
+                                autotuner times both).  Results are identical; with lists the
+                                sort-order readbacks sort the step's keys on demand. */
+  float cyclic_z[2];         /* cyclic vertical boundary (the gear tower of Sec. III): when
+                                cyclic_z[1] > cyclic_z[0], a particle whose z falls below cyclic_z[0]
+                                in a step moves up by cyclic_z[1] - cyclic_z[0], velocity unchanged.
+                                The contact search does not wrap.  {0, 0}: off */
 } gg_params;
 
 typedef struct {

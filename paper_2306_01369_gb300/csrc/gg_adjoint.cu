@@ -113,6 +113,12 @@ __device__ __forceinline__ float3 body_fgrad(const DevBody &b, float3 y, int bra
 
 __device__ __forceinline__ float3 body_grad_adj(const DevBody &b, float3 y, int branch, float3 gb) {
   if (b.kind == 4) return grid_grad_adj(b, y, branch, gb);
+  if (b.kind == 5) {  // tube: n = -(y_x, y_y, 0) / rho, dn/dy = -(I_2 - n n^T) / rho on the xy block
+    const float rho = sqrtf(y.x * y.x + y.y * y.y);
+    if (!(rho > 0.f)) return make_float3(0.f, 0.f, 0.f);
+    const float nx = -y.x / rho, ny = -y.y / rho, d = nx * gb.x + ny * gb.y;
+    return make_float3(-(gb.x - nx * d) / rho, -(gb.y - ny * d) / rho, 0.f);
+  }
   if (b.kind == 1) return box_grad_adj(y, b.shape, branch, gb);
   if (b.kind == 2) {
     if (branch < 4) return box_grad_adj(y, b.shape, branch, gb);

@@ -27,9 +27,9 @@ using gg::StepArgs;
 namespace {
 
 // Launch-shape sets accepted by gg_params.tuning (index k-1).
-// (iters, per-launch sweep block, fused sweep block, fused grid)
-const gg::LaunchShape kShapes[] = {{0, 256, 0, 0}, {0, 128, 0, 0}, {0, 512, 0, 0}, {0, 64, 0, 0},
-                                   {0, 256, 1024, 0}, {0, 256, 512, 0}};
+// (iters, per-launch sweep block, fused sweep block, fused grid, binning by lists)
+const gg::LaunchShape kShapes[] = {{0, 256, 0, 0, 0},    {0, 128, 0, 0, 0}, {0, 512, 0, 0, 0}, {0, 64, 0, 0, 0},
+                                   {0, 256, 1024, 0, 0}, {0, 256, 512, 0, 0}, {0, 256, 0, 0, 1}, {0, 128, 0, 0, 1}};
 constexpr uint32_t kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 constexpr uint32_t kStateMagic = 0x31534747u;  // "GGS1"
@@ -206,9 +206,16 @@ gg_status set_shape(gg_sim *s, uint32_t k) {
     ls.fused_grid = per > 0 ? (uint32_t)(per * nsm) : 0;
   }
   s->ls = ls;
+  s->a.lists = ls.lists;
   s->tuning_sel = k;
   free_graph(s);
   return GG_OK;
+}
+
+// Launch-shape sets allowed by gg_params.binning (0: any, 1: sort only, 2: lists only).
+bool shape_allowed(const gg_sim *s, uint32_t k) {
+  const uint32_t b = s->p.binning;
+  return b == 0 || (b == 1 && !kShapes[k - 1].lists) || (b == 2 && kShapes[k - 1].lists);
 }
 
 gg_status capture(gg_sim *s);
@@ -231,7 +238,9 @@ gg_status autotune(gg_sim *s, cudaStream_t st) {
   gg_status rc = save_state(s, saved, st);
   if (rc == GG_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
     rc = cuda_fail(s, cudaGetLastError(), "cudaEventCreate");
+  bool first = true;
   for (uint32_t k = 1; rc == GG_OK && k <= kNumShapes; ++k) {
+    if (!shape_allowed(s, k)) continue;
     if ((rc = set_shape(s, k)) != GG_OK || (kShapes[k - 1].fused_block && !s->ls.fused_grid)) continue;
     if ((rc = capture(s)) != GG_OK) break;
     if ((rc = restore_state(s, saved, st)) != GG_OK) break;
@@ -246,9 +255,10 @@ gg_status autotune(gg_sim *s, cudaStream_t st) {
       rc = cuda_fail(s, ce, "autotune trial");
       break;
     }
-    if (k == 1 || ms < best) {
+    if (first || ms < best) {
       best = ms;
       best_k = k;
+      first = false;
     }
   }
   if (rc == GG_OK) rc = restore_state(s, saved, st);
@@ -383,6 +393,9 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
   if (s->K > (uint32_t)gg::kMaxK || s->Kb > (uint32_t)gg::kMaxKb || s->maxb > 64 || s->H > (1u << 20))
     return bail(GG_ERR_INVALID_ARG);
   if (P.tuning > kNumShapes) return bail(GG_ERR_INVALID_ARG);
+  if (P.binning > 2 || !std::isfinite(P.cyclic_z[0]) || !std::isfinite(P.cyclic_z[1]) ||
+      (P.cyclic_z[1] < P.cyclic_z[0]))
+    return bail(GG_ERR_INVALID_ARG);
   s->F = P.max_free_bodies;
   s->Lcap = P.free_contact_capacity ? P.free_contact_capacity : 4096;
   if (s->F > 4096 || s->Lcap > 8192) return bail(GG_ERR_INVALID_ARG);
@@ -473,6 +486,8 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
   a.dt = P.dt;
   a.mu = P.mu;
   a.ab = P.alpha / P.dt;
+  a.cyc_lo = P.cyclic_z[0];
+  a.cyc_h = P.cyclic_z[1] > P.cyclic_z[0] ? P.cyclic_z[1] - P.cyclic_z[0] : 0.f;
   for (int k = 0; k < 3; ++k) a.g[k] = P.gravity[k];
   const size_t nK = (size_t)n * s->K, nKb = (size_t)n * s->Kb;
   if ((rc = dalloc(s, &a.pos_id, n)) || (rc = dalloc(s, &a.vel_id, n)) || (rc = dalloc(s, &a.env_of, n)) ||
@@ -489,6 +504,7 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
       (rc = dalloc(s, &a.fcount, s->F)) || (rc = dalloc(s, &a.flist, (size_t)s->F * s->Lcap)) ||
       (rc = dalloc(s, &a.fgb, s->F)) || (rc = dalloc(s, &a.fcc, (size_t)s->F * 8 * s->maxb)))
     return bail(rc);
+  if ((rc = dalloc(s, &a.head, s->nh_pad)) || (rc = dalloc(s, &a.next, n))) return bail(rc);
   a.F = s->F;
   a.Lcap = s->Lcap;
   s->fgb.assign(s->F, 0xffffffffu);
@@ -528,7 +544,8 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
     if ((e = cudaMemcpy(&a.ctrl->bar_extra, &ph, sizeof(ph), cudaMemcpyHostToDevice)) != cudaSuccess)
       return bail(cuda_fail(s, e, "initialising the control word"));
   }
-  s->tuning_sel = P.tuning ? P.tuning : 1;
+  s->tuning_sel = P.tuning ? P.tuning : (P.binning == 2 ? 7u : 1u);
+  if (!shape_allowed(s, s->tuning_sel)) return bail(fail(s, GG_ERR_INVALID_ARG, "tuning set and binning disagree"));
   if ((rc = set_shape(s, s->tuning_sel)) != GG_OK) return bail(rc);
   *out = s;
   return GG_OK;
@@ -549,7 +566,7 @@ gg_status gg_set_bodies(gg_sim *s, uint32_t env, uint32_t n_bodies, const gg_bod
   for (uint32_t b = 0; b < n_bodies; ++b) {
     const gg_body &in = bodies[b];
     DevBody &o = hb[b];
-    if (in.kind > GG_BODY_GRID) return fail(s, GG_ERR_INVALID_ARG, "unknown body kind");
+    if (in.kind > GG_BODY_TUBE) return fail(s, GG_ERR_INVALID_ARG, "unknown body kind");
     if (in.kind == GG_BODY_GRID && in.is_free)
       return fail(s, GG_ERR_UNSUPPORTED, "GRID bodies are kinematic (free bodies are boxes)");
     if (in.is_free && !(in.mass > 0.f && in.inertia[0] > 0.f && in.inertia[1] > 0.f && in.inertia[2] > 0.f))
@@ -801,9 +818,11 @@ gg_status gg_readback(gg_sim *s, gg_field f, void *dst, size_t bytes, int dst_on
     if (n) GG_CUDA(s, cudaMemcpyAsync(dst, s->a.key_id, need, d2x, st));
     break;
   case GG_FIELD_SORT_PERM:
+    if (s->a.lists) GG_CUDA(s, gg::enqueue_sort_from_keys(s->a, st));  // binned by lists: sort on demand
     if (n) GG_CUDA(s, cudaMemcpyAsync(dst, s->a.sid, need, d2x, st));
     break;
   case GG_FIELD_CELL_START:
+    if (s->a.lists) GG_CUDA(s, gg::enqueue_sort_from_keys(s->a, st));
     GG_CUDA(s, cudaMemcpyAsync(dst, s->a.start, need, d2x, st));
     break;
   case GG_FIELD_CONTACTS:

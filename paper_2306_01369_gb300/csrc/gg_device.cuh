@@ -21,6 +21,7 @@ constexpr uint32_t kFlagNonFinite = 4u;
 constexpr uint32_t kFlagTimeout = 8u;    // a bounded device-side wait gave up
 constexpr long long kBarrierCycles = 1000000000LL;  // grid-barrier wait limit (~0.5 s at 2 GHz)
 
+constexpr uint32_t kListEnd = 0xffffffffu;  // end of a bucket's linked list
 constexpr int kMaxK = 32;   // particle-particle capacity limit
 constexpr int kMaxKb = 8;   // particle-body capacity limit
 constexpr int kScanItems = 16;          // counts per thread in the bucket scan
@@ -101,6 +102,10 @@ struct StepArgs {
   uint32_t n, n_envs, nh_total, nh_pad, maxb, K, Kb, n_chunks, wrench_hist;
   float dt, mu, ab;       // ab = alpha / dt
   float g[3];
+  float cyc_lo, cyc_h;    // cyclic vertical boundary: z < cyc_lo moves up by cyc_h (cyc_h > 0), else off
+  uint32_t lists;         // binning: 0 counting sort (contiguous buckets), 1 linked lists (Alg. 2)
+  uint32_t *head;         // lists: first particle of each bucket (kListEnd: empty), nh_pad entries
+  uint32_t *next;         // lists: next particle of the same bucket, [n]
   // id order
   float4 *pos_id;   // x, y, z, r
   float4 *vel_id;   // vx, vy, vz, 1/m
@@ -347,6 +352,9 @@ __device__ __forceinline__ float body_sdf(const DevBody &b, float3 y, int *branc
   }
   case 4:
     return grid_sdf(b, y, branch);
+  case 5:  // tube: inside of a vertical cylinder, f = R - |(y_x, y_y)|
+    *branch = 0;
+    return __fsub_rn(b.shape[0], __fsqrt_rn(__fadd_rn(__fmul_rn(y.x, y.x), __fmul_rn(y.y, y.y))));
   }
   *branch = -1;
   return __int_as_float(0x7f800000);  // +inf: never in contact
@@ -388,6 +396,11 @@ __device__ __forceinline__ float3 body_grad(const DevBody &b, float3 y, int bran
     if (branch == 3) g.y = 1.f;
     if (branch == 4) g.z = 1.f;
     return g;
+  }
+  case 5: {
+    const float rho = sqrtf(y.x * y.x + y.y * y.y);
+    if (!(rho > 0.f)) return make_float3(-1.f, 0.f, 0.f);
+    return make_float3(-y.x / rho, -y.y / rho, 0.f);
   }
   case 4: {
     const float3 g = grid_dt(b, y, branch, nullptr);

@@ -32,6 +32,7 @@ struct LaunchShape {
   int pja_block;        // threads per block of k_pja (one launch per sweep)
   int fused_block;      // > 0: all sweeps in one cooperative launch of this block size ...
   uint32_t fused_grid;  // ... and this many blocks (all resident); 0: one launch per sweep
+  uint32_t lists;       // binning: 0 counting sort, 1 linked list per bucket (Alg. 2)
 };
 int fused_pja_blocks_per_sm(int block);
 
@@ -41,6 +42,9 @@ int fused_pja_blocks_per_sm(int block);
 cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st, cudaEvent_t *ev = nullptr,
                          const Tape *tape = nullptr);
 uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls);
+// the counting sort of the keys of the last binning (for the sort-order readbacks when
+// the step bins by linked lists)
+cudaError_t enqueue_sort_from_keys(const StepArgs &a, cudaStream_t st);
 // reverse of one taped step (after enqueue_step with a tape, which stops after the sweeps)
 cudaError_t enqueue_adjoint_step(const StepArgs &a, const AdjArgs &d, uint32_t k_local, cudaStream_t st);
 uint32_t adjoint_blocks(uint32_t n);

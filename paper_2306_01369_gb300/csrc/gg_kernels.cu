@@ -20,6 +20,8 @@
 // neighbours' data in nearby cache lines.
 // Detection and impulse computation are separate launches, the split the paper
 // finds fastest (Sec. II-D).
+#include <algorithm>
+
 #include "gg_device.cuh"
 #include "gg_internal.h"
 
@@ -95,6 +97,19 @@ __device__ void prep_body(const StepArgs &a, uint32_t gb) {
   }
 }
 
+// Histogram of the stored keys (the sort-order readbacks of a step that binned by lists).
+__global__ void k_hist_keys(StepArgs a) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n) atomicAdd(&a.cnt[a.key_id[i]], 1u);
+}
+
+// Linked-list binning: every bucket's list starts empty.
+__global__ void k_list_clear(StepArgs a) {
+  pdl_enter();
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < a.nh_total; b += gridDim.x * blockDim.x)
+    a.head[b] = kListEnd;
+}
+
 __global__ void k_key(StepArgs a) {
   pdl_enter();
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -104,7 +119,10 @@ __global__ void k_key(StepArgs a) {
     int32_t k0 = cell_of(p.x, E.inv_cell), k1 = cell_of(p.y, E.inv_cell), k2 = cell_of(p.z, E.inv_cell);
     uint32_t key = E.hbase + hash_cell_fm(k0, k1, k2, E);
     a.key_id[i] = key;
-    atomicAdd(&a.cnt[key], 1u);
+    if (a.lists)
+      a.next[i] = atomicExch(&a.head[key], i);  // lock-free push onto the bucket's list (Alg. 2)
+    else
+      atomicAdd(&a.cnt[key], 1u);
   }
   if (i < a.n_envs * a.maxb) {
     prep_body(a, i);
@@ -252,6 +270,23 @@ __global__ void k_reorder(StepArgs a) {
 // 5. contacts: particle-particle (27 buckets) and particle-body (SDF)
 // ---------------------------------------------------------------------------
 
+// Inserts partner jid into the thread's list (shared memory, stride S) kept in
+// ascending id order; a bucket reached twice yields the same id, which is skipped.
+__device__ __forceinline__ void insert_partner(uint32_t *fid, uint32_t S, uint32_t K, uint32_t jid, uint32_t &npp,
+                                               bool &ovf) {
+  uint32_t p = 0;
+  while (p < npp && fid[p * S] < jid) ++p;
+  if (p < npp && fid[p * S] == jid) return;
+  if (npp == K) {
+    ovf = true;
+    if (p == K) return;
+  } else {
+    ++npp;
+  }
+  for (uint32_t q2 = npp - 1; q2 > p; --q2) fid[q2 * S] = fid[(q2 - 1) * S];
+  fid[p * S] = jid;
+}
+
 constexpr int kWalkGroup = 3;       // buckets of a row (dx = -1, 0, 1), walked together
 constexpr int kContactsBlock = 128;  // threads per block of k_contacts
 
@@ -259,6 +294,7 @@ constexpr int kContactsBlock = 128;  // threads per block of k_contacts
 // in shared memory, slot p of thread t at [p * blockDim.x + t] (conflict-free): an
 // array indexed at run time in registers would go to local memory, which at full
 // occupancy does not fit in L1.  Dynamic shared memory: K * blockDim.x words.
+template <bool LISTS>
 __global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
   pdl_enter();
   extern __shared__ uint32_t s_fid[];
@@ -308,6 +344,7 @@ __global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
       const float rr = pi.w * E.inv_cell + 0.5f + 0.0009765625f + um * 4.76837158203125e-7f;  // 2^-10, 2^-21
       reach = rr * rr;
     }
+    if constexpr (!LISTS) {
     // The 27 buckets are walked as nine rows of three (dx = -1, 0, 1 at fixed dy, dz).
     // A row's three ranges are loaded while the previous row is walked; within a row
     // the walk takes one candidate from every non-empty bucket per round, so the
@@ -371,21 +408,43 @@ __global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
           r0[q] += (live >> q) & 1u;
           if (!((hit >> q) & 1u)) continue;
           const uint32_t jid = jc[q];
-          if (jid == i) continue;
-          // insert by ascending id; a bucket reached twice yields the same id: skip it
-          uint32_t p = 0;
-          while (p < npp && fid[p * S] < jid) ++p;
-          if (p < npp && fid[p * S] == jid) continue;
-          if (npp == K) {
-            ovf = true;
-            if (p == K) continue;
-          } else {
-            ++npp;
-          }
-          for (uint32_t q2 = npp - 1; q2 > p; --q2) fid[q2 * S] = fid[(q2 - 1) * S];
-          fid[p * S] = jid;
+          if (jid != i) insert_partner(fid, S, K, jid, npp, ovf);
         }
       }
+    }
+    } else {
+    // Linked lists (Alg. 2): the three buckets of a row are walked together, one link
+    // of each per round (each link is a load that depends on the previous one).
+#pragma unroll 1
+    for (int row = 0; row < 9; ++row) {
+      const uint32_t hyz = hy[row % 3] ^ hz[row / 3];
+      const float g2yz = g2y[row % 3] + g2z[row / 3];
+      uint32_t jn[kWalkGroup];
+#pragma unroll
+      for (int q = 0; q < kWalkGroup; ++q)
+        jn[q] = (g2x[q] + g2yz <= reach) ? a.head[E.hbase + mod_nh(hx[q] ^ hyz, E)] : kListEnd;
+      for (;;) {
+        float4 pc[kWalkGroup];
+        uint32_t nx[kWalkGroup];
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < kWalkGroup; ++q)
+          if (jn[q] != kListEnd) {
+            any = true;
+            pc[q] = a.pos_id[jn[q]];
+            nx[q] = a.next[jn[q]];
+          }
+        if (!any) break;
+#pragma unroll
+        for (int q = 0; q < kWalkGroup; ++q) {
+          if (jn[q] == kListEnd) continue;
+          float d2;
+          float3 d;
+          if (jn[q] != i && sphere_hit(pi, pc[q], &d2, &d)) insert_partner(fid, S, K, jn[q], npp, ovf);
+          jn[q] = nx[q];
+        }
+      }
+    }
     }
     const size_t n = a.n;
     for (uint32_t c = 0; c < npp; ++c) {
@@ -804,7 +863,9 @@ __device__ __forceinline__ void integrate_particle(const StepArgs &a, int s, uin
   const float4 u = a.U[s][i];
   const float4 p = a.pos_id[i];
   const float invm = a.vel_id[i].w;
-  const float x = p.x + a.dt * u.x, y = p.y + a.dt * u.y, z = p.z + a.dt * u.z;
+  const float x = p.x + a.dt * u.x, y = p.y + a.dt * u.y;
+  float z = p.z + a.dt * u.z;
+  if (a.cyc_h > 0.f && z < a.cyc_lo) z += a.cyc_h;  // cyclic vertical boundary (gear tower)
   if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(u.x) && isfinite(u.y) && isfinite(u.z)))
     flag(a.ctrl, kFlagNonFinite);
   a.pos_id[i] = make_float4(x, y, z, p.w);
@@ -1057,8 +1118,8 @@ static inline cudaError_t mark(cudaEvent_t *ev, int k, cudaStream_t st) {
 }
 
 uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls) {
-  uint32_t k = 6;  // key, scan x3, wrench_sum, body_update
-  if (a.n) k += 3 + ((ls.fused_grid && !a.F) ? 1 : ls.iters);  // scatter, reorder, contacts, pja
+  uint32_t k = a.lists ? 4 : 6;  // key + list clear or scan x3, wrench_sum, body_update
+  if (a.n) k += (a.lists ? 1 : 3) + ((ls.fused_grid && !a.F) ? 1 : ls.iters);  // (scatter, reorder,) contacts, pja
   if (a.n_chunks) k += 1;  // integrate + wrench partials
   if (a.F) k += 1 + ls.iters;  // free_prep, free_update x I
   return k;
@@ -1086,19 +1147,28 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
     }                                                          \
   } while (0)
   GG_MARK(0);
-  GG_LAUNCH(k_key, dim3(grid_for(nk, 256)), 256, 0, a);
-  const uint32_t nblk = a.nh_pad / kScanTile;
-  GG_LAUNCH(k_scan_reduce, dim3(nblk), kScanThreads, 0, a);
-  GG_LAUNCH(k_scan_top, dim3(1), 1024, 0, a, nblk);
-  GG_LAUNCH(k_scan_down, dim3(nblk), kScanThreads, 0, a);
-  if (a.n) {
-    GG_LAUNCH(k_scatter, dim3(grid_for(a.n, 256)), 256, 0, a);
-    GG_LAUNCH(k_reorder, dim3(grid_for(a.n, 256)), 256, 0, a);
+  if (a.lists) {
+    GG_LAUNCH(k_list_clear, dim3(std::min<uint32_t>(grid_for(a.nh_total, 256), 4096u)), 256, 0, a);
+    GG_LAUNCH(k_key, dim3(grid_for(nk, 256)), 256, 0, a);
+  } else {
+    GG_LAUNCH(k_key, dim3(grid_for(nk, 256)), 256, 0, a);
+    const uint32_t nblk = a.nh_pad / kScanTile;
+    GG_LAUNCH(k_scan_reduce, dim3(nblk), kScanThreads, 0, a);
+    GG_LAUNCH(k_scan_top, dim3(1), 1024, 0, a, nblk);
+    GG_LAUNCH(k_scan_down, dim3(nblk), kScanThreads, 0, a);
+    if (a.n) {
+      GG_LAUNCH(k_scatter, dim3(grid_for(a.n, 256)), 256, 0, a);
+      GG_LAUNCH(k_reorder, dim3(grid_for(a.n, 256)), 256, 0, a);
+    }
   }
   GG_MARK(1);
-  if (a.n)
-    GG_LAUNCH(k_contacts, dim3(grid_for(a.n, kContactsBlock)), kContactsBlock,
-              (size_t)a.K * kContactsBlock * sizeof(uint32_t), a);
+  if (a.n) {
+    const size_t smem = (size_t)a.K * kContactsBlock * sizeof(uint32_t);
+    if (a.lists)
+      GG_LAUNCH(k_contacts<true>, dim3(grid_for(a.n, kContactsBlock)), kContactsBlock, smem, a);
+    else
+      GG_LAUNCH(k_contacts<false>, dim3(grid_for(a.n, kContactsBlock)), kContactsBlock, smem, a);
+  }
   if (a.F) GG_LAUNCH(k_free_prep, dim3(a.F), 1024, 0, a);
   GG_MARK(2);
   if (tp && a.n) {  // U^0 and lambda^0 = 0 open the tape
@@ -1138,6 +1208,19 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
   GG_MARK(4);
 #undef GG_LAUNCH
 #undef GG_MARK
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_sort_from_keys(const StepArgs &a, cudaStream_t st) {
+  if (a.n) k_hist_keys<<<grid_for(a.n, 256), 256, 0, st>>>(a);
+  const uint32_t nblk = a.nh_pad / kScanTile;
+  k_scan_reduce<<<nblk, kScanThreads, 0, st>>>(a);
+  k_scan_top<<<1, 1024, 0, st>>>(a, nblk);
+  k_scan_down<<<nblk, kScanThreads, 0, st>>>(a);
+  if (a.n) {
+    k_scatter<<<grid_for(a.n, 256), 256, 0, st>>>(a);
+    k_reorder<<<grid_for(a.n, 256), 256, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

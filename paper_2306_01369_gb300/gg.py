@@ -59,7 +59,8 @@ class GGParams(C.Structure):
                 ("hash_factor", C.c_uint32), ("hash_size", C.c_uint32), ("max_contacts", C.c_uint32),
                 ("max_body_contacts", C.c_uint32), ("max_bodies", C.c_uint32), ("density", C.c_float),
                 ("tuning", C.c_uint32), ("wrench_history", C.c_uint32), ("max_free_bodies", C.c_uint32),
-                ("free_contact_capacity", C.c_uint32), ("barrier_test_phantoms", C.c_uint32)]
+                ("free_contact_capacity", C.c_uint32), ("barrier_test_phantoms", C.c_uint32),
+                ("binning", C.c_uint32), ("cyclic_z", C.c_float * 2)]
 
 
 class GGBody(C.Structure):
@@ -124,7 +125,7 @@ def _stream(stream):
 
 
 def make_params(p, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0, max_free_bodies=0,
-                barrier_test_phantoms=0) -> GGParams:
+                barrier_test_phantoms=0, binning=0) -> GGParams:
     q = GGParams()
     q.struct_size = C.sizeof(GGParams)
     q.dt = p.dt
@@ -145,6 +146,9 @@ def make_params(p, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0, max_
     q.max_free_bodies = max_free_bodies
     q.free_contact_capacity = 0
     q.barrier_test_phantoms = barrier_test_phantoms
+    q.binning = binning
+    cz = getattr(p, "cyclic_z", (0.0, 0.0))
+    q.cyclic_z[0], q.cyclic_z[1] = cz[0], cz[1]
     return q
 
 
@@ -171,12 +175,12 @@ class Sim:
     """One libgg simulation (single environment, or batched when env_offsets is given)."""
 
     def __init__(self, pos_r, vel=None, mass=None, params=None, env_offsets=None, tuning=0, wrench_history=1,
-                 max_bodies=8, hash_factor=0, max_free_bodies=0, barrier_test_phantoms=0):
+                 max_bodies=8, hash_factor=0, max_free_bodies=0, barrier_test_phantoms=0, binning=0):
         L = load()
         self._L = L
         self.params = params
         self.gp = make_params(params, tuning, wrench_history, max_bodies, hash_factor, max_free_bodies,
-                              barrier_test_phantoms)
+                              barrier_test_phantoms, binning)
         n = int(pos_r.shape[0])
         self.n = n
         pp, dev = _ptr(pos_r)
@@ -241,12 +245,13 @@ class Sim:
         self._check(self._L.gg_set_particles(self.h, pp, vp, dev, _stream(stream)), "gg_set_particles")
 
     @classmethod
-    def from_scene(cls, scene, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0, device_inputs=None):
+    def from_scene(cls, scene, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0, device_inputs=None,
+                   binning=0):
         args = (scene.pos_r, scene.vel, scene.mass) if device_inputs is None else device_inputs
         n_free = sum(1 for b in scene.bodies if b.is_free)
         sim = cls(*args, params=scene.params, env_offsets=scene.env_offsets, tuning=tuning,
                   wrench_history=wrench_history, max_bodies=max_bodies, hash_factor=hash_factor,
-                  max_free_bodies=n_free)
+                  max_free_bodies=n_free, binning=binning)
         if scene.body_offsets is None:
             if scene.bodies:
                 sim.set_bodies(scene.bodies, 0)

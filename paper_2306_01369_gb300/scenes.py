@@ -553,3 +553,64 @@ def gear_bed(n=4096, seed=1005, n_gears=1, teeth=8, module=0.003, width=0.012, o
     assert pr.shape[0] == n
     return Scene(f"gear_bed_{n}_{n_gears}", pr, np.zeros((n, 3), np.float32), sphere_mass(pr[:, 3]), bodies,
                  Params(dt=1e-4, mu=0.5, pja_iters=20), n_steps, info={"foot": foot, "ra": ra})
+
+
+def gear_tower(n=65536, n_gears=10, seed=1006, radius=0.06, r0=2e-3, teeth=10, module=0.003, width=0.012,
+               omega=4.0, gap=0.04, n_steps=500, gear=None):
+    """The paper's helical-gear benchmark (Sec. III): n spheres (r0 +-10 %) in a tall
+    vertical tube of the given radius with a cyclic vertical boundary (spheres leaving
+    through the bottom re-enter at the top), and n_gears involute helical gears (GRID
+    bodies sharing one baked grid) on the axis every `gap` metres, each with a seeded
+    random orientation, spinning about its own axis at U(-omega, omega) rad/s.  The
+    spheres start on a jittered lattice inside the tube (sites touching a gear left
+    empty).  dt = 1e-4 s, 20 PJA iterations, mu = 0.5."""
+    jit = 0.10
+    pitch = 2.0 * r0 * (1 + jit) * 1.02
+    side = int(math.floor(2.0 * (radius - 1.2 * r0) / pitch))
+    foot = side * pitch
+    per_layer = None
+    g = gear if gear is not None else gear_body(teeth, module, width, margin=max(0.004, 2.5 * r0))
+    sdf = helical_gear_sdf(teeth, module, width)
+    ra = 0.5 * module * teeth + module
+    u = uniform(seed * 13 + 5, 4 * max(n_gears, 1))
+    gears = []
+    for k in range(n_gears):
+        rv = (np.array(u[4 * k:4 * k + 3]) * 2.0 - 1.0) * math.pi / math.sqrt(3.0)
+        q = _quat_from_rotvec(rv)
+        w = (2.0 * u[4 * k + 3] - 1.0) * omega
+        qa = np.array(q, np.float64)
+        a, b, c, d = qa / np.linalg.norm(qa)
+        axis = np.array([2 * (b * d + a * c), 2 * (c * d - a * b), 1 - 2 * (b * b + c * c)])  # R e_z
+        z = gap * (k + 1)
+        gears.append((np.array([0.0, 0.0, z]), q, w * axis))
+    # enough lattice layers for n spheres after removing the sites in the tube's
+    # corners and around the gears
+    inside = None
+    layers = 8
+    while True:
+        cand, _ = jittered_lattice((side, side, layers), side * side * layers, r0, jit, seed,
+                                   origin=(-0.5 * foot, -0.5 * foot, 0.5 * pitch), pitch=pitch)
+        x = cand[:, :3].astype(np.float64)
+        keep = np.hypot(x[:, 0], x[:, 1]) < radius - cand[:, 3] - 0.2 * r0
+        for pos, q, _ in gears:
+            qa = np.array(q, np.float64)
+            a, b, c, d = qa / np.linalg.norm(qa)
+            R = np.array([[1 - 2 * (c * c + d * d), 2 * (b * c - a * d), 2 * (b * d + a * c)],
+                          [2 * (b * c + a * d), 1 - 2 * (b * b + d * d), 2 * (c * d - a * b)],
+                          [2 * (b * d - a * c), 2 * (c * d + a * b), 1 - 2 * (b * b + c * c)]])
+            y = (x - pos) @ R
+            near = np.linalg.norm(y, axis=1) < ra + width + 2 * r0
+            if near.any():
+                idx = np.nonzero(near)[0]
+                keep[idx[sdf(y[near]) < cand[idx, 3] + 2e-4]] = False
+        if keep.sum() >= n:
+            break
+        layers = int(layers * 1.3) + 4
+    pr = cand[keep][:n].copy()
+    top = max(float(pr[:, 2].max()) + 2 * r0, gap * (n_gears + 1))
+    bodies = [Body(kind=TUBE, shape=(radius,))]
+    for pos, q, w in gears:
+        bodies.append(Body(kind=GRID, pos=tuple(pos), quat=q, ang_vel=tuple(float(v) for v in w), grid=g.grid))
+    return Scene(f"gear_tower_{n}_{n_gears}", pr, np.zeros((n, 3), np.float32), sphere_mass(pr[:, 3]), bodies,
+                 Params(dt=1e-4, mu=0.5, pja_iters=20, cyclic_z=(0.0, top)), n_steps,
+                 info={"radius": radius, "height": top, "ra": ra})

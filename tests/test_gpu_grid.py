@@ -154,3 +154,92 @@ def test_adjoint_with_grid_tool_matches_oracle_gradient(torch, grid_tool_scene):
     cos = float((g_tw * want).sum() / (np.linalg.norm(g_tw) * np.linalg.norm(want)))
     rel = float(np.abs(g_tw - want).max() / np.abs(want).max())
     assert cos > 0.999 and rel < 1e-2, (cos, rel)
+
+
+# --------------------------------------------------------------------------- #
+# the gear tower: tube wall, gears at random orientations, cyclic vertical boundary
+# --------------------------------------------------------------------------- #
+
+@pytest.fixture(scope="module")
+def tower_scene():
+    return S.gear_tower(n=4096, n_gears=3)
+
+
+def test_tower_contacts_and_dynamics_lockstep(gg, tower_scene):
+    sim, o, sc = lockstep_pair(gg, tower_scene, 1500)
+    want = o.contacts()
+    sim.step(1)
+    sim.sync()
+    assert_contacts_equal(sim.contacts(), want)
+    assert int((want["bc_b"] >= 1).sum()) > 10       # contacts with the gears
+    o.step(1)
+    assert vel_err(sim.vel(), o.v, sc, length=0.1) < 1
+
+
+def test_tube_wall_contacts_and_dynamics(gg, orc):
+    """Spheres pressed slightly into the tube's wall (and into each other): contact
+    sets bit-exact, one-step velocities within tolerance."""
+    rng = np.random.default_rng(8)
+    n, R, r = 600, 0.06, 0.002
+    ang = rng.uniform(0, 2 * np.pi, n)
+    rho = R - r + rng.uniform(0.0, 0.3 * r, n)
+    pr = np.stack([rho * np.cos(ang), rho * np.sin(ang), rng.uniform(0.0, 0.1, n), np.full(n, r)], 1).astype(F32)
+    vel = (rng.normal(size=(n, 3)) * 0.05).astype(F32)
+    sc = S.Scene("tube_wall", pr, vel, S.sphere_mass(pr[:, 3]), [S.Body(kind=S.TUBE, shape=(R,))],
+                 S.Params(dt=1e-4, mu=0.5, pja_iters=20), 1)
+    sim = gg.Sim.from_scene(sc)
+    o = orc.Sim(sc.pos_r, sc.vel, sc.mass, sc.bodies, sc.params)
+    want = o.contacts()
+    sim.step(1)
+    sim.sync()
+    assert int(want["stats"]["n_body"]) > 300
+    assert_contacts_equal(sim.contacts(), want)
+    o.step(1)
+    assert vel_err(sim.vel(), o.v, sc, length=0.1) < 1
+
+
+def test_cyclic_boundary_wraps_like_the_oracle(gg, orc):
+    """Spheres falling through the bottom of the period re-enter at the top with their
+    velocity; positions agree with the oracle to float32 rounding over many wraps."""
+    p = S.Params(dt=1e-3, mu=0.5, pja_iters=5, cyclic_z=(0.0, 0.0625))
+    rng = np.random.default_rng(5)
+    pr = np.zeros((64, 4), F32)
+    pr[:, 0] = rng.uniform(-1, 1, 64) * 0.5
+    pr[:, 1] = rng.uniform(-1, 1, 64) * 0.5
+    pr[:, 2] = rng.uniform(0.0, 0.06, 64)
+    pr[:, 3] = 0.001
+    sim = gg.Sim(pr, np.zeros((64, 3), F32), np.full(64, 1e-3, F32), p)
+    o = orc.Sim(pr, np.zeros((64, 3), F32), np.full(64, 1e-3, F32), [], p)
+    sim.step(300)
+    o.step(300)
+    x = sim.pos()[:, :3].astype(np.float64)
+    assert np.all((x[:, 2] >= 0.0) & (x[:, 2] < 0.0625))
+    assert np.abs(sim.vel() - o.v).max() < 1e-5 * np.abs(o.v).max()
+    dz = np.abs(x[:, 2] - o.x[:, 2])
+    assert dz.max() < 1e-5, dz.max()
+
+
+# --------------------------------------------------------------------------- #
+# binning by linked lists (Alg. 2) against the counting sort
+# --------------------------------------------------------------------------- #
+
+@pytest.mark.parametrize("which", ["gear_bed", "scoop", "batched"])
+def test_list_binning_gives_identical_results(gg, which, gear_scene):
+    if which == "gear_bed":
+        sc = gear_scene
+    elif which == "scoop":
+        sc = S.scoop_bed(n=4096, n_steps=60, dims=(16, 16, 16))
+    else:
+        sc = S.batched_beds(n_envs=6, n_steps=40, n_min=1024, n_max=4096)
+    out = []
+    for binning in (1, 2):
+        sim = gg.Sim.from_scene(sc, binning=binning)    # the autotuner picks a set of that binning
+        sim.step(30)
+        assert (sim.tuning_selected >= 7) == (binning == 2)
+        out.append((sim.pos(), sim.vel(), sim.cell_keys(), sim.contacts(), sim.sort_perm(), sim.cell_start()))
+        sim.close()
+    (p0, v0, k0, c0, s0, t0), (p1, v1, k1, c1, s1, t1) = out
+    assert np.array_equal(k0, k1)
+    assert np.array_equal(s0, s1) and np.array_equal(t0, t1)   # lists: the keys sorted on demand
+    assert_contacts_equal(c1, c0)
+    assert np.array_equal(p0, p1) and np.array_equal(v0, v1)
