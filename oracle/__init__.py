@@ -50,6 +50,13 @@ class OrcBody(C.Structure):
                 ("grid_dims", C.c_uint32 * 3)]
 
 
+class OrcCamera(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("width", C.c_int32), ("height", C.c_int32), ("pos", C.c_double * 3),
+                ("quat", C.c_double * 4), ("extent", C.c_double * 2), ("fov_y", C.c_double),
+                ("near_clip", C.c_double), ("far_clip", C.c_double), ("empty", C.c_double),
+                ("body_mask", C.c_uint32), ("march_steps", C.c_uint32), ("march_eps", C.c_double)]
+
+
 class OrcStats(C.Structure):
     _fields_ = [("n_pp", C.c_int64), ("n_body", C.c_int64), ("n_corner", C.c_int64), ("max_pp", C.c_int32),
                 ("max_body", C.c_int32), ("max_psi", C.c_double), ("ncp_residual", C.c_double)]
@@ -84,6 +91,9 @@ def lib():
                                P(OrcStats)]
         L.orc_sdf.restype = C.c_double
         L.orc_sdf.argtypes = [P(OrcBody), P(C.c_double), P(C.c_double)]
+        L.orc_render.restype = None
+        L.orc_render.argtypes = [P(OrcCamera), C.c_uint32, P(C.c_double), P(C.c_double), C.c_uint32, P(OrcBody),
+                                 P(C.c_double)]
         L.orc_scoop_loss.restype = C.c_double
         L.orc_scoop_loss.argtypes = [C.c_uint32, P(C.c_double), P(C.c_double), P(OrcBody), C.c_double]
         _lib = L
@@ -195,6 +205,26 @@ def contacts(x, r, bodies, params, brute=False, n_threads=1):
                    _p(bc_b, C.c_uint32), _p(bc_geom, C.c_double), C.byref(st))
     return {"pp_off": pp_off, "pp_j": pp_j[:npp], "pp_geom": pp_geom[:npp], "bc_off": bc_off,
             "bc_b": bc_b[:nbc], "bc_geom": bc_geom[:nbc], "stats": st.as_dict()}
+
+
+def render(cam, x, r, bodies) -> np.ndarray:
+    """Depth observation (height, width) of spheres (x: (n, 3), r: (n,)) and bodies."""
+    c = OrcCamera()
+    c.kind, c.width, c.height = int(cam.kind), int(cam.width), int(cam.height)
+    for k in range(3):
+        c.pos[k] = _f32(cam.pos[k])
+    for k in range(4):
+        c.quat[k] = _f32(cam.quat[k])
+    c.extent[0], c.extent[1] = _f32(cam.extent[0]), _f32(cam.extent[1])
+    c.fov_y, c.near_clip, c.far_clip, c.empty = _f32(cam.fov_y), _f32(cam.near), _f32(cam.far), _f32(cam.empty)
+    c.body_mask, c.march_steps, c.march_eps = int(cam.body_mask) & 0xFFFFFFFF, int(cam.march_steps), _f32(cam.march_eps)
+    x = np.ascontiguousarray(np.asarray(x, np.float64)[:, :3])
+    r = np.ascontiguousarray(r, np.float64)
+    ba = make_bodies(bodies)
+    out = np.zeros((c.height, c.width), np.float64)
+    lib().orc_render(C.byref(c), x.shape[0], _p(x, C.c_double), _p(r, C.c_double), len(bodies), ba,
+                     _p(out, C.c_double))
+    return out
 
 
 def sdf(body, xw) -> tuple:

@@ -1115,3 +1115,145 @@ double orc_scoop_loss(uint32_t n, const double *x, const double *m, const orc_bo
   }
   return L;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Depth observations (Sec. III-A)                                            */
+/* ------------------------------------------------------------------------- */
+
+/* SDF used to step the sphere tracing: the body's FP32 SDF; outside a GRID body's
+ * sampled box (where the SDF is not defined) the distance to that box, at least eps. */
+static float march_f32(const bodyf *b, const float *y, float eps) {
+  int br;
+  float f = sdf_f32(b, y, &br);
+  if (b->kind != ORC_GRID || br >= 0) return f;
+  float q[3];
+  for (int k = 0; k < 3; ++k) {
+    float lo = b->s[k];
+    float hi = b->s[k] + b->s[3] * (float)(b->gn[k] - 1);
+    float a = lo - y[k];
+    float c = y[k] - hi;
+    q[k] = fmaxf(fmaxf(a, c), 0.0f);
+  }
+  float s2 = q[0] * q[0];
+  float t = q[1] * q[1];
+  s2 = s2 + t;
+  t = q[2] * q[2];
+  s2 = s2 + t;
+  return fmaxf(sqrtf(s2), eps);
+}
+
+void orc_render(const orc_camera *cam, uint32_t n, const double *x, const double *r, uint32_t nb,
+                const orc_body *bodies, double *out) {
+  const int W = cam->width, H = cam->height;
+  if (cam->kind == 0) {
+    const float cx = (float)cam->pos[0], cy = (float)cam->pos[1];
+    const float ex = (float)cam->extent[0], ey = (float)cam->extent[1];
+    const float sx = ex / (float)W, sy = ey / (float)H;
+    const float bx = cx - 0.5f * ex, by = cy - 0.5f * ey;
+    for (int v = 0; v < H; ++v)
+      for (int u = 0; u < W; ++u) {
+        const float px = bx + ((float)u + 0.5f) * sx;
+        const float py = by + ((float)v + 0.5f) * sy;
+        double best = -INFINITY;
+        int hit = 0;
+        for (uint32_t i = 0; i < n; ++i) {
+          const float dx = (float)x[3 * i] - px, dy = (float)x[3 * i + 1] - py, rf = (float)r[i];
+          float d2 = dx * dx;
+          float t = dy * dy;
+          d2 = d2 + t;
+          if (!(d2 <= rf * rf)) continue;
+          const double ddx = x[3 * i] - (double)px, ddy = x[3 * i + 1] - (double)py;
+          const double h2 = r[i] * r[i] - (ddx * ddx + ddy * ddy);
+          const double h = x[3 * i + 2] + sqrt(h2 > 0 ? h2 : 0.0);
+          if (!hit || h > best) best = h;
+          hit = 1;
+        }
+        out[(size_t)v * W + u] = hit ? best : cam->empty;
+      }
+    return;
+  }
+  /* perspective depth */
+  const float f = (float)(0.5 * (double)H / tan(0.5 * (double)(float)cam->fov_y));
+  float q[4], R[9], o[3];
+  for (int k = 0; k < 4; ++k) q[k] = (float)cam->quat[k];
+  rot_f32(q, R);
+  for (int k = 0; k < 3; ++k) o[k] = (float)cam->pos[k];
+  const float nearc = (float)cam->near_clip, farc = (float)cam->far_clip, eps = (float)cam->march_eps;
+  const uint32_t steps = cam->march_steps;
+  bodyf *bf = (bodyf *)malloc(sizeof(bodyf) * (nb ? nb : 1));
+  for (uint32_t b = 0; b < nb; ++b) body_to_f32(&bodies[b], &bf[b]);
+  for (int v = 0; v < H; ++v)
+    for (int u = 0; u < W; ++u) {
+      const float ax = ((float)u + 0.5f) - 0.5f * (float)W;
+      const float ay = ((float)v + 0.5f) - 0.5f * (float)H;
+      const float dxc = ax / f, dyc = ay / f;
+      float s2 = dxc * dxc;
+      float t2 = dyc * dyc;
+      s2 = s2 + t2;
+      s2 = s2 + 1.0f;
+      const float nr = sqrtf(s2);
+      const float dc[3] = {dxc / nr, dyc / nr, 1.0f / nr};
+      float d[3];
+      for (int k = 0; k < 3; ++k) {
+        float a = R[3 * k] * dc[0];
+        float c = R[3 * k + 1] * dc[1];
+        a = a + c;
+        c = R[3 * k + 2] * dc[2];
+        d[k] = a + c;
+      }
+      double best = INFINITY;
+      /* spheres: FP32 hit decision, FP64 distance */
+      for (uint32_t i = 0; i < n; ++i) {
+        const float oc0 = (float)x[3 * i] - o[0], oc1 = (float)x[3 * i + 1] - o[1], oc2 = (float)x[3 * i + 2] - o[2];
+        const float rf = (float)r[i];
+        float b = d[0] * oc0;
+        float tt = d[1] * oc1;
+        b = b + tt;
+        tt = d[2] * oc2;
+        b = b + tt;
+        float c = oc0 * oc0;
+        tt = oc1 * oc1;
+        c = c + tt;
+        tt = oc2 * oc2;
+        c = c + tt;
+        c = c - rf * rf;
+        const float disc = b * b - c;
+        if (!(disc >= 0.0f)) continue;
+        const float t0 = b - sqrtf(disc);
+        if (!(t0 >= nearc && t0 <= farc)) continue;
+        const double e0 = x[3 * i] - (double)o[0], e1 = x[3 * i + 1] - (double)o[1], e2 = x[3 * i + 2] - (double)o[2];
+        const double bb = (double)d[0] * e0 + (double)d[1] * e1 + (double)d[2] * e2;
+        const double cc = e0 * e0 + e1 * e1 + e2 * e2 - r[i] * r[i];
+        const double dd = bb * bb - cc;
+        const double td = bb - sqrt(dd > 0 ? dd : 0.0);
+        if (td < best) best = td;
+      }
+      /* bodies: FP32 sphere tracing */
+      if (nb && cam->body_mask) {
+        float t = nearc;
+        for (uint32_t k = 0; k < steps; ++k) {
+          float p[3];
+          for (int a = 0; a < 3; ++a) {
+            float m = t * d[a];
+            p[a] = o[a] + m;
+          }
+          float fmin = INFINITY;
+          for (uint32_t b = 0; b < nb && b < 32; ++b) {
+            if (!((cam->body_mask >> b) & 1u)) continue;
+            float y[3];
+            to_body_f32(&bf[b], p, y);
+            const float fb = march_f32(&bf[b], y, eps);
+            fmin = fminf(fmin, fb);
+          }
+          if (fmin < eps) {
+            if ((double)t < best) best = (double)t;
+            break;
+          }
+          t = t + fmin;
+          if (!(t <= farc)) break;
+        }
+      }
+      out[(size_t)v * W + u] = best <= (double)farc ? best : (double)farc;
+    }
+  free(bf);
+}

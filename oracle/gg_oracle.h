@@ -100,6 +100,32 @@ int orc_step(const orc_params *p, uint32_t n, double *x, double *v, const double
              const double *m, uint32_t n_bodies, orc_body *bodies, const double *twist,
              double *wrench, double *pp_lam, double *bc_lam, orc_stats *st);
 
+/*
+ * Depth observations (the paper's Sec. III-A "sky" and "ego" cameras), per pixel by
+ * brute force.  kind 0 (height): orthographic, looking down; pixel (u, v) samples the
+ * point (pos[0] - extent[0]/2 + (u + 1/2) extent[0]/width, pos[1] - ... same in y);
+ * its value is the highest particle surface point above it, max z_i + sqrt(r_i^2 - d^2)
+ * over spheres whose horizontal distance d to the point is <= r_i (else `empty`).
+ * kind 1 (depth): pinhole at pos, orientation quat (camera x right, y down, z along the
+ * optical axis), vertical field of view fov_y; pixel (u, v) looks along the unit ray
+ * ((u + 1/2 - W/2) / f, (v + 1/2 - H/2) / f, 1), f = (H/2) / tan(fov_y / 2); its value is
+ * the distance along the ray to the first surface in [near_clip, far_clip]: spheres
+ * exactly, bodies in body_mask by sphere tracing (march_steps steps, hit when the SDF
+ * is below march_eps); far_clip if none.  Decisions (coverage, ray-sphere hit, the
+ * tracing) are taken in FP32 in a fixed order; sphere values are FP64.
+ * out: height * width values, row v = 0 first.
+ */
+typedef struct {
+  int32_t kind, width, height;
+  double pos[3], quat[4], extent[2];
+  double fov_y, near_clip, far_clip, empty;
+  uint32_t body_mask, march_steps;
+  double march_eps;
+} orc_camera;
+
+void orc_render(const orc_camera *cam, uint32_t n, const double *x, const double *r, uint32_t n_bodies,
+                const orc_body *bodies, double *out);
+
 /* Signed distance of world point xw to body b (FP64), for tests and losses. */
 double orc_sdf(const orc_body *b, const double *xw, double *normal_world);
 

@@ -82,6 +82,28 @@ class Body:
         return tuple(float(v) for v in s[:12])
 
 
+HEIGHT_CAMERA = 0  # orthographic, looking down: per pixel the highest particle surface point
+DEPTH_CAMERA = 1   # perspective pinhole: per pixel the distance to the first surface
+
+
+@dataclass
+class Camera:
+    """A depth observation (the paper's sky and ego cameras, Sec. III-A)."""
+    kind: int = DEPTH_CAMERA
+    width: int = 36
+    height: int = 36
+    pos: tuple = (0.0, 0.0, 0.0)
+    quat: tuple = (1.0, 0.0, 0.0, 0.0)      # camera -> world; camera x right, y down, z forward
+    extent: tuple = (1.0, 1.0)              # height camera: rectangle size in x, y
+    fov_y: float = 1.0                      # depth camera: vertical field of view (rad)
+    near: float = 0.01
+    far: float = 2.0
+    empty: float = 0.0                      # height camera: value where no particle is
+    body_mask: int = 0xFFFFFFFF             # depth camera: bodies the rays see
+    march_steps: int = 64
+    march_eps: float = 1e-4
+
+
 @dataclass
 class Params:
     dt: float = 1e-4

@@ -655,3 +655,97 @@ def test_tube_sdf_values(orc):
         rho = math.hypot(y[0], y[1])
         if rho > 0:
             assert np.allclose(n, [-y[0] / rho, -y[1] / rho, 0.0], atol=1e-12)
+
+
+# --------------------------------------------------------------------------- #
+# depth observations (Sec. III-A sky and ego cameras)
+# --------------------------------------------------------------------------- #
+
+def test_height_camera_single_sphere(orc):
+    """Orthographic height map of one sphere: z + sqrt(r^2 - d^2) at the pixel centres
+    it covers (d = horizontal distance), `empty` elsewhere."""
+    cam = S.Camera(kind=S.HEIGHT_CAMERA, width=16, height=8, pos=(0.0, 0.0, 0.0), extent=(0.032, 0.016),
+                   empty=-1.0)
+    x = np.array([[0.0011, -0.0007, 0.02]])
+    r = np.array([0.005])
+    img = orc.render(cam, x, r, [])
+    covered = 0
+    for v in range(8):
+        for u in range(16):
+            # pixel centres are float32 values (the camera's sample points)
+            px = float(F32(F32(-0.016) + F32(F32(u + 0.5) * F32(F32(0.032) / F32(16)))))
+            py = float(F32(F32(-0.008) + F32(F32(v + 0.5) * F32(F32(0.016) / F32(8)))))
+            d2 = (x[0, 0] - px) ** 2 + (x[0, 1] - py) ** 2
+            if d2 < r[0] ** 2 * (1 - 1e-5):
+                assert abs(img[v, u] - (0.02 + math.sqrt(r[0] ** 2 - d2))) < 1e-9
+                covered += 1
+            elif d2 > r[0] ** 2 * (1 + 1e-5):
+                assert img[v, u] == -1.0
+    assert covered > 10
+
+
+def test_height_camera_takes_the_highest_surface(orc):
+    cam = S.Camera(kind=S.HEIGHT_CAMERA, width=4, height=4, pos=(0.0, 0.0, 0.0), extent=(0.008, 0.008))
+    x = np.array([[0.001, 0.001, 0.01], [0.001, 0.001, 0.013], [0.001, 0.001, 0.004]])
+    r = np.array([0.002, 0.002, 0.002])
+    img = orc.render(cam, x, r, [])
+    assert abs(img[2, 2] - (0.013 + 0.002)) < 1e-12   # pixel centre (0.001, 0.001): right above all three
+
+
+def test_depth_camera_sphere_and_plane(orc):
+    """Pinhole camera 0.5 m above a floor plane looking straight down: per pixel the
+    ray distance to the plane is 0.5 / (d . -z); a sphere on the axis shows its near
+    surface 0.5 - z_c - r away at the centre pixels; a distance beyond `far` clips."""
+    down = S._quat_from_rotvec((math.pi, 0.0, 0.0))   # camera z (forward) -> world -z
+    cam = S.Camera(kind=S.DEPTH_CAMERA, width=12, height=10, pos=(0.0, 0.0, 0.5), quat=down, fov_y=0.8,
+                   near=0.01, far=2.0, march_steps=200, march_eps=1e-6)
+    floor = S.Body(kind=S.PLANE)
+    img = orc.render(cam, np.zeros((0, 3)), np.zeros(0), [floor])
+    f = 0.5 * 10 / math.tan(0.4)
+    for v in range(10):
+        for u in range(12):
+            dx, dy = (u + 0.5 - 6) / f, (v + 0.5 - 5) / f
+            t = 0.5 * math.sqrt(dx * dx + dy * dy + 1.0)   # the ray's z component is -1/|(dx, dy, 1)|
+            assert abs(img[v, u] - t) < 2e-6, (u, v, img[v, u], t)
+    img = orc.render(cam, np.array([[0.0, 0.0, 0.1]]), np.array([0.05]), [floor])
+    # a sphere below the camera: ray (dx, -dy, -1) / n from (0, 0, 0.5) meets the sphere
+    # of radius 0.05 about (0, 0, 0.1) at t = b - sqrt(b^2 - 0.4^2 + 0.05^2), b = 0.4 / n
+    hits = 0
+    for v in range(10):
+        for u in range(12):
+            dx, dy = (u + 0.5 - 6) / f, (v + 0.5 - 5) / f
+            nrm = math.sqrt(dx * dx + dy * dy + 1.0)
+            b = 0.4 / nrm
+            disc = b * b - 0.4 ** 2 + 0.05 ** 2
+            if disc > 1e-6:
+                assert abs(img[v, u] - (b - math.sqrt(disc))) < 1e-6
+                hits += 1
+            elif disc < -1e-6:
+                assert abs(img[v, u] - 0.5 * nrm) < 2e-6
+    assert hits >= 4
+    far = S.Camera(kind=S.DEPTH_CAMERA, width=4, height=4, pos=(0.0, 0.0, 5.0), quat=down, fov_y=0.5, far=2.0)
+    assert np.all(orc.render(far, np.zeros((0, 3)), np.zeros(0), [floor]) == 2.0)
+
+
+def test_depth_camera_traces_a_box_and_a_grid_box_alike(orc):
+    """Sphere tracing a closed-form box and the same box baked onto a grid (outside the
+    samples the tracing steps by the distance to the sampled box) gives the same face
+    distance, 0.3 - 0.05 along the optical axis."""
+    half = (0.05, 0.04, 0.03)
+    box = S.Body(kind=S.BOX, shape=half)
+
+    def f(y):
+        q = np.abs(y) - np.array(half)
+        return np.linalg.norm(np.maximum(q, 0.0), axis=-1) + np.minimum(q.max(axis=-1), 0.0)
+
+    grid = S.Body(kind=S.GRID, grid=S.bake_grid(f, (-0.0625, -0.0625, -0.0625), (0.0625, 0.0625, 0.0625), 1.0 / 256))
+    look = S._quat_from_rotvec((0.0, -math.pi / 2, 0.0))  # camera z (forward) -> world -x
+    cam = S.Camera(kind=S.DEPTH_CAMERA, width=6, height=6, pos=(0.3, 0.0, 0.0), quat=look, fov_y=0.2,
+                   march_steps=300, march_eps=1e-6)
+    a = orc.render(cam, np.zeros((0, 3)), np.zeros(0), [box])
+    b = orc.render(cam, np.zeros((0, 3)), np.zeros(0), [grid])
+    fz = 0.5 * 6 / math.tan(0.1)
+    dx = 0.5 / fz
+    want = 0.25 * math.sqrt(1 + 2 * dx * dx)   # pixel (2, 2)/(3, 3): the rays next to the axis hit x = 0.05
+    assert abs(a[2, 2] - want) < 1e-5 and abs(a[3, 3] - want) < 1e-5
+    assert np.allclose(a, b, atol=1e-5)
