@@ -410,6 +410,8 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
                                          "helical gears (GRID bodies: 10 teeth, module 3 mm, 0.75 mm samples) "
                                          "spinning at U(-4, 4) rad/s, I=20; timed steps 300-400",
                              "by_gear_count": rates, "grid_samples": int(gear.grid.values.size)}
+    # depth observations (Sec. III-A): the 72x36 sky camera and the 36x36 ego camera on
+    # the settled 1M-sphere excavation bed are timed in the excavation block below
     # ablations of the paper's design choices on the column (262,144 spheres, 1,000
     # steps into the collapse): binning by counting sort vs the paper's per-bucket
     # linked lists (Alg. 2), and the hash table size n_h (Fig. hashtable-benchmark,
@@ -443,8 +445,31 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
         ms = _timed_steps(sim, steps_exc, stream, torch)
         sim.sync(stream)
         st = sim.stats()
+        # the observations of one step: sky camera over the whole bed, ego camera from the
+        # scoop's side looking at the bed (every body traced)
+        foot = ex.info["side"] * ex.info["pitch"]
+        sky = scenes.Camera(kind=scenes.HEIGHT_CAMERA, width=72, height=36, extent=(foot, 0.5 * foot), empty=0.0)
+        ego = scenes.Camera(kind=scenes.DEPTH_CAMERA, width=36, height=36, pos=(-0.45 * foot, 0.0, 0.3),
+                            quat=scenes._quat_from_rotvec((0.0, 2.3, 0.0)), fov_y=1.2, near=0.01, far=1.5,
+                            march_steps=96, march_eps=1e-4)
+        img_s = torch.empty((36, 72), dtype=torch.float32, device=dev)
+        img_e = torch.empty((36, 36), dtype=torch.float32, device=dev)
+        for _ in range(3):
+            sim.render(sky, out=img_s, stream=stream)
+            sim.render(ego, out=img_e, stream=stream)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        for _ in range(20):
+            sim.render(sky, out=img_s, stream=stream)
+        e1.record(stream)
+        for _ in range(20):
+            sim.render(ego, out=img_e, stream=stream)
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        cams = {"sky_72x36_us": 1e3 * e0.elapsed_time(e1) / 20, "ego_36x36_us": 1e3 * e1.elapsed_time(e2) / 20,
+                "ego_pixels_hit": int((img_e < 1.5).sum())}
         out["excavation"] = {"workload": f"1,048,576 spheres, scoop + 2 free cubes + container, I=30, bed settled "
-                                         f"for {settle_steps_exc} steps before the scoop digs",
+                                         f"for {settle_steps_exc} steps before the scoop digs", "cameras": cams,
                              "particle_steps_per_s": ex.n * steps_exc / (ms * 1e-3), "ms_per_step": ms / steps_exc,
                              "timed_steps": [10, 10 + steps_exc], "n_pp_last": st["n_pp"], "n_body_last": st["n_body"],
                              "mean_pp_per_particle": st["n_pp"] / ex.n}

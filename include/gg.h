@@ -241,6 +241,45 @@ GG_API size_t gg_field_bytes(const gg_sim *sim, gg_field field);
 GG_API gg_status gg_readback(gg_sim *sim, gg_field field, void *dst, size_t bytes, int dst_on_device,
                       void *stream);
 
+/*
+ * Depth observations computed on the device (Sec. III-A: the "sky" and "ego" cameras).
+ *  GG_CAMERA_HEIGHT: orthographic, looking down.  Pixel (u, v) samples the point
+ *    (pos[0] - extent[0]/2 + (u + 1/2) extent[0]/width, pos[1] - extent[1]/2 + (v + 1/2)
+ *    extent[1]/height) (FP32, in that order); its value is the highest particle surface
+ *    above it, max z_i + sqrt(r_i^2 - d^2) over the spheres whose horizontal distance d
+ *    to the point is <= r_i, else `empty`.
+ *  GG_CAMERA_DEPTH: pinhole at pos with orientation quat (unit; camera -> world; camera
+ *    x right, y down, z along the optical axis), vertical field of view fov_y.  Pixel
+ *    (u, v) looks along the unit ray ((u + 1/2 - width/2)/f, (v + 1/2 - height/2)/f, 1),
+ *    f = (height/2) / tan(fov_y/2); its value is the distance along the ray to the first
+ *    surface in [near_clip, far_clip]: spheres exactly, the bodies in body_mask (bit b =
+ *    body b of the environment, b < 32) by sphere tracing (march_steps steps from
+ *    near_clip, a hit when the SDF falls below march_eps); far_clip if none.
+ * Images are float[height][width], row v = 0 first, at most 4096 x 4096.
+ */
+typedef enum { GG_CAMERA_HEIGHT = 0, GG_CAMERA_DEPTH = 1 } gg_camera_kind;
+
+typedef struct {
+  uint32_t struct_size;  /* sizeof(gg_camera) */
+  uint32_t kind;         /* gg_camera_kind */
+  uint32_t width, height;
+  float pos[3];          /* DEPTH: camera origin; HEIGHT: centre of the image rectangle (x, y) */
+  float quat[4];         /* DEPTH: orientation (w, x, y, z), camera -> world */
+  float extent[2];       /* HEIGHT: rectangle size along world x and y */
+  float fov_y;           /* DEPTH: radians, in (0, pi) */
+  float near_clip, far_clip;  /* DEPTH: 0 < near_clip < far_clip */
+  float empty;           /* HEIGHT: value of pixels no particle covers */
+  uint32_t body_mask;    /* DEPTH */
+  uint32_t march_steps;  /* DEPTH: 0 -> 64 */
+  float march_eps;       /* DEPTH: 0 -> 1e-4 */
+} gg_camera;
+
+/* Render environment env's current state into out (float[height][width]); out on the
+ * device: asynchronous on `stream`, else waits.  May allocate a scratch image (outside
+ * gg_step). */
+GG_API gg_status gg_render(gg_sim *sim, uint32_t env, const gg_camera *camera, float *out, int out_on_device,
+                           void *stream);
+
 /* Restore a GG_FIELD_STATE checkpoint taken from a simulation with the same sizes. */
 GG_API gg_status gg_set_state(gg_sim *sim, const void *state, size_t bytes, int on_device, void *stream);
 

@@ -18,8 +18,10 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code: no fused multiply-add contraction (Arm's gcc contracts by default), so the
+# few host-side float computations that feed FP32 decisions round like the oracle's
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-              "--expt-relaxed-constexpr"]
+              "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr"]
 
 
 def _nvcc() -> str:

@@ -65,6 +65,9 @@ struct gg_sim {
   void *staging = nullptr;
   size_t staging_bytes = 0;
   float *vel3 = nullptr;  // n*3 staging for velocity upload / readback
+  uint32_t *render_img = nullptr;  // gg_render scratch (ordered bits per pixel) and ...
+  float *render_out = nullptr;     // ... device image for host destinations
+  size_t render_px = 0;
   // differentiation: checkpoints, per-step tape, adjoint buffers
   struct {
     uint32_t n_steps = 0, K = 0, taped = 0, tool = 0xffffffffu;
@@ -196,6 +199,23 @@ gg_status ad_alloc(gg_sim *s, T **ptr, size_t count) {
 }
 
 // Launch shape k (1-based); a fused shape gets its resident grid from the occupancy.
+// Rotation of a float quaternion (w, x, y, z), each entry in the order the step's
+// kernels use (host code is compiled without multiply-add contraction).
+void rot_from_quat(const float *q, float *R) {
+  const float w = q[0], x = q[1], y = q[2], z = q[3];
+  const float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y,
+              wz = w * z;
+  R[0] = 1.0f - 2.0f * (yy + zz);
+  R[1] = 2.0f * (xy - wz);
+  R[2] = 2.0f * (xz + wy);
+  R[3] = 2.0f * (xy + wz);
+  R[4] = 1.0f - 2.0f * (xx + zz);
+  R[5] = 2.0f * (yz - wx);
+  R[6] = 2.0f * (xz - wy);
+  R[7] = 2.0f * (yz + wx);
+  R[8] = 1.0f - 2.0f * (xx + yy);
+}
+
 gg_status set_shape(gg_sim *s, uint32_t k) {
   gg::LaunchShape ls = kShapes[k - 1];
   ls.iters = s->p.pja_iters;
@@ -351,6 +371,8 @@ void gg_destroy(gg_sim *sim) {
   for (float *g : sim->grids)
     if (g) cudaFree(g);
   if (sim->staging) cudaFree(sim->staging);
+  if (sim->render_img) cudaFree(sim->render_img);
+  if (sim->render_out) cudaFree(sim->render_out);
   delete sim;
 }
 
@@ -586,6 +608,7 @@ gg_status gg_set_bodies(gg_sim *s, uint32_t env, uint32_t n_bodies, const gg_bod
     // keep the caller's float quaternion when it is already unit length to FP32 precision
     const bool unit = std::fabs(qn - 1.0) < 1e-6;
     for (int k = 0; k < 4; ++k) o.q[k] = unit ? in.quat[k] : (float)(in.quat[k] / qn);
+    rot_from_quat(o.q, o.R);  // valid before the first step (gg_render); each step recomputes it
     o.mass = in.mass;
     o.env = env;
     o.active = 1;
@@ -685,6 +708,64 @@ gg_status gg_set_body_grid(gg_sim *s, uint32_t env, uint32_t body, const uint32_
   hb.shape[4] = (float)(1.0 / (double)spacing);
   hb.grid = g;
   GG_CUDA(s, cudaMemcpy(s->a.bodies + gb, &hb, sizeof(DevBody), cudaMemcpyHostToDevice));
+  return GG_OK;
+}
+
+gg_status gg_render(gg_sim *s, uint32_t env, const gg_camera *cam, float *out, int out_on_device, void *stream) {
+  if (!s) return GG_ERR_INVALID_ARG;
+  if (!cam || !out || cam->struct_size != sizeof(gg_camera) || env >= s->n_envs)
+    return fail(s, GG_ERR_INVALID_ARG, "gg_render: bad camera, output or environment");
+  const gg_camera &C = *cam;
+  if (C.kind > GG_CAMERA_DEPTH || C.width == 0 || C.height == 0 || C.width > 4096 || C.height > 4096)
+    return fail(s, GG_ERR_INVALID_ARG, "gg_render: bad camera kind or size");
+  gg::RenderArgs r{};
+  r.kind = C.kind;
+  r.W = C.width;
+  r.H = C.height;
+  if (C.kind == GG_CAMERA_HEIGHT) {
+    if (!(C.extent[0] > 0.f) || !(C.extent[1] > 0.f) || !std::isfinite(C.extent[0]) || !std::isfinite(C.extent[1]))
+      return fail(s, GG_ERR_INVALID_ARG, "gg_render: extents must be positive");
+    // the oracle's order: step = extent / W; corner = centre - extent / 2
+    r.sx = C.extent[0] / (float)C.width;
+    r.sy = C.extent[1] / (float)C.height;
+    r.bx = C.pos[0] - 0.5f * C.extent[0];
+    r.by = C.pos[1] - 0.5f * C.extent[1];
+    r.empty = C.empty;
+  } else {
+    if (!(C.fov_y > 0.f && C.fov_y < 3.14159f) || !(C.near_clip > 0.f) || !(C.far_clip > C.near_clip) ||
+        !std::isfinite(C.far_clip))
+      return fail(s, GG_ERR_INVALID_ARG, "gg_render: bad field of view or clip range");
+    r.f = (float)(0.5 * (double)C.height / std::tan(0.5 * (double)C.fov_y));
+    rot_from_quat(C.quat, r.R);
+    for (int k = 0; k < 3; ++k) r.o[k] = C.pos[k];
+    r.near = C.near_clip;
+    r.far = C.far_clip;
+    r.eps = C.march_eps > 0.f ? C.march_eps : 1e-4f;
+    r.steps = C.march_steps ? C.march_steps : 64;
+    r.mask = C.body_mask;
+  }
+  const size_t np = (size_t)C.width * C.height;
+  if (np > s->render_px) {
+    if (s->render_img) cudaFree(s->render_img);
+    if (s->render_out) cudaFree(s->render_out);
+    s->render_img = nullptr;
+    s->render_out = nullptr;
+    s->render_px = 0;
+    if (cudaMalloc(&s->render_img, np * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&s->render_out, np * sizeof(float)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(s, GG_ERR_OOM, "gg_render: scratch allocation failed");
+    }
+    s->render_px = np;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const gg::DevEnv &E = s->envs[env];
+  float *dst = out_on_device ? out : s->render_out;
+  GG_CUDA(s, gg::enqueue_render(s->a, E.off, E.n, env * s->maxb, s->nbodies[env], r, s->render_img, dst, st));
+  if (!out_on_device) {
+    GG_CUDA(s, cudaMemcpyAsync(out, dst, np * sizeof(float), cudaMemcpyDeviceToHost, st));
+    GG_CUDA(s, cudaStreamSynchronize(st));
+  }
   return GG_OK;
 }
 

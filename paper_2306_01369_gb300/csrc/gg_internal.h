@@ -48,6 +48,16 @@ cudaError_t enqueue_sort_from_keys(const StepArgs &a, cudaStream_t st);
 // reverse of one taped step (after enqueue_step with a tape, which stops after the sweeps)
 cudaError_t enqueue_adjoint_step(const StepArgs &a, const AdjArgs &d, uint32_t k_local, cudaStream_t st);
 uint32_t adjoint_blocks(uint32_t n);
+// Depth observation (gg_render): everything the kernels need, precomputed on the host.
+struct RenderArgs {
+  uint32_t kind, W, H;
+  float bx, by, sx, sy, empty;  // height camera: first pixel centre's corner, pixel steps, empty value
+  float o[3], R[9], f;          // depth camera: origin, rotation camera -> world, focal length (pixels)
+  float near, far, eps;
+  uint32_t mask, steps;
+};
+cudaError_t enqueue_render(const StepArgs &a, uint32_t env_off, uint32_t env_n, uint32_t gb0, uint32_t nb,
+                           const RenderArgs &c, uint32_t *img, float *out, cudaStream_t st);
 cudaError_t enqueue_pack3(float4 *dst, const float *src3, uint32_t n, cudaStream_t st);
 cudaError_t enqueue_export_contacts(const StepArgs &a, uint32_t *rows, float *geom, float *lam, float *bgeom,
                                     float *blam, cudaStream_t st);

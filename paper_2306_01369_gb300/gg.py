@@ -33,6 +33,7 @@ SIGNATURES = {
     "gg_set_bodies": (C.c_int, [_P, C.c_uint32, C.c_uint32, _P]),
     "gg_set_trajectory": (C.c_int, [_P, C.c_uint32, C.c_uint32, C.c_uint32, _P, C.c_int]),
     "gg_set_body_grid": (C.c_int, [_P, C.c_uint32, C.c_uint32, _P, _P, C.c_float, _P, C.c_int]),
+    "gg_render": (C.c_int, [_P, C.c_uint32, _P, _P, C.c_int, _P]),
     "gg_set_particles": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "gg_step": (C.c_int, [_P, C.c_uint32, _P]),
     "gg_sync": (C.c_int, [_P, _P]),
@@ -67,6 +68,27 @@ class GGBody(C.Structure):
     _fields_ = [("kind", C.c_uint32), ("is_free", C.c_uint32), ("shape", C.c_float * 12), ("pos", C.c_float * 3),
                 ("quat", C.c_float * 4), ("lin_vel", C.c_float * 3), ("ang_vel", C.c_float * 3),
                 ("mass", C.c_float), ("inertia", C.c_float * 3)]
+
+
+class GGCamera(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("kind", C.c_uint32), ("width", C.c_uint32), ("height", C.c_uint32),
+                ("pos", C.c_float * 3), ("quat", C.c_float * 4), ("extent", C.c_float * 2), ("fov_y", C.c_float),
+                ("near_clip", C.c_float), ("far_clip", C.c_float), ("empty", C.c_float), ("body_mask", C.c_uint32),
+                ("march_steps", C.c_uint32), ("march_eps", C.c_float)]
+
+
+def make_camera(cam) -> GGCamera:
+    c = GGCamera()
+    c.struct_size = C.sizeof(GGCamera)
+    c.kind, c.width, c.height = int(cam.kind), int(cam.width), int(cam.height)
+    for k in range(3):
+        c.pos[k] = cam.pos[k]
+    for k in range(4):
+        c.quat[k] = cam.quat[k]
+    c.extent[0], c.extent[1] = cam.extent
+    c.fov_y, c.near_clip, c.far_clip, c.empty = cam.fov_y, cam.near, cam.far, cam.empty
+    c.body_mask, c.march_steps, c.march_eps = int(cam.body_mask) & 0xFFFFFFFF, int(cam.march_steps), cam.march_eps
+    return c
 
 
 class GGStats(C.Structure):
@@ -316,6 +338,16 @@ class Sim:
 
     def vel(self):
         return self.read("VEL", shape=(self.n, 3))
+
+    def render(self, camera, env=0, out=None, stream=None):
+        """Depth observation (height, width) of environment env (gg_render): into `out`
+        (a CUDA tensor: asynchronous) or a new numpy array."""
+        c = make_camera(camera)
+        if out is None:
+            out = np.empty((c.height, c.width), np.float32)
+        p, dev = _ptr(out)
+        self._check(self._L.gg_render(self.h, env, C.byref(c), p, dev, _stream(stream)), "gg_render")
+        return out
 
     def pos_vel(self, out=None, stream=None):
         """Positions (n, 4) and velocities (n, 3) in one copy (and one wait, to the host):

@@ -58,6 +58,7 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(gg.GGParams) == 4 * 23
     assert ctypes.sizeof(gg.GGBody) == 4 * (2 + 12 + 3 + 4 + 3 + 3 + 1 + 3)
     assert ctypes.sizeof(gg.GGStats) == 8 + 4 * 6
+    assert ctypes.sizeof(gg.GGCamera) == 4 * 20
 
 
 def test_create_rejects_bad_params_before_touching_a_device(lib):
