@@ -449,8 +449,8 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
         # scoop's side looking at the bed (every body traced)
         foot = ex.info["side"] * ex.info["pitch"]
         sky = scenes.Camera(kind=scenes.HEIGHT_CAMERA, width=72, height=36, extent=(foot, 0.5 * foot), empty=0.0)
-        ego = scenes.Camera(kind=scenes.DEPTH_CAMERA, width=36, height=36, pos=(-0.45 * foot, 0.0, 0.3),
-                            quat=scenes._quat_from_rotvec((0.0, 2.3, 0.0)), fov_y=1.2, near=0.01, far=1.5,
+        ego = scenes.Camera(kind=scenes.DEPTH_CAMERA, width=36, height=36, pos=(-0.45 * foot, 0.0, 0.45),
+                            quat=scenes._quat_from_rotvec((0.0, 2.41, 0.0)), fov_y=1.2, near=0.01, far=1.5,
                             march_steps=96, march_eps=1e-4)
         img_s = torch.empty((36, 72), dtype=torch.float32, device=dev)
         img_e = torch.empty((36, 36), dtype=torch.float32, device=dev)

@@ -66,7 +66,8 @@ struct gg_sim {
   size_t staging_bytes = 0;
   float *vel3 = nullptr;  // n*3 staging for velocity upload / readback
   uint32_t *render_img = nullptr;  // gg_render scratch (ordered bits per pixel) and ...
-  float *render_out = nullptr;     // ... device image for host destinations
+  float *render_out = nullptr;     // ... device image for host destinations, ...
+  float4 *render_rays = nullptr;   // ... and the depth camera's per-pixel rays
   size_t render_px = 0;
   // differentiation: checkpoints, per-step tape, adjoint buffers
   struct {
@@ -373,6 +374,7 @@ void gg_destroy(gg_sim *sim) {
   if (sim->staging) cudaFree(sim->staging);
   if (sim->render_img) cudaFree(sim->render_img);
   if (sim->render_out) cudaFree(sim->render_out);
+  if (sim->render_rays) cudaFree(sim->render_rays);
   delete sim;
 }
 
@@ -748,16 +750,20 @@ gg_status gg_render(gg_sim *s, uint32_t env, const gg_camera *cam, float *out, i
   if (np > s->render_px) {
     if (s->render_img) cudaFree(s->render_img);
     if (s->render_out) cudaFree(s->render_out);
+    if (s->render_rays) cudaFree(s->render_rays);
     s->render_img = nullptr;
     s->render_out = nullptr;
+    s->render_rays = nullptr;
     s->render_px = 0;
     if (cudaMalloc(&s->render_img, np * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&s->render_out, np * sizeof(float)) != cudaSuccess) {
+        cudaMalloc(&s->render_out, np * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&s->render_rays, np * sizeof(float4)) != cudaSuccess) {
       (void)cudaGetLastError();
       return fail(s, GG_ERR_OOM, "gg_render: scratch allocation failed");
     }
     s->render_px = np;
   }
+  r.rays = s->render_rays;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const gg::DevEnv &E = s->envs[env];
   float *dst = out_on_device ? out : s->render_out;

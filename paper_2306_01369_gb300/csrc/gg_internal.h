@@ -55,6 +55,7 @@ struct RenderArgs {
   float o[3], R[9], f;          // depth camera: origin, rotation camera -> world, focal length (pixels)
   float near, far, eps;
   uint32_t mask, steps;
+  float4 *rays;                 // depth camera: per-pixel unit ray (scratch, W * H)
 };
 cudaError_t enqueue_render(const StepArgs &a, uint32_t env_off, uint32_t env_n, uint32_t gb0, uint32_t nb,
                            const RenderArgs &c, uint32_t *img, float *out, cudaStream_t st);

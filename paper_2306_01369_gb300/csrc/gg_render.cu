@@ -81,6 +81,14 @@ __device__ __forceinline__ float3 pixel_ray(const RenderArgs &c, uint32_t u, uin
   return make_float3(d[0], d[1], d[2]);
 }
 
+// The ray of every pixel, once per image (the splat tests many spheres against each).
+__global__ void k_make_rays(RenderArgs c) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= c.W * c.H) return;
+  const float3 d = pixel_ray(c, p % c.W, p / c.W);
+  c.rays[p] = make_float4(d.x, d.y, d.z, 0.f);
+}
+
 __global__ void k_splat_depth(StepArgs a, uint32_t off, uint32_t n, RenderArgs c, uint32_t *img) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -107,7 +115,7 @@ __global__ void k_splat_depth(StepArgs a, uint32_t off, uint32_t n, RenderArgs c
   const float cc = __fsub_rn(__fadd_rn(__fadd_rn(__fmul_rn(oc0, oc0), __fmul_rn(oc1, oc1)), __fmul_rn(oc2, oc2)), rr);
   for (int v = v0; v <= v1; ++v)
     for (int u = u0; u <= u1; ++u) {
-      const float3 d = pixel_ray(c, (uint32_t)u, (uint32_t)v);
+      const float4 d = c.rays[(size_t)v * c.W + u];
       const float b = __fadd_rn(__fadd_rn(__fmul_rn(d.x, oc0), __fmul_rn(d.y, oc1)), __fmul_rn(d.z, oc2));
       const float disc = __fsub_rn(__fmul_rn(b, b), cc);
       if (!(disc >= 0.0f)) continue;
@@ -138,10 +146,9 @@ __device__ __forceinline__ float march_sdf(const DevBody &b, float3 y, float eps
 __global__ void k_trace_depth(StepArgs a, uint32_t gb0, uint32_t nb, RenderArgs c, const uint32_t *img, float *out) {
   const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= c.W * c.H) return;
-  const uint32_t u = p % c.W, v = p / c.W;
   float best = __uint_as_float(img[p]);
   if (nb && c.mask) {
-    const float3 d = pixel_ray(c, u, v);
+    const float4 d = c.rays[p];
     float t = c.near;
     for (uint32_t k = 0; k < c.steps; ++k) {
       const float3 x = make_float3(__fadd_rn(c.o[0], __fmul_rn(t, d.x)), __fadd_rn(c.o[1], __fmul_rn(t, d.y)),
@@ -176,6 +183,7 @@ cudaError_t enqueue_render(const StepArgs &a, uint32_t env_off, uint32_t env_n, 
     k_finish_height<<<cdiv(np, 256), 256, 0, st>>>(img, np, c.empty, out);
   } else {
     k_fill<<<cdiv(np, 256), 256, 0, st>>>(img, np, 0x7f800000u);
+    k_make_rays<<<cdiv(np, 128), 128, 0, st>>>(c);
     if (env_n) k_splat_depth<<<cdiv(env_n, 128), 128, 0, st>>>(a, env_off, env_n, c, img);
     k_trace_depth<<<cdiv(np, 128), 128, 0, st>>>(a, gb0, nb, c, img, out);
   }
