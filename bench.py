@@ -39,10 +39,49 @@ WORKLOAD = "column_collapse_262144"
 COLLAPSE_STEPS = 2000   # length of the column-collapse run the metric is quoted on
 
 
-def workload_config(sc):
-    return {"workload": WORKLOAD, "n_particles": sc.n, "pja_iters": sc.params.pja_iters, "dt": sc.params.dt,
-            "mu": sc.params.mu, "alpha": sc.params.alpha, "radius_m": "2e-3 +-10%", "column_sites": "40x40x164",
-            "bodies": "ground plane", "l2": "flushed between timed steps (512 MiB write)"}
+def workload_config(sc, workload="column"):
+    base = {"n_particles": sc.n, "pja_iters": sc.params.pja_iters, "dt": sc.params.dt, "mu": sc.params.mu,
+            "alpha": sc.params.alpha, "l2": "flushed between timed steps (512 MiB write)"}
+    if workload == "excavation":
+        return {"workload": "excavation_1048576", **base, "radius_m": "2e-3 +-15%",
+                "bed": "128x128x64 sites, settled 3000 steps under the parked scoop",
+                "bodies": "container, kinematic scoop on 6 waypoints, 2 free 3 cm cubes"}
+    if workload == "batched":
+        return {"workload": "batched_beds_256", **base, "envs": len(sc.env_offsets) - 1,
+                "bed": "16 layers per environment, settled 1500 steps under the parked tools",
+                "bodies": "container + scoop per environment"}
+    return {"workload": WORKLOAD, **base, "radius_m": "2e-3 +-10%", "column_sites": "40x40x164",
+            "bodies": "ground plane"}
+
+
+def setup_workload(args, scenes, gg, rank, stream):
+    """(scene, simulation, untimed steps before the warm-up) of the timed workload."""
+    if args.workload == "column":
+        sc = scenes.column_collapse(seed=1001 + rank)
+        sim = gg.Sim.from_scene(sc, tuning=args.tuning)
+        preroll = max(0, (COLLAPSE_STEPS - args.steps) // 2 - args.warmup)
+        if preroll:
+            sim.step(preroll, stream=stream)
+        return sc, sim, preroll
+    n_run = args.warmup + args.steps + 20
+    if args.workload == "excavation":
+        sc = scenes.excavation(n=1048576, seed=1002 + rank, n_steps=n_run)
+        settle = 3000
+    else:
+        sc = scenes.batched_beds(n_envs=256, seed=1003 + rank, n_steps=n_run)
+        settle = 1500
+    parked = scenes.Scene(sc.name, sc.pos_r, sc.vel, sc.mass, sc.bodies, sc.params, sc.n_steps,
+                          env_offsets=sc.env_offsets, body_offsets=sc.body_offsets)
+    sim = gg.Sim.from_scene(parked, tuning=args.tuning)
+    sim.step(settle, stream=stream)       # the bed settles, then the tools start digging
+    bo = sc.body_offsets
+    for gb, tw in sc.twist.items():
+        if bo is None:
+            sim.set_trajectory(gb, tw)
+        else:
+            e = int(np.searchsorted(bo, gb, side="right") - 1)
+            sim.set_trajectory(gb - int(bo[e]), tw, e)
+    return sc, sim, settle
 
 
 # --------------------------------------------------------------------------- #
@@ -207,7 +246,7 @@ def kernel_digest() -> str:
 # --------------------------------------------------------------------------- #
 
 def oracle_sample(sc, state_pos, state_vel, seconds=15.0, max_steps=2000, threads=None):
-    """Time the FP64 oracle, as it stands, on the column: whole steps of all n
+    """Time the FP64 oracle, as it stands, on the workload: whole steps of all n
     particles from the generator's initial state until `seconds` have passed (at
     least one step).  Oracle inputs never come from the CUDA path."""
     import oracle
@@ -222,8 +261,8 @@ def oracle_sample(sc, state_pos, state_vel, seconds=15.0, max_steps=2000, thread
     el = time.perf_counter() - t0
     one = _oracle_rate(sc, state_pos, state_vel, 1, threads=1)
     return {"value": sc.n * steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"the first {steps} time steps of the {sc.n}-sphere column from its initial state (FP64 C "
-                      f"oracle, {threads} OpenMP threads); {el:.1f} s",
+            "sample": f"the first {steps} time steps of {sc.name} ({sc.n} spheres) from its initial state "
+                      f"(FP64 C oracle, {threads} OpenMP threads); {el:.1f} s",
             "single_core_value": one["value"], "single_core_sample": one["sample"]}
 
 
@@ -499,17 +538,12 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     _build.build()
 
-    sc = scenes.column_collapse(seed=1001 + rank)
-    sim = gg.Sim.from_scene(sc, tuning=args.tuning)
     stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    # untimed pre-roll so that the timed window sits in the middle of the 2000-step
-    # collapse (none when K >= 2000 - 2W), then the warm-up, which alternates the
+    # untimed pre-roll (the column: so that the timed window sits in the middle of the
+    # 2000-step collapse; the beds: settling), then the warm-up, which alternates the
     # plain and the instrumented step graphs so that both are captured before timing
-    preroll = max(0, (COLLAPSE_STEPS - args.steps) // 2 - args.warmup)
-    if preroll:
-        sim.step(preroll, stream=stream)
+    sc, sim, preroll = setup_workload(args, scenes, gg, rank, stream)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for w in range(max(args.warmup, 2)):
         sim.enable_timing(w % 2 == 1)
         sim.step(1, stream=stream)
@@ -591,17 +625,17 @@ def run_gpu(args):
     e2e_val = sum_over_ranks(float(sc.n * e2e_steps), world, dev) / e2e_s
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and sc.env_offsets is None:
         cpu = oracle_sample(sc, sc.pos_r, sc.vel, seconds=args.cpu_seconds)
     xtra = None
-    if rank == 0 and world == 1 and not args.no_extras:
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == "column":
         xtra = extras(torch, dev, stream)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {**workload_config(sc), "replicas": world, "tuning_set": sim.tuning_selected,
+                "config": {**workload_config(sc, args.workload), "replicas": world, "tuning_set": sim.tuning_selected,
                            "timed_steps": window},
                 "roofline": roof_main, "roofline_next": roof_other, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "steps": e2e_steps,
@@ -630,6 +664,9 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / adjoint / excavation figures")
+    ap.add_argument("--workload", choices=["column", "excavation", "batched"], default="column",
+                    help="the timed workload (column: the headline; the others for profiling at sizes that "
+                         "do not fit in L2)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

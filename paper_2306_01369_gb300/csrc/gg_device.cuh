@@ -94,7 +94,7 @@ struct DevCtrl {
   uint32_t bar_gen;       // grid barrier: completed rounds
   uint32_t bar_abort;     // set when a barrier wait gave up (later barriers return at once)
   uint32_t bar_extra;     // phantom arrivals a barrier waits for (0; tests set it to force a timeout)
-  uint32_t pad;
+  uint32_t blocks_done;     // k_wrench_bodies: blocks finished this step (0 between steps)
 };
 
 // Everything a step's kernels read or write; passed by value to each kernel.

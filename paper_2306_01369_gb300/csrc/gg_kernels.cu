@@ -13,8 +13,8 @@
 //   k_free_update    each followed (free bodies) by the bodies' twist update
 //   k_integrate_wrench  symplectic Euler (Eq. 4-5) in place, and per-body impulse
 //                    sums over fixed chunks of particles (deterministic)
-//   k_wrench_sum     per-body sums over chunks into the wrench readback ring
-//   k_body_update    kinematic body poses, step counter
+//   k_wrench_bodies  per-body sums over chunks into the wrench readback ring, body
+//                    poses, step counter
 // Contacts, sweeps and integration run over particles in the caller's order (their
 // storage order); the bucket table is only walked, so spatially ordered inputs keep
 // neighbours' data in nearby cache lines.
@@ -878,21 +878,23 @@ __device__ __forceinline__ void integrate_particle(const StepArgs &a, int s, uin
 //      each body's contact forces and torques over them in a fixed order
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_integrate_wrench(StepArgs a, int s) {
+constexpr int kIntegrateThreads = kWrenchChunk;  // one particle of the chunk per thread
+
+__global__ void __launch_bounds__(kIntegrateThreads) k_integrate_wrench(StepArgs a, int s) {
   pdl_enter();
   const uint32_t c = blockIdx.x;
   const uint32_t e = a.chunk_env[c];
   const DevEnv &E = a.envs[e];
   const uint32_t s0 = E.off + (c - E.chunk0) * kWrenchChunk;
   const uint32_t s1 = min(s0 + kWrenchChunk, E.off + E.n);
-  for (uint32_t i = s0 + threadIdx.x; i < s1; i += 256) integrate_particle(a, s, i);
+  for (uint32_t i = s0 + threadIdx.x; i < s1; i += kIntegrateThreads) integrate_particle(a, s, i);
   const size_t n = a.n, KbN = (size_t)a.Kb * n;
   const float inv_dt = 1.0f / a.dt;
   for (uint32_t lb = 0; lb < E.nbodies; ++lb) {
     const uint32_t gb = e * a.maxb + lb;
     const DevBody &B = a.bodies[gb];
     float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (uint32_t i = s0 + threadIdx.x; i < s1; i += 256) {
+    for (uint32_t i = s0 + threadIdx.x; i < s1; i += kIntegrateThreads) {
       const uint32_t nbc = (a.ccount[i] >> 8) & 0xffu;
       for (uint32_t k = 0; k < nbc; ++k) {
         const size_t o = (size_t)k * n + i;
@@ -908,7 +910,7 @@ __global__ void __launch_bounds__(256) k_integrate_wrench(StepArgs a, int s) {
         v[5] += rx * fy - ry * fx;
       }
     }
-    block_sum6<256>(v);
+    block_sum6<kIntegrateThreads>(v);
     if (threadIdx.x == 0) {
       float *dst = a.wpart + ((size_t)c * a.maxb + lb) * 6;
 #pragma unroll
@@ -918,96 +920,101 @@ __global__ void __launch_bounds__(256) k_integrate_wrench(StepArgs a, int s) {
   }
 }
 
+// Pose of a body after the step: p += dt v, q <- exp(dt w / 2) q; a free body keeps
+// the twist of its last sweep as its own.
+__device__ __forceinline__ void advance_body(const StepArgs &a, DevBody &B) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) B.p[k] += a.dt * B.v[k];
+  const float tx = a.dt * B.w[0], ty = a.dt * B.w[1], tz = a.dt * B.w[2];
+  const float ang = sqrtf(tx * tx + ty * ty + tz * tz);
+  if (ang > 0.f) {
+    float sh, ch;
+    sincosf(0.5f * ang, &sh, &ch);
+    const float sc = sh / ang;
+    const float dw = ch, dx = tx * sc, dy = ty * sc, dz = tz * sc;
+    const float qw = B.q[0], qx = B.q[1], qy = B.q[2], qz = B.q[3];
+    float rw = dw * qw - dx * qx - dy * qy - dz * qz;
+    float rx = dw * qx + dx * qw + dy * qz - dz * qy;
+    float ry = dw * qy - dx * qz + dy * qw + dz * qx;
+    float rz = dw * qz + dx * qy - dy * qx + dz * qw;
+    const float inv = rsqrtf(rw * rw + rx * rx + ry * ry + rz * rz);
+    B.q[0] = rw * inv;
+    B.q[1] = rx * inv;
+    B.q[2] = ry * inv;
+    B.q[3] = rz * inv;
+  }
+  if (B.is_free) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      B.own_v[k] = B.v[k];
+      B.own_w[k] = B.w[k];
+    }
+  }
+}
+
 // One warp per body: sum its environment's chunk partials in a fixed order
-// (lane-strided, then a fixed butterfly) into the wrench ring.
-__global__ void __launch_bounds__(256) k_wrench_sum(StepArgs a) {
+// (lane-strided, then a fixed butterfly) into the wrench ring, then advance the body's
+// pose (no warp reads another body's pose).  The last block to finish advances the
+// step counter (every block read it first; no block waits for another).
+__global__ void __launch_bounds__(256) k_wrench_bodies(StepArgs a) {
   pdl_enter();
   const uint32_t gb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const uint32_t nbt = a.n_envs * a.maxb;
-  if (gb >= nbt) return;
   const uint32_t step = a.ctrl->step;
-  float *dst = a.wrench + ((size_t)(step % a.wrench_hist) * nbt + gb) * 6;
-  const DevBody &B = a.bodies[gb];
-  float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if (B.active) {
-    const uint32_t e = gb / a.maxb, lb = gb % a.maxb;
-    const DevEnv &E = a.envs[e];
-    for (uint32_t c = E.chunk0 + lane; c < E.chunk0 + E.nchunks; c += 32) {
-      const float *src = a.wpart + ((size_t)c * a.maxb + lb) * 6;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) v[k] += src[k];
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < 6; ++k)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-  if (lane == 0 && B.active && a.F) {  // free-box corners: +lambda on the box, -lambda on the other body
-    const uint32_t e = gb / a.maxb;
-    const float inv_dt = 1.0f / a.dt;
-    for (uint32_t lb = 0; lb < a.maxb; ++lb) {
-      const DevBody &Fb = a.bodies[e * a.maxb + lb];
-      if (!Fb.active || !Fb.is_free) continue;
-      const CornerContact *cc = a.fcc + (size_t)Fb.fid * 8 * a.maxb;
-      for (uint32_t t = 0; t < 8 * a.maxb; ++t) {
-        if (!cc[t].valid) continue;
-        const float sg = (e * a.maxb + lb == gb) ? inv_dt : ((e * a.maxb + cc[t].o == gb) ? -inv_dt : 0.f);
-        if (sg == 0.f) continue;
-        const float fx = sg * cc[t].lam[0], fy = sg * cc[t].lam[1], fz = sg * cc[t].lam[2];
-        const float rx = cc[t].xc[0] - B.p[0], ry = cc[t].xc[1] - B.p[1], rz = cc[t].xc[2] - B.p[2];
-        v[0] += fx;
-        v[1] += fy;
-        v[2] += fz;
-        v[3] += ry * fz - rz * fy;
-        v[4] += rz * fx - rx * fz;
-        v[5] += rx * fy - ry * fx;
-      }
-    }
-  }
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < 6; ++k) dst[k] = v[k];
-}
-
-// Body poses after the step (p += dt v, q <- exp(dt w / 2) q), then the step counter.
-__global__ void __launch_bounds__(256) k_body_update(StepArgs a) {
-  pdl_enter();
-  const uint32_t step = a.ctrl->step;
-  const uint32_t nbt = a.n_envs * a.maxb;
-  for (uint32_t gb = threadIdx.x; gb < nbt; gb += blockDim.x) {
+  if (gb < nbt) {
+    float *dst = a.wrench + ((size_t)(step % a.wrench_hist) * nbt + gb) * 6;
     DevBody &B = a.bodies[gb];
-    if (!B.active) continue;
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (B.active) {
+      const uint32_t e = gb / a.maxb, lb = gb % a.maxb;
+      const DevEnv &E = a.envs[e];
+      for (uint32_t c = E.chunk0 + lane; c < E.chunk0 + E.nchunks; c += 32) {
+        const float *src = a.wpart + ((size_t)c * a.maxb + lb) * 6;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) B.p[k] += a.dt * B.v[k];
-    const float tx = a.dt * B.w[0], ty = a.dt * B.w[1], tz = a.dt * B.w[2];
-    const float ang = sqrtf(tx * tx + ty * ty + tz * tz);
-    if (ang > 0.f) {
-      float sh, ch;
-      sincosf(0.5f * ang, &sh, &ch);
-      const float sc = sh / ang;
-      const float dw = ch, dx = tx * sc, dy = ty * sc, dz = tz * sc;
-      const float qw = B.q[0], qx = B.q[1], qy = B.q[2], qz = B.q[3];
-      float rw = dw * qw - dx * qx - dy * qy - dz * qz;
-      float rx = dw * qx + dx * qw + dy * qz - dz * qy;
-      float ry = dw * qy - dx * qz + dy * qw + dz * qx;
-      float rz = dw * qz + dx * qy - dy * qx + dz * qw;
-      const float inv = rsqrtf(rw * rw + rx * rx + ry * ry + rz * rz);
-      B.q[0] = rw * inv;
-      B.q[1] = rx * inv;
-      B.q[2] = ry * inv;
-      B.q[3] = rz * inv;
-    }
-    if (B.is_free) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        B.own_v[k] = B.v[k];
-        B.own_w[k] = B.w[k];
+        for (int k = 0; k < 6; ++k) v[k] += src[k];
       }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0 && B.active && a.F) {  // free-box corners: +lambda on the box, -lambda on the other body
+      const uint32_t e = gb / a.maxb;
+      const float inv_dt = 1.0f / a.dt;
+      for (uint32_t lb = 0; lb < a.maxb; ++lb) {
+        const DevBody &Fb = a.bodies[e * a.maxb + lb];
+        if (!Fb.active || !Fb.is_free) continue;
+        const CornerContact *cc = a.fcc + (size_t)Fb.fid * 8 * a.maxb;
+        for (uint32_t t = 0; t < 8 * a.maxb; ++t) {
+          if (!cc[t].valid) continue;
+          const float sg = (e * a.maxb + lb == gb) ? inv_dt : ((e * a.maxb + cc[t].o == gb) ? -inv_dt : 0.f);
+          if (sg == 0.f) continue;
+          const float fx = sg * cc[t].lam[0], fy = sg * cc[t].lam[1], fz = sg * cc[t].lam[2];
+          const float rx = cc[t].xc[0] - B.p[0], ry = cc[t].xc[1] - B.p[1], rz = cc[t].xc[2] - B.p[2];
+          v[0] += fx;
+          v[1] += fy;
+          v[2] += fz;
+          v[3] += ry * fz - rz * fy;
+          v[4] += rz * fx - rx * fz;
+          v[5] += rx * fy - ry * fx;
+        }
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) dst[k] = v[k];
+      if (B.active) advance_body(a, B);
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) a.ctrl->step = step + 1;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&a.ctrl->blocks_done, 1u) == gridDim.x - 1) {
+      a.ctrl->blocks_done = 0;
+      a.ctrl->step = step + 1;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1118,7 +1125,7 @@ static inline cudaError_t mark(cudaEvent_t *ev, int k, cudaStream_t st) {
 }
 
 uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls) {
-  uint32_t k = a.lists ? 4 : 6;  // key + list clear or scan x3, wrench_sum, body_update
+  uint32_t k = a.lists ? 3 : 5;  // key + list clear or scan x3, wrench sums + body poses
   if (a.n) k += (a.lists ? 1 : 3) + ((ls.fused_grid && !a.F) ? 1 : ls.iters);  // (scatter, reorder,) contacts, pja
   if (a.n_chunks) k += 1;  // integrate + wrench partials
   if (a.F) k += 1 + ls.iters;  // free_prep, free_update x I
@@ -1202,9 +1209,8 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
   }
   if (tp) return cudaGetLastError();
   GG_MARK(3);
-  if (a.n_chunks) GG_LAUNCH(k_integrate_wrench, dim3(a.n_chunks), 256, 0, a, (int)(ls.iters & 1));
-  GG_LAUNCH(k_wrench_sum, dim3(grid_for(nbt * 32, 256)), 256, 0, a);
-  GG_LAUNCH(k_body_update, dim3(1), 256, 0, a);
+  if (a.n_chunks) GG_LAUNCH(k_integrate_wrench, dim3(a.n_chunks), kIntegrateThreads, 0, a, (int)(ls.iters & 1));
+  GG_LAUNCH(k_wrench_bodies, dim3(grid_for(nbt * 32, 256)), 256, 0, a);
   GG_MARK(4);
 #undef GG_LAUNCH
 #undef GG_MARK
