@@ -74,6 +74,7 @@ def setup_workload(args, scenes, gg, rank, stream):
                           env_offsets=sc.env_offsets, body_offsets=sc.body_offsets)
     sim = gg.Sim.from_scene(parked, tuning=args.tuning)
     sim.step(settle, stream=stream)       # the bed settles, then the tools start digging
+    sim.autotune(stream)                  # the settled bed, not the lattice, decides the launch shapes
     bo = sc.body_offsets
     for gb, tw in sc.twist.items():
         if bo is None:
@@ -332,6 +333,21 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
     from paper_2306_01369_gb300.autograd import rollout, scoop_mass
     out = {}
     t_start = time.perf_counter()
+    # the column's pile: 262,144 spheres run for 20,000 steps (1 s; the collapse is still
+    # creeping then), repose angle and centre of mass of what it has become
+    from paper_2306_01369_gb300.stats import pile_statistics
+    col = scenes.column_collapse()
+    sim = gg.Sim.from_scene(col)
+    sim.step(20000, stream=stream)
+    sim.sync(stream)
+    pv = sim.pos_vel()
+    ke = 0.5 * float((col.mass * (pv[1].astype(np.float64) ** 2).sum(1)).sum())
+    angle, com, nbins = pile_statistics(pv[0][:, :3], col.mass, float(col.pos_r[:, 3].max()))
+    sim.close()
+    out["column_pile"] = {"workload": "column collapse 262,144, mu 0.6, after 20,000 steps (1 s)",
+                          "repose_angle_deg": angle, "centre_of_mass_m": [float(c) for c in com],
+                          "initial_height_m": float(col.pos_r[:, 2].max()), "fit_bins": nbins,
+                          "kinetic_energy_j": ke}
     # small settle: 4,096 spheres in an open box, 200 steps (the oracle runs it whole)
     ss = scenes.settle_box(n=4096, n_steps=200)
     sim = gg.Sim.from_scene(ss)
@@ -352,6 +368,7 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
                           env_offsets=sc.env_offsets, body_offsets=sc.body_offsets)
     sim = gg.Sim.from_scene(parked)
     sim.step(settle_steps, stream=stream)
+    sim.autotune(stream)
     bo = sc.body_offsets
     for gb, tw in sc.twist.items():
         e = int(np.searchsorted(bo, gb, side="right") - 1)
@@ -479,6 +496,7 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
         parked = scenes.Scene(ex.name, ex.pos_r, ex.vel, ex.mass, ex.bodies, ex.params, ex.n_steps)
         sim = gg.Sim.from_scene(parked, wrench_history=steps_exc)
         sim.step(settle_steps_exc, stream=stream)   # the bed settles under the parked scoop
+        sim.autotune(stream)
         sim.set_trajectory(1, ex.twist[1])
         sim.step(10, stream=stream)
         ms = _timed_steps(sim, steps_exc, stream, torch)

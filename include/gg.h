@@ -95,8 +95,9 @@ typedef struct {
   float density;             /* mass = density 4/3 pi r^3 when no masses are given; 0 -> 2500 */
   uint32_t tuning;           /* 0: the first gg_step times every launch-shape set (binning
                                 included) on a copy of the state (restored bit-exactly) and keeps
-                                the fastest; k >= 1: fixed set k (see gg_tuning_count; sets 7-8 bin
-                                by linked lists).  Results do not depend on it. */
+                                the fastest; k >= 1: fixed set k (see gg_tuning_count; sets 7-9 bin
+                                by linked lists, sets 9-10 cap the sweep at 40 registers).
+                                Results do not depend on it. */
   uint32_t wrench_history;   /* per-step body wrenches kept for readback; 0 -> 1 */
   uint32_t max_free_bodies;  /* free rigid bodies over all environments (beyond the paper's
                                 kinematic bodies, Sec. V two-way coupling); 0 -> none */
@@ -113,6 +114,9 @@ typedef struct {
                                 cyclic_z[1] > cyclic_z[0], a particle whose z falls below cyclic_z[0]
                                 in a step moves up by cyclic_z[1] - cyclic_z[0], velocity unchanged.
                                 The contact search does not wrap.  {0, 0}: off */
+  uint32_t wait_limit_us;    /* bound of every device-side wait (the grid barrier of the fused
+                                sweep), microseconds at the SM's maximum clock; past it the step
+                                reports GG_ERR_DEVICE_TIMEOUT.  0 -> 500,000 */
 } gg_params;
 
 typedef struct {
@@ -328,6 +332,14 @@ GG_API gg_status gg_backward(gg_sim *sim, const float *dL_dpos, const float *dL_
 /* Number of fixed launch-shape sets accepted by gg_params.tuning, and the set chosen. */
 GG_API uint32_t gg_tuning_count(void);
 GG_API uint32_t gg_tuning_selected(const gg_sim *sim);
+
+/* Time every launch-shape set gg_params.binning allows on the current state (3 steps
+ * each, the state restored bit-exactly before each trial and at the end) and keep the
+ * fastest.  gg_step does this once, on its first call, when gg_params.tuning = 0; call
+ * it again when the workload changes character (a bed that has settled, a tool that
+ * starts digging).  A no-op when gg_params.tuning fixes the set.  Waits for `stream`;
+ * allocates a state copy for the duration of the call. */
+GG_API gg_status gg_autotune(gg_sim *sim, void *stream);
 
 /* Last error message of this simulation (never NULL). */
 GG_API const char *gg_last_error(const gg_sim *sim);

@@ -27,9 +27,11 @@ using gg::StepArgs;
 namespace {
 
 // Launch-shape sets accepted by gg_params.tuning (index k-1).
-// (iters, per-launch sweep block, fused sweep block, fused grid, binning by lists)
-const gg::LaunchShape kShapes[] = {{0, 256, 0, 0, 0},    {0, 128, 0, 0, 0}, {0, 512, 0, 0, 0}, {0, 64, 0, 0, 0},
-                                   {0, 256, 1024, 0, 0}, {0, 256, 512, 0, 0}, {0, 256, 0, 0, 1}, {0, 128, 0, 0, 1}};
+// (iters, per-launch sweep block, fused sweep block, fused grid, binning by lists, lean sweeps)
+const gg::LaunchShape kShapes[] = {{0, 256, 0, 0, 0, 0},    {0, 128, 0, 0, 0, 0}, {0, 512, 0, 0, 0, 0},
+                                   {0, 64, 0, 0, 0, 0},     {0, 256, 1024, 0, 0, 0}, {0, 256, 512, 0, 0, 0},
+                                   {0, 256, 0, 0, 1, 0},    {0, 128, 0, 0, 1, 0}, {0, 256, 0, 0, 1, 1},
+                                   {0, 256, 0, 0, 0, 1}};
 constexpr uint32_t kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 constexpr uint32_t kStateMagic = 0x31534747u;  // "GGS1"
@@ -357,6 +359,13 @@ gg_status gg_stage_ms(gg_sim *s, float *ms) {
 
 uint32_t gg_tuning_selected(const gg_sim *sim) { return sim ? sim->tuning_sel : 0; }
 
+gg_status gg_autotune(gg_sim *s, void *stream) {
+  if (!s) return GG_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GG_CUDA(s, cudaStreamSynchronize(st));
+  return autotune(s, st);
+}
+
 void gg_destroy(gg_sim *sim) {
   if (!sim) return;
   cudaSetDevice(sim->device);
@@ -510,6 +519,12 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
   a.dt = P.dt;
   a.mu = P.mu;
   a.ab = P.alpha / P.dt;
+  {
+    int khz = 0;
+    if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, s->device) != cudaSuccess || khz <= 0) khz = 2000000;
+    const double us = P.wait_limit_us ? (double)P.wait_limit_us : 500000.0;
+    a.wait_cycles = (long long)(us * (double)khz / 1000.0);
+  }
   a.cyc_lo = P.cyclic_z[0];
   a.cyc_h = P.cyclic_z[1] > P.cyclic_z[0] ? P.cyclic_z[1] - P.cyclic_z[0] : 0.f;
   for (int k = 0; k < 3; ++k) a.g[k] = P.gravity[k];

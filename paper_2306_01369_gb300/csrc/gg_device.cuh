@@ -19,7 +19,6 @@ constexpr uint32_t kFlagPPOverflow = 1u;
 constexpr uint32_t kFlagBodyOverflow = 2u;
 constexpr uint32_t kFlagNonFinite = 4u;
 constexpr uint32_t kFlagTimeout = 8u;    // a bounded device-side wait gave up
-constexpr long long kBarrierCycles = 1000000000LL;  // grid-barrier wait limit (~0.5 s at 2 GHz)
 
 constexpr uint32_t kListEnd = 0xffffffffu;  // end of a bucket's linked list
 constexpr int kMaxK = 32;   // particle-particle capacity limit
@@ -103,6 +102,7 @@ struct StepArgs {
   float dt, mu, ab;       // ab = alpha / dt
   float g[3];
   float cyc_lo, cyc_h;    // cyclic vertical boundary: z < cyc_lo moves up by cyc_h (cyc_h > 0), else off
+  long long wait_cycles;  // bound of device-side waits (SM clock cycles)
   uint32_t lists;         // binning: 0 counting sort (contiguous buckets), 1 linked lists (Alg. 2)
   uint32_t *head;         // lists: first particle of each bucket (kListEnd: empty), nh_pad entries
   uint32_t *next;         // lists: next particle of the same bucket, [n]

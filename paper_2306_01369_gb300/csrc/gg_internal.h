@@ -33,6 +33,8 @@ struct LaunchShape {
   int fused_block;      // > 0: all sweeps in one cooperative launch of this block size ...
   uint32_t fused_grid;  // ... and this many blocks (all resident); 0: one launch per sweep
   uint32_t lists;       // binning: 0 counting sort, 1 linked list per bucket (Alg. 2)
+  uint32_t lean;        // per-launch sweeps capped at 40 registers (more resident warps: pays
+                        // when the working set spills out of L2, costs when it fits)
 };
 int fused_pja_blocks_per_sm(int block);
 

@@ -658,10 +658,20 @@ __global__ void __launch_bounds__(512) k_pja(StepArgs a, int s, Tape tp, int it)
   if (i < a.n) pja_particle<TAPE, false>(a, i, s, tp, it);
 }
 
+// One sweep per launch with at most 40 registers per thread (62.5 % -> 75 % occupancy
+// at 256-thread blocks, at the price of a few spilled values): the autotuner's choice
+// when the sweep's working set streams from DRAM.
+__global__ void __maxnreg__(40) k_pja_lean(StepArgs a, int s, int it) {
+  pdl_enter();
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const Tape none{};
+  if (i < a.n) pja_particle<false, false>(a, i, s, none, it);
+}
+
 // Grid-wide barrier of a cooperative launch (all blocks resident).  The wait is
-// bounded: past kBarrierCycles it latches kFlagTimeout and sets bar_abort, after
+// bounded: past `limit` SM cycles it latches kFlagTimeout and sets bar_abort, after
 // which every later barrier returns at once, so the kernel always finishes.
-__device__ __forceinline__ void grid_barrier(DevCtrl *c) {
+__device__ __forceinline__ void grid_barrier(DevCtrl *c, long long limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile uint32_t *vgen = &c->bar_gen;
@@ -677,7 +687,7 @@ __device__ __forceinline__ void grid_barrier(DevCtrl *c) {
       const long long t0 = clock64();
       while (*vgen == gen) {
         if (*vab) break;
-        if (clock64() - t0 > kBarrierCycles) {
+        if (clock64() - t0 > limit) {
           atomicOr(&c->status, kFlagTimeout);
           atomicExch(&c->bar_abort, 1u);
           break;
@@ -699,7 +709,7 @@ __global__ void __launch_bounds__(1024) k_pja_fused(StepArgs a, uint32_t iters) 
   for (uint32_t it = 0; it < iters; ++it) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x)
       pja_particle<false, true>(a, i, (int)(it & 1), none, (int)it);
-    if (it + 1 < iters) grid_barrier(a.ctrl);
+    if (it + 1 < iters) grid_barrier(a.ctrl, a.wait_cycles);
   }
 }
 
@@ -1202,6 +1212,8 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
     if (a.n) {
       if (tp)
         GG_LAUNCH(k_pja<true>, dim3(grid_for(a.n, ls.pja_block)), ls.pja_block, 0, a, (int)(it & 1), *tp, (int)it);
+      else if (ls.lean)
+        GG_LAUNCH(k_pja_lean, dim3(grid_for(a.n, ls.pja_block)), ls.pja_block, 0, a, (int)(it & 1), (int)it);
       else
         GG_LAUNCH(k_pja<false>, dim3(grid_for(a.n, ls.pja_block)), ls.pja_block, 0, a, (int)(it & 1), none, (int)it);
     }

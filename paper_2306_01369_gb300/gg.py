@@ -34,6 +34,7 @@ SIGNATURES = {
     "gg_set_trajectory": (C.c_int, [_P, C.c_uint32, C.c_uint32, C.c_uint32, _P, C.c_int]),
     "gg_set_body_grid": (C.c_int, [_P, C.c_uint32, C.c_uint32, _P, _P, C.c_float, _P, C.c_int]),
     "gg_render": (C.c_int, [_P, C.c_uint32, _P, _P, C.c_int, _P]),
+    "gg_autotune": (C.c_int, [_P, _P]),
     "gg_set_particles": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "gg_step": (C.c_int, [_P, C.c_uint32, _P]),
     "gg_sync": (C.c_int, [_P, _P]),
@@ -61,7 +62,7 @@ class GGParams(C.Structure):
                 ("max_body_contacts", C.c_uint32), ("max_bodies", C.c_uint32), ("density", C.c_float),
                 ("tuning", C.c_uint32), ("wrench_history", C.c_uint32), ("max_free_bodies", C.c_uint32),
                 ("free_contact_capacity", C.c_uint32), ("barrier_test_phantoms", C.c_uint32),
-                ("binning", C.c_uint32), ("cyclic_z", C.c_float * 2)]
+                ("binning", C.c_uint32), ("cyclic_z", C.c_float * 2), ("wait_limit_us", C.c_uint32)]
 
 
 class GGBody(C.Structure):
@@ -147,7 +148,7 @@ def _stream(stream):
 
 
 def make_params(p, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0, max_free_bodies=0,
-                barrier_test_phantoms=0, binning=0) -> GGParams:
+                barrier_test_phantoms=0, binning=0, wait_limit_us=0) -> GGParams:
     q = GGParams()
     q.struct_size = C.sizeof(GGParams)
     q.dt = p.dt
@@ -169,6 +170,7 @@ def make_params(p, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0, max_
     q.free_contact_capacity = 0
     q.barrier_test_phantoms = barrier_test_phantoms
     q.binning = binning
+    q.wait_limit_us = wait_limit_us
     cz = getattr(p, "cyclic_z", (0.0, 0.0))
     q.cyclic_z[0], q.cyclic_z[1] = cz[0], cz[1]
     return q
@@ -197,12 +199,13 @@ class Sim:
     """One libgg simulation (single environment, or batched when env_offsets is given)."""
 
     def __init__(self, pos_r, vel=None, mass=None, params=None, env_offsets=None, tuning=0, wrench_history=1,
-                 max_bodies=8, hash_factor=0, max_free_bodies=0, barrier_test_phantoms=0, binning=0):
+                 max_bodies=8, hash_factor=0, max_free_bodies=0, barrier_test_phantoms=0, binning=0,
+                 wait_limit_us=0):
         L = load()
         self._L = L
         self.params = params
         self.gp = make_params(params, tuning, wrench_history, max_bodies, hash_factor, max_free_bodies,
-                              barrier_test_phantoms, binning)
+                              barrier_test_phantoms, binning, wait_limit_us)
         n = int(pos_r.shape[0])
         self.n = n
         pp, dev = _ptr(pos_r)
@@ -309,6 +312,10 @@ class Sim:
     @property
     def kernels_per_step(self):
         return self._L.gg_kernels_per_step(self.h)
+
+    def autotune(self, stream=None):
+        """Re-time the launch-shape sets on the current state and keep the fastest."""
+        self._check(self._L.gg_autotune(self.h, _stream(stream)), "gg_autotune")
 
     @property
     def tuning_selected(self):

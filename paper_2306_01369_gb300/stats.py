@@ -1,5 +1,6 @@
-"""The pile statistics of the long-run statistical parity test (the paper prints no
-repose measurement; this is the reading used here)."""
+"""Statistics of a collapsed pile: repose angle and centre of mass (the paper prints no
+repose measurement; this is the reading used here).  Used by the long-run statistical
+parity test and reported by the benchmark."""
 import numpy as np
 
 

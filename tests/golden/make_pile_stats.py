@@ -21,7 +21,7 @@ def run_member(args):
     member, threads = args
     import numpy as np
     import oracle
-    from pile_stats import pile_statistics
+    from paper_2306_01369_gb300.stats import pile_statistics
     from paper_2306_01369_gb300 import scenes as S
     sc = S.pile_column(member)
     o = oracle.Sim(sc.pos_r, sc.vel, sc.mass, sc.bodies, sc.params, n_threads=threads)

@@ -265,9 +265,13 @@ def test_autotuner_picks_a_set_and_changes_nothing(gg):
     ref = gg.Sim.from_scene(sc, tuning=1)
     ref.step(8)
     auto = gg.Sim.from_scene(sc, tuning=0)
-    auto.step(8)
+    auto.step(5)
+    auto.autotune()                 # re-timed mid-run: the state is restored bit-exactly
+    auto.step(3)
     assert 1 <= auto.tuning_selected <= gg.load().gg_tuning_count()
     assert np.array_equal(auto.pos(), ref.pos()) and np.array_equal(auto.vel(), ref.vel())
+    ref.autotune()                  # a fixed set: nothing to do
+    assert ref.tuning_selected == 1
 
 
 def test_grid_barrier_wait_runs_out_and_reports(gg):
@@ -276,13 +280,18 @@ def test_grid_barrier_wait_runs_out_and_reports(gg):
     GG_ERR_DEVICE_TIMEOUT, and the GPU context stays usable."""
     sc = squeezed_box(2048)
     fused = [5, 6]   # tuning sets with the fused cooperative sweep
-    sim = gg.Sim(sc.pos_r, sc.vel, sc.mass, sc.params, tuning=fused[0], barrier_test_phantoms=1)
-    sim.set_bodies(sc.bodies)
-    sim.step(1)
-    with pytest.raises(gg.GGError) as e:
-        sim.sync()
-    assert e.value.status == gg.ERR_DEVICE_TIMEOUT
-    sim.close()
+    import time
+    for limit_us, slowest_s in ((0, 30.0), (20000, 5.0)):   # the default bound, and a 20 ms one
+        sim = gg.Sim(sc.pos_r, sc.vel, sc.mass, sc.params, tuning=fused[0], barrier_test_phantoms=1,
+                     wait_limit_us=limit_us)
+        sim.set_bodies(sc.bodies)
+        t0 = time.perf_counter()
+        sim.step(1)
+        with pytest.raises(gg.GGError) as e:
+            sim.sync()
+        assert e.value.status == gg.ERR_DEVICE_TIMEOUT
+        assert time.perf_counter() - t0 < slowest_s
+        sim.close()
     ok = gg.Sim.from_scene(sc, tuning=fused[0])
     ok.step(2)
     ok.sync()

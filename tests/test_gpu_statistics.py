@@ -1,7 +1,7 @@
 """Long-run statistics.  Trajectories of a collapsing column are chaotic, so after
 thousands of steps FP32 (CUDA path) and FP64 (oracle) agree on what the flow
 produces, not on where each sphere ends up.  The measures are the repose angle of
-the collapsed pile and its centre of mass (pile_stats.pile_statistics).
+the collapsed pile and its centre of mass (paper_2306_01369_gb300.stats.pile_statistics).
 
 Case: scenes.pile_column, 32,768 spheres, mu = 0.2, 20,000 steps (1 s), by which the
 pile has come to rest.  One run's angle varies by about 0.3 degrees (one standard
@@ -19,7 +19,7 @@ import pytest
 
 from conftest import ROOT
 from gpu_helpers import need_gpu
-from pile_stats import pile_statistics
+from paper_2306_01369_gb300.stats import pile_statistics
 from paper_2306_01369_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu

@@ -1,6 +1,4 @@
 """Seeded input generators: shapes and recipes of the workloads (no GPU)."""
-import os
-
 import numpy as np
 
 from paper_2306_01369_gb300 import scenes as S
@@ -42,9 +40,7 @@ def test_pile_statistics_recovers_a_cone():
     known base angle filled uniformly with points.  Below a surface of height H(r) the
     95th percentile of z is 0.95 H(r), so the measure must return atan(0.95 tan(angle));
     the centre of mass must sit h/4 above the base (closed form)."""
-    import sys
-    sys.path.insert(0, os.path.dirname(__file__))
-    from pile_stats import pile_statistics
+    from paper_2306_01369_gb300.stats import pile_statistics
     rng = np.random.default_rng(7)
     for deg in (10.0, 25.0, 35.0):
         R = 0.2
