@@ -95,9 +95,10 @@ typedef struct {
   float density;             /* mass = density 4/3 pi r^3 when no masses are given; 0 -> 2500 */
   uint32_t tuning;           /* 0: the first gg_step times every launch-shape set (binning
                                 included) on a copy of the state (restored bit-exactly) and keeps
-                                the fastest; k >= 1: fixed set k (see gg_tuning_count; sets 7-9 bin
-                                by linked lists, sets 9-10 cap the sweep at 40 registers).
-                                Results do not depend on it. */
+                                the fastest; k >= 1: fixed set k (see gg_tuning_count; sets 7-9,
+                                11-12 bin by linked lists, sets 9, 10, 12 cap the sweep at 40
+                                registers, sets 11-13 find pairs over half the stencil and mirror
+                                them).  Results do not depend on it. */
   uint32_t wrench_history;   /* per-step body wrenches kept for readback; 0 -> 1 */
   uint32_t max_free_bodies;  /* free rigid bodies over all environments (beyond the paper's
                                 kinematic bodies, Sec. V two-way coupling); 0 -> none */

@@ -27,11 +27,13 @@ using gg::StepArgs;
 namespace {
 
 // Launch-shape sets accepted by gg_params.tuning (index k-1).
-// (iters, per-launch sweep block, fused sweep block, fused grid, binning by lists, lean sweeps)
-const gg::LaunchShape kShapes[] = {{0, 256, 0, 0, 0, 0},    {0, 128, 0, 0, 0, 0}, {0, 512, 0, 0, 0, 0},
-                                   {0, 64, 0, 0, 0, 0},     {0, 256, 1024, 0, 0, 0}, {0, 256, 512, 0, 0, 0},
-                                   {0, 256, 0, 0, 1, 0},    {0, 128, 0, 0, 1, 0}, {0, 256, 0, 0, 1, 1},
-                                   {0, 256, 0, 0, 0, 1}};
+// (iters, per-launch sweep block, fused sweep block, fused grid, binning by lists, lean sweeps,
+//  half-stencil pair search)
+const gg::LaunchShape kShapes[] = {{0, 256, 0, 0, 0, 0, 0},    {0, 128, 0, 0, 0, 0, 0}, {0, 512, 0, 0, 0, 0, 0},
+                                   {0, 64, 0, 0, 0, 0, 0},     {0, 256, 1024, 0, 0, 0, 0}, {0, 256, 512, 0, 0, 0, 0},
+                                   {0, 256, 0, 0, 1, 0, 0},    {0, 128, 0, 0, 1, 0, 0}, {0, 256, 0, 0, 1, 1, 0},
+                                   {0, 256, 0, 0, 0, 1, 0},    {0, 256, 0, 0, 1, 0, 1}, {0, 256, 0, 0, 1, 1, 1},
+                                   {0, 256, 0, 0, 0, 0, 1}};
 constexpr uint32_t kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 constexpr uint32_t kStateMagic = 0x31534747u;  // "GGS1"
@@ -543,7 +545,9 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
       (rc = dalloc(s, &a.fcount, s->F)) || (rc = dalloc(s, &a.flist, (size_t)s->F * s->Lcap)) ||
       (rc = dalloc(s, &a.fgb, s->F)) || (rc = dalloc(s, &a.fcc, (size_t)s->F * 8 * s->maxb)))
     return bail(rc);
-  if ((rc = dalloc(s, &a.head, s->nh_pad)) || (rc = dalloc(s, &a.next, n))) return bail(rc);
+  if ((rc = dalloc(s, &a.head, s->nh_pad)) || (rc = dalloc(s, &a.next, n)) || (rc = dalloc(s, &a.pcnt, n)) ||
+      (rc = dalloc(s, &a.pscr, (size_t)2 * s->K * n)))
+    return bail(rc);
   a.F = s->F;
   a.Lcap = s->Lcap;
   s->fgb.assign(s->F, 0xffffffffu);
@@ -567,6 +571,7 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
       (e = cudaMemset(a.bodies, 0, sizeof(DevBody) * nbt)) != cudaSuccess ||
       (e = cudaMemset(a.wrench, 0, sizeof(float) * s->H * nbt * 6)) != cudaSuccess ||
       (e = cudaMemset(a.ccount, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
+      (e = cudaMemset(a.pcnt, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
       (e = cudaMemset(a.sid, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
       (e = cudaMemset(a.key_id, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
       (e = cudaMemset(a.ctrl, 0, sizeof(DevCtrl))) != cudaSuccess ||

@@ -106,6 +106,8 @@ struct StepArgs {
   uint32_t lists;         // binning: 0 counting sort (contiguous buckets), 1 linked lists (Alg. 2)
   uint32_t *head;         // lists: first particle of each bucket (kListEnd: empty), nh_pad entries
   uint32_t *next;         // lists: next particle of the same bucket, [n]
+  uint32_t *pcnt;         // half-stencil pair search: entries per particle (0 between steps), [n]
+  uint32_t *pscr;         // half-stencil pair search: unsorted partners, [2K][n]
   // id order
   float4 *pos_id;   // x, y, z, r
   float4 *vel_id;   // vx, vy, vz, 1/m

@@ -35,6 +35,7 @@ struct LaunchShape {
   uint32_t lists;       // binning: 0 counting sort, 1 linked list per bucket (Alg. 2)
   uint32_t lean;        // per-launch sweeps capped at 40 registers (more resident warps: pays
                         // when the working set spills out of L2, costs when it fits)
+  uint32_t half;        // pair search over half the stencil in two passes instead of k_contacts
 };
 int fused_pja_blocks_per_sm(int block);
 

@@ -290,6 +290,96 @@ __device__ __forceinline__ void insert_partner(uint32_t *fid, uint32_t S, uint32
 constexpr int kWalkGroup = 3;       // buckets of a row (dx = -1, 0, 1), walked together
 constexpr int kContactsBlock = 128;  // threads per block of k_contacts
 
+// Contact records of particle i from its partner list (ascending ids, shared memory,
+// stride S), then its body contacts in ascending body index; counts and U^0.
+__device__ __forceinline__ void contact_records(const StepArgs &a, uint32_t i, float4 pi, uint32_t e, const DevEnv &E,
+                                                const uint32_t *fid, uint32_t S, uint32_t K, uint32_t npp, bool ovf,
+                                                uint32_t &nbc, float &psi_max) {
+    const size_t n = a.n;
+    for (uint32_t c = 0; c < npp; ++c) {
+      const uint32_t j = fid[c * S];
+      float d2;
+      float3 d;
+      const float4 pj = a.pos_id[j];
+      sphere_hit(pi, pj, &d2, &d);
+      const float dist = __fsqrt_rn(d2);
+      float3 nn;
+      if (dist > 0.f) {
+        const float id = __frcp_rn(dist);
+        nn = make_float3(d.x * id, d.y * id, d.z * id);
+      } else {
+        nn = make_float3(0.f, 0.f, i > j ? 1.f : -1.f);
+      }
+      const float psi = __fsub_rn(__fadd_rn(pi.w, pj.w), dist);
+      psi_max = fmaxf(psi_max, psi);
+      const size_t o = (size_t)c * n + i;
+      a.cj[o] = j;
+      a.cn[o] = make_float4(nn.x, nn.y, nn.z, psi);
+      a.clam[o] = 0.f;
+      a.clam[o + (size_t)K * n] = 0.f;
+      a.clam[o + 2 * (size_t)K * n] = 0.f;
+    }
+    // particle-body contacts, bodies in ascending index
+    const float3 xi = make_float3(pi.x, pi.y, pi.z);
+    for (uint32_t b = 0; b < E.nbodies; ++b) {
+      const uint32_t gb = e * a.maxb + b;
+      const DevBody &B = a.bodies[gb];
+      const float3 y = world_to_body(B, xi);
+      int br;
+      const float f = body_sdf(B, y, &br);
+      if (!(f <= pi.w)) continue;
+      if (nbc == a.Kb) {
+        flag(a.ctrl, kFlagBodyOverflow);
+        continue;
+      }
+      const float3 g = body_grad(B, y, br);
+      const float3 nn = rot_apply(B.R, g);
+      const float psi = pi.w - f;
+      psi_max = fmaxf(psi_max, psi);
+      const size_t o = (size_t)nbc * n + i;
+      if (B.is_free) {
+        atomicAdd(&a.ncb[gb], 1u);
+        const uint32_t pos = atomicAdd(&a.fcount[B.fid], 1u);
+        if (pos < a.Lcap)
+          a.flist[(size_t)B.fid * a.Lcap + pos] = i * a.Kb + nbc;
+        else
+          flag(a.ctrl, kFlagBodyOverflow);
+      }
+      a.bj[o] = gb;
+      a.bn[o] = make_float4(nn.x, nn.y, nn.z, psi);
+      a.bxc[o] = make_float4(xi.x - f * nn.x, xi.y - f * nn.y, xi.z - f * nn.z, 0.f);
+      a.blam[o] = 0.f;
+      a.blam[o + (size_t)a.Kb * n] = 0.f;
+      a.blam[o + 2 * (size_t)a.Kb * n] = 0.f;
+      ++nbc;
+    }
+    if (ovf) flag(a.ctrl, kFlagPPOverflow);
+    a.ccount[i] = npp | (nbc << 8);
+    const float4 sb = base_velocity(a, a.vel_id[i]);
+    a.U[0][i] = make_float4(sb.x, sb.y, sb.z, (float)(npp + nbc) * sb.w);
+  }
+
+// Per-step statistics (integer atomics: order-independent); every thread of the warp calls.
+__device__ __forceinline__ void contact_stats(const StepArgs &a, uint32_t npp, uint32_t nbc, float psi_max) {
+  uint32_t s_pp = npp, s_b = nbc, m_pp = npp, m_b = nbc;
+  float m_psi = psi_max;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s_pp += __shfl_xor_sync(0xffffffffu, s_pp, o);
+    s_b += __shfl_xor_sync(0xffffffffu, s_b, o);
+    m_pp = max(m_pp, __shfl_xor_sync(0xffffffffu, m_pp, o));
+    m_b = max(m_b, __shfl_xor_sync(0xffffffffu, m_b, o));
+    m_psi = fmaxf(m_psi, __shfl_xor_sync(0xffffffffu, m_psi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (s_pp) atomicAdd(&a.ctrl->n_pp, s_pp);
+    if (s_b) atomicAdd(&a.ctrl->n_body, s_b);
+    if (m_pp) atomicMax(&a.ctrl->max_pp, m_pp);
+    if (m_b) atomicMax(&a.ctrl->max_body, m_b);
+    if (m_psi > 0.f) atomicMax(&a.ctrl->max_psi_bits, __float_as_uint(m_psi));
+  }
+}
+
 // The partner list of a thread, kept sorted by id while the buckets are walked, lives
 // in shared memory, slot p of thread t at [p * blockDim.x + t] (conflict-free): an
 // array indexed at run time in registers would go to local memory, which at full
@@ -446,87 +536,178 @@ __global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
       }
     }
     }
-    const size_t n = a.n;
-    for (uint32_t c = 0; c < npp; ++c) {
-      const uint32_t j = fid[c * S];
-      float d2;
-      float3 d;
-      const float4 pj = a.pos_id[j];
-      sphere_hit(pi, pj, &d2, &d);
-      const float dist = __fsqrt_rn(d2);
-      float3 nn;
-      if (dist > 0.f) {
-        const float id = __frcp_rn(dist);
-        nn = make_float3(d.x * id, d.y * id, d.z * id);
-      } else {
-        nn = make_float3(0.f, 0.f, i > j ? 1.f : -1.f);
-      }
-      const float psi = __fsub_rn(__fadd_rn(pi.w, pj.w), dist);
-      psi_max = fmaxf(psi_max, psi);
-      const size_t o = (size_t)c * n + i;
-      a.cj[o] = j;
-      a.cn[o] = make_float4(nn.x, nn.y, nn.z, psi);
-      a.clam[o] = 0.f;
-      a.clam[o + (size_t)K * n] = 0.f;
-      a.clam[o + 2 * (size_t)K * n] = 0.f;
-    }
-    // particle-body contacts, bodies in ascending index
-    const float3 xi = make_float3(pi.x, pi.y, pi.z);
-    for (uint32_t b = 0; b < E.nbodies; ++b) {
-      const uint32_t gb = e * a.maxb + b;
-      const DevBody &B = a.bodies[gb];
-      const float3 y = world_to_body(B, xi);
-      int br;
-      const float f = body_sdf(B, y, &br);
-      if (!(f <= pi.w)) continue;
-      if (nbc == a.Kb) {
-        flag(a.ctrl, kFlagBodyOverflow);
-        continue;
-      }
-      const float3 g = body_grad(B, y, br);
-      const float3 nn = rot_apply(B.R, g);
-      const float psi = pi.w - f;
-      psi_max = fmaxf(psi_max, psi);
-      const size_t o = (size_t)nbc * n + i;
-      if (B.is_free) {
-        atomicAdd(&a.ncb[gb], 1u);
-        const uint32_t pos = atomicAdd(&a.fcount[B.fid], 1u);
-        if (pos < a.Lcap)
-          a.flist[(size_t)B.fid * a.Lcap + pos] = i * a.Kb + nbc;
-        else
-          flag(a.ctrl, kFlagBodyOverflow);
-      }
-      a.bj[o] = gb;
-      a.bn[o] = make_float4(nn.x, nn.y, nn.z, psi);
-      a.bxc[o] = make_float4(xi.x - f * nn.x, xi.y - f * nn.y, xi.z - f * nn.z, 0.f);
-      a.blam[o] = 0.f;
-      a.blam[o + (size_t)a.Kb * n] = 0.f;
-      a.blam[o + 2 * (size_t)a.Kb * n] = 0.f;
-      ++nbc;
-    }
-    if (ovf) flag(a.ctrl, kFlagPPOverflow);
-    a.ccount[i] = npp | (nbc << 8);
-    const float4 sb = base_velocity(a, a.vel_id[i]);
-    a.U[0][i] = make_float4(sb.x, sb.y, sb.z, (float)(npp + nbc) * sb.w);
+    contact_records(a, i, pi, e, E, fid, S, K, npp, ovf, nbc, psi_max);
   }
-  // per-step statistics (integer atomics: order-independent)
-  uint32_t s_pp = npp, s_b = nbc, m_pp = npp, m_b = nbc;
-  float m_psi = psi_max;
+  contact_stats(a, npp, nbc, psi_max);
+}
+
+// Half-stencil pair search, two passes (the autotuner's alternative to k_contacts).
+// Pass 1 walks the particle's own cell and the 13 neighbour cells of the forward half
+// (offset (dx, dy, dz) > 0 in (dz, dy, dx) order; in its own cell only partners with a
+// larger id).  Scratch rows 0..K-1 of particle i hold the partners i found (written by
+// i alone), rows K..2K-1 the particles that found i (appended with one atomic per pair
+// on the low half of pcnt[i]); i adds its own count to the high half at the end.  The
+// hit test is symmetric in FP32, so each pair is found once, or twice when two of the
+// walked cells share a bucket.  Pass 2 sorts and deduplicates the entries and writes
+// the same records as k_contacts.
+__device__ __forceinline__ void record_pair(const StepArgs &a, uint32_t i, uint32_t j, uint32_t &nf) {
+  if (nf < a.K) a.pscr[(size_t)nf * a.n + i] = j;
+  ++nf;
+  const uint32_t aj = atomicAdd(&a.pcnt[j], 1u) & 0xffffu;
+  if (aj < a.K) a.pscr[(size_t)(a.K + aj) * a.n + j] = i;
+}
+
+template <bool LISTS>
+__global__ void __launch_bounds__(kContactsBlock) k_pairs_half(StepArgs a) {
+  pdl_enter();
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const float4 pi = a.pos_id[i];
+  const uint32_t e = a.env_of[i];
+  const DevEnv E = a.envs[e];
+  const int32_t k0 = cell_of(pi.x, E.inv_cell), k1 = cell_of(pi.y, E.inv_cell), k2 = cell_of(pi.z, E.inv_cell);
+  uint32_t nf = 0;  // partners found by i
+    // Eq. 6 terms of the three cells along each axis, combined 27 ways below
+    uint32_t hx[3], hy[3], hz[3];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s_pp += __shfl_xor_sync(0xffffffffu, s_pp, o);
-    s_b += __shfl_xor_sync(0xffffffffu, s_b, o);
-    m_pp = max(m_pp, __shfl_xor_sync(0xffffffffu, m_pp, o));
-    m_b = max(m_b, __shfl_xor_sync(0xffffffffu, m_b, o));
-    m_psi = fmaxf(m_psi, __shfl_xor_sync(0xffffffffu, m_psi, o));
+    for (int q = 0; q < 3; ++q) {
+      hx[q] = ((uint32_t)(k0 + q - 1) - kHashQ) * kHashP1;
+      hy[q] = ((uint32_t)(k1 + q - 1) - kHashQ) * kHashP2;
+      hz[q] = ((uint32_t)(k2 + q - 1) - kHashQ) * kHashP3;
+    }
+    // Neighbour cells that cannot hold a partner are not walked.  In cell units
+    // (u = x inv_c, cell k spans [k - 1/2, k + 1/2)) the gap from u_i to the cell
+    // at offset d along an axis is 0 for d = 0 and 1/2 -+ f for d = -+1, f = u_i - k_i.
+    // A partner j has |x_i - x_j| <= r_i + r_j <= r_i + c/2 (c >= 2 r_max is checked
+    // at creation), so a cell whose gap vector is longer than r_i inv_c + 1/2 plus a
+    // margin (float32 rounding of u and of the cell assignment: 2^-10 cells plus
+    // four ulps of |u|) is skipped.  A bucket shared with a nearer cell is still
+    // walked for that cell, so the contact set is exactly the 27-cell one.
+    float g2x[3], g2y[3], g2z[3];
+    {
+      const float ux = __fmul_rn(pi.x, E.inv_cell), uy = __fmul_rn(pi.y, E.inv_cell), uz = __fmul_rn(pi.z, E.inv_cell);
+      const float fx = __fsub_rn(ux, (float)k0), fy = __fsub_rn(uy, (float)k1), fz = __fsub_rn(uz, (float)k2);
+      const float lo_x = fmaxf(0.5f + fx, 0.f), hi_x = fmaxf(0.5f - fx, 0.f);
+      const float lo_y = fmaxf(0.5f + fy, 0.f), hi_y = fmaxf(0.5f - fy, 0.f);
+      const float lo_z = fmaxf(0.5f + fz, 0.f), hi_z = fmaxf(0.5f - fz, 0.f);
+      g2x[0] = lo_x * lo_x; g2x[1] = 0.f; g2x[2] = hi_x * hi_x;
+      g2y[0] = lo_y * lo_y; g2y[1] = 0.f; g2y[2] = hi_y * hi_y;
+      g2z[0] = lo_z * lo_z; g2z[1] = 0.f; g2z[2] = hi_z * hi_z;
+    }
+    float reach;
+    {
+      const float um = fabsf(__fmul_rn(pi.x, E.inv_cell)) + fabsf(__fmul_rn(pi.y, E.inv_cell)) +
+                       fabsf(__fmul_rn(pi.z, E.inv_cell));
+      const float rr = pi.w * E.inv_cell + 0.5f + 0.0009765625f + um * 4.76837158203125e-7f;  // 2^-10, 2^-21
+      reach = rr * rr;
+    }
+  // rows (qy, qz) of the forward half, index 1 = offset 0: (0..2, 2) whole, (2, 1) whole,
+  // (1, 1) with qx = 1 (the own cell) and 2
+#pragma unroll 1
+  for (int row = 0; row < 5; ++row) {
+    const int qz = row < 4 ? (row < 3 ? 2 : 1) : 1;
+    const int qy = row < 3 ? row : (row == 3 ? 2 : 1);
+    const uint32_t mask = row == 4 ? 6u : 7u;
+    const uint32_t hyz = hy[qy] ^ hz[qz];
+    const float g2yz = g2y[qy] + g2z[qz];
+    if constexpr (LISTS) {
+      uint32_t jn[kWalkGroup];
+#pragma unroll
+      for (int q = 0; q < kWalkGroup; ++q)
+        jn[q] = (((mask >> q) & 1u) && g2x[q] + g2yz <= reach) ? a.head[E.hbase + mod_nh(hx[q] ^ hyz, E)]
+                                                                : kListEnd;
+      for (;;) {
+        float4 pc[kWalkGroup];
+        uint32_t nx[kWalkGroup];
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < kWalkGroup; ++q)
+          if (jn[q] != kListEnd) {
+            any = true;
+            pc[q] = a.pos_id[jn[q]];
+            nx[q] = a.next[jn[q]];
+          }
+        if (!any) break;
+#pragma unroll
+        for (int q = 0; q < kWalkGroup; ++q) {
+          if (jn[q] == kListEnd) continue;
+          const uint32_t j = jn[q];
+          float d2;
+          float3 d;
+          const bool own = row == 4 && q == 1;
+          if ((own ? j > i : j != i) && sphere_hit(pi, pc[q], &d2, &d)) record_pair(a, i, j, nf);
+          jn[q] = nx[q];
+        }
+      }
+    } else {
+      uint32_t r0[kWalkGroup], r1[kWalkGroup];
+#pragma unroll
+      for (int q = 0; q < kWalkGroup; ++q) {
+        r0[q] = r1[q] = 0u;
+        if (((mask >> q) & 1u) && g2x[q] + g2yz <= reach) {
+          const uint2 rg = a.range[E.hbase + mod_nh(hx[q] ^ hyz, E)];
+          r0[q] = rg.x;
+          r1[q] = rg.y;
+        }
+      }
+      for (;;) {
+        float4 pc[kWalkGroup];
+        uint32_t live = 0;
+#pragma unroll
+        for (int q = 0; q < kWalkGroup; ++q)
+          if (r0[q] < r1[q]) {
+            live |= 1u << q;
+            pc[q] = a.pos_s[r0[q]];
+          }
+        if (!live) break;
+        uint32_t hit = 0;
+#pragma unroll
+        for (int q = 0; q < kWalkGroup; ++q) {
+          float d2;
+          float3 d;
+          if (((live >> q) & 1u) && sphere_hit(pi, pc[q], &d2, &d)) hit |= 1u << q;
+        }
+        uint32_t jc[kWalkGroup];
+#pragma unroll
+        for (int q = 0; q < kWalkGroup; ++q)
+          if ((hit >> q) & 1u) jc[q] = a.sid[r0[q]];
+#pragma unroll
+        for (int q = 0; q < kWalkGroup; ++q) {
+          r0[q] += (live >> q) & 1u;
+          if (!((hit >> q) & 1u)) continue;
+          const bool own = row == 4 && q == 1;
+          if (own ? jc[q] > i : jc[q] != i) record_pair(a, i, jc[q], nf);
+        }
+      }
+    }
   }
-  if ((threadIdx.x & 31) == 0) {
-    if (s_pp) atomicAdd(&a.ctrl->n_pp, s_pp);
-    if (s_b) atomicAdd(&a.ctrl->n_body, s_b);
-    if (m_pp) atomicMax(&a.ctrl->max_pp, m_pp);
-    if (m_b) atomicMax(&a.ctrl->max_body, m_b);
-    if (m_psi > 0.f) atomicMax(&a.ctrl->max_psi_bits, __float_as_uint(m_psi));
+  if (nf) atomicAdd(&a.pcnt[i], min(nf, a.K + 1u) << 16);
+}
+
+// Pass 2: the partner list of particle i from its scratch entries (sorted, duplicates
+// dropped, the K smallest ids kept as in k_contacts), then the same records.
+__global__ void __launch_bounds__(kContactsBlock) k_pairs_finish(StepArgs a) {
+  pdl_enter();
+  extern __shared__ uint32_t s_fid[];
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t npp = 0, nbc = 0;
+  float psi_max = 0.f;
+  if (i < a.n) {
+    const float4 pi = a.pos_id[i];
+    const uint32_t e = a.env_of[i];
+    const DevEnv E = a.envs[e];
+    uint32_t *fid = s_fid + threadIdx.x;
+    const uint32_t S = blockDim.x;
+    const uint32_t K = a.K;
+    const uint32_t cnt = a.pcnt[i];
+    const uint32_t nfw = cnt >> 16, nbw = cnt & 0xffffu;
+    bool ovf = nfw > K || nbw > K;  // entries were lost: the list may be incomplete
+    for (uint32_t p = 0; p < min(nfw, K); ++p) insert_partner(fid, S, K, a.pscr[(size_t)p * a.n + i], npp, ovf);
+    for (uint32_t p = 0; p < min(nbw, K); ++p) insert_partner(fid, S, K, a.pscr[(size_t)(K + p) * a.n + i], npp, ovf);
+    a.pcnt[i] = 0;  // ready for the next step
+    contact_records(a, i, pi, e, E, fid, S, K, npp, ovf, nbc, psi_max);
   }
+  contact_stats(a, npp, nbc, psi_max);
 }
 
 // ---------------------------------------------------------------------------
@@ -1136,7 +1317,7 @@ static inline cudaError_t mark(cudaEvent_t *ev, int k, cudaStream_t st) {
 
 uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls) {
   uint32_t k = a.lists ? 3 : 5;  // key + list clear or scan x3, wrench sums + body poses
-  if (a.n) k += (a.lists ? 1 : 3) + ((ls.fused_grid && !a.F) ? 1 : ls.iters);  // (scatter, reorder,) contacts, pja
+  if (a.n) k += (a.lists ? 1 : 3) + (ls.half ? 1 : 0) + ((ls.fused_grid && !a.F) ? 1 : ls.iters);  // (scatter, reorder,) contacts, pja
   if (a.n_chunks) k += 1;  // integrate + wrench partials
   if (a.F) k += 1 + ls.iters;  // free_prep, free_update x I
   return k;
@@ -1181,10 +1362,18 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
   GG_MARK(1);
   if (a.n) {
     const size_t smem = (size_t)a.K * kContactsBlock * sizeof(uint32_t);
-    if (a.lists)
-      GG_LAUNCH(k_contacts<true>, dim3(grid_for(a.n, kContactsBlock)), kContactsBlock, smem, a);
-    else
-      GG_LAUNCH(k_contacts<false>, dim3(grid_for(a.n, kContactsBlock)), kContactsBlock, smem, a);
+    const dim3 g(grid_for(a.n, kContactsBlock));
+    if (ls.half) {
+      if (a.lists)
+        GG_LAUNCH(k_pairs_half<true>, g, kContactsBlock, 0, a);
+      else
+        GG_LAUNCH(k_pairs_half<false>, g, kContactsBlock, 0, a);
+      GG_LAUNCH(k_pairs_finish, g, kContactsBlock, smem, a);
+    } else if (a.lists) {
+      GG_LAUNCH(k_contacts<true>, g, kContactsBlock, smem, a);
+    } else {
+      GG_LAUNCH(k_contacts<false>, g, kContactsBlock, smem, a);
+    }
   }
   if (a.F) GG_LAUNCH(k_free_prep, dim3(a.F), 1024, 0, a);
   GG_MARK(2);
