@@ -212,10 +212,23 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def profile_traffic(kernel: str, kernel_digest: str):
-    """ncu DRAM bytes per launch of `kernel` from its committed profile summary
-    ("key: value" lines), if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_column_collapse.txt")
+PROFILE_WORKLOAD = {"column": "column_collapse", "excavation": "excavation", "batched": "batched_beds"}
+
+
+def stage_kernels(flags):
+    """(sweep kernel, contact-stage kernels) that a launch-shape set with GG_TUNE_* names
+    `flags` runs."""
+    sweep = "k_pja_fused" if "fused" in flags else ("k_pja_lean" if "lean" in flags else "k_pja")
+    contacts = "k_pairs_half+k_pairs_finish" if "half" in flags else "k_contacts"
+    return sweep, contacts
+
+
+def profile_traffic(kernel: str, workload: str, kernel_digest: str):
+    """ncu DRAM bytes per launch of `kernel` (the contact stage's kernels summed) from its
+    committed profile summary ("key: value" lines) on this workload, if it was taken on
+    the current kernel source (else None)."""
+    stem = kernel.split("+")[0]
+    path = os.path.join(ROOT, "profiles", f"{stem}_{PROFILE_WORKLOAD[workload]}.txt")
     try:
         kv = {}
         with open(path) as f:
@@ -616,12 +629,14 @@ def run_gpu(args):
         achieved = per_launch / avg_s / 1e9
         return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy), burst",
-                "traffic": profile_traffic(kernel, digest), "bytes_per_launch": per_launch,
+                "traffic": profile_traffic(kernel, args.workload, digest), "bytes_per_launch": per_launch,
                 "avg_launch_us": avg_s * 1e6, "share_of_step": total_ms / sampled_ms,
                 "sampled_steps": len(sampled)}
 
-    roofs = [roof("k_pja", pja_ms, pja_bytes_tot, len(sampled) * sc.params.pja_iters),
-             roof("k_contacts", con_ms, con_bytes_tot, len(sampled))]
+    sweep_kernel, contact_kernels = stage_kernels(sim.tuning_flags)
+    sweep_launches = len(sampled) * (1 if sweep_kernel == "k_pja_fused" else sc.params.pja_iters)
+    roofs = [roof(sweep_kernel, pja_ms, pja_bytes_tot, sweep_launches),
+             roof(contact_kernels, con_ms, con_bytes_tot, len(sampled))]
     roofs.sort(key=lambda r: -r["share_of_step"])
     roof_main, roof_other = roofs
 

@@ -334,6 +334,14 @@ GG_API gg_status gg_backward(gg_sim *sim, const float *dL_dpos, const float *dL_
 GG_API uint32_t gg_tuning_count(void);
 GG_API uint32_t gg_tuning_selected(const gg_sim *sim);
 
+/* What set k (1..gg_tuning_count()) does, as GG_TUNE_* bits; 0 when k is out of range.
+ * Every set gives the same results; the bits only describe how the step is launched. */
+#define GG_TUNE_LISTS 1u /* binning by per-bucket linked lists (else the counting sort) */
+#define GG_TUNE_FUSED 2u /* all sweeps in one cooperative launch with grid barriers */
+#define GG_TUNE_LEAN 4u  /* the sweep capped at 40 registers */
+#define GG_TUNE_HALF 8u  /* pair search over half the stencil, then a mirroring pass */
+GG_API uint32_t gg_tuning_flags(uint32_t k);
+
 /* Time every launch-shape set gg_params.binning allows on the current state (3 steps
  * each, the state restored bit-exactly before each trial and at the end) and keep the
  * fastest.  gg_step does this once, on its first call, when gg_params.tuning = 0; call

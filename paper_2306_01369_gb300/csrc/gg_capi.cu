@@ -341,6 +341,13 @@ const char *gg_last_error(const gg_sim *sim) { return sim ? sim->err.c_str() : "
 
 uint32_t gg_tuning_count(void) { return kNumShapes; }
 
+uint32_t gg_tuning_flags(uint32_t k) {
+  if (k < 1 || k > kNumShapes) return 0;
+  const gg::LaunchShape &ls = kShapes[k - 1];
+  return (ls.lists ? GG_TUNE_LISTS : 0u) | (ls.fused_block ? GG_TUNE_FUSED : 0u) | (ls.lean ? GG_TUNE_LEAN : 0u) |
+         (ls.half ? GG_TUNE_HALF : 0u);
+}
+
 uint32_t gg_kernels_per_step(const gg_sim *sim) { return sim ? gg::kernels_per_step(sim->a, sim->ls) : 0; }
 
 gg_status gg_enable_timing(gg_sim *s, int on) {

@@ -42,6 +42,7 @@ SIGNATURES = {
     "gg_readback": (C.c_int, [_P, C.c_int, _P, C.c_size_t, C.c_int, _P]),
     "gg_set_state": (C.c_int, [_P, _P, C.c_size_t, C.c_int, _P]),
     "gg_tuning_count": (C.c_uint32, []),
+    "gg_tuning_flags": (C.c_uint32, [C.c_uint32]),
     "gg_enable_timing": (C.c_int, [_P, C.c_int]),
     "gg_stage_ms": (C.c_int, [_P, C.POINTER(C.c_float)]),
     "gg_kernels_per_step": (C.c_uint32, [_P]),
@@ -116,6 +117,15 @@ def load():
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+TUNE_BITS = {"lists": 1, "fused": 2, "lean": 4, "half": 8}   # GG_TUNE_* of gg.h
+
+
+def tuning_flags(k):
+    """Names of the GG_TUNE_* bits of launch-shape set k."""
+    bits = load().gg_tuning_flags(k)
+    return {name for name, b in TUNE_BITS.items() if bits & b}
 
 
 class GGError(RuntimeError):
@@ -320,6 +330,11 @@ class Sim:
     @property
     def tuning_selected(self):
         return self._L.gg_tuning_selected(self.h)
+
+    @property
+    def tuning_flags(self):
+        """Names of the GG_TUNE_* bits of the selected set ("lists", "fused", "lean", "half")."""
+        return tuning_flags(self.tuning_selected)
 
     # ------------------------------------------------------------------ readback
     def field_bytes(self, field):

@@ -48,8 +48,20 @@ def test_host_only_calls(lib):
     assert lib.gg_status_string(0) == b"ok"
     assert lib.gg_status_string(4) == b"contact capacity overflow"
     assert lib.gg_tuning_count() >= 2
+    assert lib.gg_tuning_flags(0) == 0 and lib.gg_tuning_flags(lib.gg_tuning_count() + 1) == 0
     assert lib.gg_last_error(None) == b"null simulation"
     lib.gg_destroy(None)   # no-op
+
+
+def test_tuning_sets_cover_every_variant():
+    """Each launch variant exists with both binnings, so the autotuner can pick any
+    combination the binning restriction allows."""
+    from paper_2306_01369_gb300 import gg
+    sets = [gg.tuning_flags(k) for k in range(1, gg.load().gg_tuning_count() + 1)]
+    assert {"lists"} in sets and set() in sets
+    for v in ("lean", "half"):
+        assert {v} in sets and {v, "lists"} in sets
+    assert {"fused"} in sets
 
 
 def test_struct_sizes_match_header():

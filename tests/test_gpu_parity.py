@@ -279,7 +279,7 @@ def test_grid_barrier_wait_runs_out_and_reports(gg):
     (a flag that nothing sets) every wait runs out, the step reports
     GG_ERR_DEVICE_TIMEOUT, and the GPU context stays usable."""
     sc = squeezed_box(2048)
-    fused = [5, 6]   # tuning sets with the fused cooperative sweep
+    fused = [k for k in range(1, gg.load().gg_tuning_count() + 1) if "fused" in gg.tuning_flags(k)]
     import time
     for limit_us, slowest_s in ((0, 30.0), (20000, 5.0)):   # the default bound, and a 20 ms one
         sim = gg.Sim(sc.pos_r, sc.vel, sc.mass, sc.params, tuning=fused[0], barrier_test_phantoms=1,
