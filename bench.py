@@ -62,6 +62,7 @@ def setup_workload(args, scenes, gg, rank, stream):
         preroll = max(0, (COLLAPSE_STEPS - args.steps) // 2 - args.warmup)
         if preroll:
             sim.step(preroll, stream=stream)
+            sim.autotune(stream)          # the collapsing column, not the lattice, decides
         return sc, sim, preroll
     n_run = args.warmup + args.steps + 20
     if args.workload == "excavation":
