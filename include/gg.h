@@ -59,7 +59,9 @@ typedef enum {
   GG_ERR_DEVICE_TIMEOUT = 5,    /* a bounded device-side wait gave up */
   GG_ERR_NONFINITE = 6,         /* a position or velocity became NaN or infinite */
   GG_ERR_UNSUPPORTED = 7,       /* valid request the library does not implement */
-  GG_ERR_NO_DEVICE = 8          /* no usable CUDA device */
+  GG_ERR_NO_DEVICE = 8,         /* no usable CUDA device */
+  GG_ERR_INTERNAL = 9           /* a device-side invariant failed (a bucket list walk longer
+                                   than the particle count); the walk was cut short */
 } gg_status;
 
 /* Rigid-body geometry as signed distance functions (Sec. II-C): closed forms, or

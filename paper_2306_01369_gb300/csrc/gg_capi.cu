@@ -123,6 +123,8 @@ gg_status dalloc(gg_sim *s, T **ptr, size_t count) {
 
 gg_status status_from_flags(gg_sim *s, uint32_t f) {
   if (f & gg::kFlagTimeout) return fail(s, GG_ERR_DEVICE_TIMEOUT, "a grid barrier wait gave up (bounded wait)");
+  if (f & gg::kFlagListBound)
+    return fail(s, GG_ERR_INTERNAL, "a bucket list walk passed the particle count (cut short)");
   if (f & gg::kFlagNonFinite) return fail(s, GG_ERR_NONFINITE, "a particle position or velocity became non-finite");
   if (f & (gg::kFlagPPOverflow | gg::kFlagBodyOverflow))
     return fail(s, GG_ERR_CONTACT_OVERFLOW, "a particle exceeded its contact capacity (flags " + std::to_string(f) + ")");
@@ -333,6 +335,7 @@ const char *gg_status_string(gg_status s) {
   case GG_ERR_NONFINITE: return "non-finite state";
   case GG_ERR_UNSUPPORTED: return "unsupported";
   case GG_ERR_NO_DEVICE: return "no CUDA device";
+  case GG_ERR_INTERNAL: return "internal device invariant failed";
   }
   return "unknown status";
 }
@@ -579,6 +582,7 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
       (e = cudaMemset(a.wrench, 0, sizeof(float) * s->H * nbt * 6)) != cudaSuccess ||
       (e = cudaMemset(a.ccount, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
       (e = cudaMemset(a.pcnt, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
+      (e = cudaMemset(a.head, 0xff, sizeof(uint32_t) * s->nh_pad)) != cudaSuccess ||  // every list empty
       (e = cudaMemset(a.sid, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
       (e = cudaMemset(a.key_id, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
       (e = cudaMemset(a.ctrl, 0, sizeof(DevCtrl))) != cudaSuccess ||

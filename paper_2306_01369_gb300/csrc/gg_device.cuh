@@ -19,6 +19,7 @@ constexpr uint32_t kFlagPPOverflow = 1u;
 constexpr uint32_t kFlagBodyOverflow = 2u;
 constexpr uint32_t kFlagNonFinite = 4u;
 constexpr uint32_t kFlagTimeout = 8u;    // a bounded device-side wait gave up
+constexpr uint32_t kFlagListBound = 16u; // a bucket list walk passed n entries (lists not emptied)
 
 constexpr uint32_t kListEnd = 0xffffffffu;  // end of a bucket's linked list
 constexpr int kMaxK = 32;   // particle-particle capacity limit

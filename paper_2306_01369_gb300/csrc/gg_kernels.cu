@@ -2,17 +2,21 @@
 //
 // One time step = the launches below, in this order (captured once into a CUDA
 // graph and replayed):
-//   k_key            bucket of every particle (Eq. 6), bucket histogram, body prep
+//   k_key            bucket of every particle (Eq. 6), body prep; then either
+//                    a push onto the bucket's linked list (Alg. 2), or
+//                    the bucket histogram for the counting sort:
 //   k_scan_*         exclusive scan of the histogram (tile sums, their scan, down-sweep)
 //                    -> bucket start table and (start, end) ranges
 //   k_scatter        counting-sort scatter (returns the histogram to zero)
 //   k_reorder        stable order inside each bucket (ascending id), positions in slot order
-//   k_contacts       27-cell bucket walk, sphere test, SDF tests (Sec. II-B, II-C)
+//   k_contacts       27-cell bucket walk, sphere test, SDF tests (Sec. II-B, II-C), or
+//   k_pairs_half     the forward half of the walk, hits mirrored into scratch, and
+//   k_pairs_finish   the partner lists sorted and deduplicated, SDF tests
 //   k_free_prep      (free bodies) sorted contact lists, box-corner contacts
 //   k_pja  x I       projected-Jacobi sweeps (Alg. 1), one launch per iteration,
 //   k_free_update    each followed (free bodies) by the bodies' twist update
-//   k_integrate_wrench  symplectic Euler (Eq. 4-5) in place, and per-body impulse
-//                    sums over fixed chunks of particles (deterministic)
+//   k_integrate_wrench  symplectic Euler (Eq. 4-5) in place, per-body impulse sums
+//                    over fixed chunks of particles (deterministic), the lists emptied
 //   k_wrench_bodies  per-body sums over chunks into the wrench readback ring, body
 //                    poses, step counter
 // Contacts, sweeps and integration run over particles in the caller's order (their
@@ -103,7 +107,8 @@ __global__ void k_hist_keys(StepArgs a) {
   if (i < a.n) atomicAdd(&a.cnt[a.key_id[i]], 1u);
 }
 
-// Linked-list binning: every bucket's list starts empty.
+// Linked-list binning: every bucket's list emptied (after a taped step, which ends
+// with its sweeps; a full step does this in k_integrate_wrench).
 __global__ void k_list_clear(StepArgs a) {
   pdl_enter();
   for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < a.nh_total; b += gridDim.x * blockDim.x)
@@ -522,7 +527,9 @@ __global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
 #pragma unroll
       for (int q = 0; q < kWalkGroup; ++q)
         jn[q] = (g2x[q] + g2yz <= reach) ? a.head[E.hbase + mod_nh(hx[q] ^ hyz, E)] : kListEnd;
-      for (;;) {
+      // an intact list has at most n links: past that the lists were not emptied
+      // before this step's pushes (a cycle), so the walk stops and the step reports it
+      for (uint32_t round = 0;; ++round) {
         float4 pc[kWalkGroup];
         uint32_t nx[kWalkGroup];
         bool any = false;
@@ -534,6 +541,10 @@ __global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
             nx[q] = a.next[jn[q]];
           }
         if (!any) break;
+        if (round >= a.n) {
+          flag(a.ctrl, kFlagListBound);
+          break;
+        }
 #pragma unroll
         for (int q = 0; q < kWalkGroup; ++q) {
           if (jn[q] == kListEnd) continue;
@@ -625,7 +636,9 @@ __global__ void __launch_bounds__(kContactsBlock, 9) k_pairs_half(StepArgs a) {
       for (int q = 0; q < kWalkGroup; ++q)
         jn[q] = (((mask >> q) & 1u) && g2x[q] + g2yz <= reach) ? a.head[E.hbase + mod_nh(hx[q] ^ hyz, E)]
                                                                 : kListEnd;
-      for (;;) {
+      // an intact list has at most n links: past that the lists were not emptied
+      // before this step's pushes (a cycle), so the walk stops and the step reports it
+      for (uint32_t round = 0;; ++round) {
         float4 pc[kWalkGroup];
         uint32_t nx[kWalkGroup];
         bool any = false;
@@ -637,6 +650,10 @@ __global__ void __launch_bounds__(kContactsBlock, 9) k_pairs_half(StepArgs a) {
             nx[q] = a.next[jn[q]];
           }
         if (!any) break;
+        if (round >= a.n) {
+          flag(a.ctrl, kFlagListBound);
+          break;
+        }
 #pragma unroll
         for (int q = 0; q < kWalkGroup; ++q) {
           if (jn[q] == kListEnd) continue;
@@ -1088,17 +1105,24 @@ __global__ void __launch_bounds__(kIntegrateThreads) k_integrate_wrench(StepArgs
   const uint32_t s0 = E.off + (c - E.chunk0) * kWrenchChunk;
   const uint32_t s1 = min(s0 + kWrenchChunk, E.off + E.n);
   for (uint32_t i = s0 + threadIdx.x; i < s1; i += kIntegrateThreads) integrate_particle(a, s, i);
+  // linked-list binning: the step's lists have been walked, so empty every bucket for
+  // the next step's pushes here instead of in a launch of its own (created empty)
+  if (a.lists)
+    for (uint32_t b = blockIdx.x * kIntegrateThreads + threadIdx.x; b < a.nh_total; b += gridDim.x * kIntegrateThreads)
+      a.head[b] = kListEnd;
   const size_t n = a.n, KbN = (size_t)a.Kb * n;
   const float inv_dt = 1.0f / a.dt;
   for (uint32_t lb = 0; lb < E.nbodies; ++lb) {
     const uint32_t gb = e * a.maxb + lb;
     const DevBody &B = a.bodies[gb];
     float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int hit = 0;
     for (uint32_t i = s0 + threadIdx.x; i < s1; i += kIntegrateThreads) {
       const uint32_t nbc = (a.ccount[i] >> 8) & 0xffu;
       for (uint32_t k = 0; k < nbc; ++k) {
         const size_t o = (size_t)k * n + i;
         if (a.bj[o] != gb) continue;
+        hit = 1;
         const float fx = -a.blam[o] * inv_dt, fy = -a.blam[o + KbN] * inv_dt, fz = -a.blam[o + 2 * KbN] * inv_dt;
         const float4 xc = a.bxc[o];
         const float rx = xc.x - B.p[0], ry = xc.y - B.p[1], rz = xc.z - B.p[2];
@@ -1110,6 +1134,10 @@ __global__ void __launch_bounds__(kIntegrateThreads) k_integrate_wrench(StepArgs
         v[5] += rx * fy - ry * fx;
       }
     }
+    if (!__syncthreads_or(hit)) {  // no contact with this body in the chunk: zero partial
+      if (threadIdx.x < 6) a.wpart[((size_t)c * a.maxb + lb) * 6 + threadIdx.x] = 0.f;
+      continue;
+    }
     block_sum6<kIntegrateThreads>(v);
     if (threadIdx.x == 0) {
       float *dst = a.wpart + ((size_t)c * a.maxb + lb) * 6;
@@ -1120,42 +1148,37 @@ __global__ void __launch_bounds__(kIntegrateThreads) k_integrate_wrench(StepArgs
   }
 }
 
-// Pose of a body after the step: p += dt v, q <- exp(dt w / 2) q; a free body keeps
-// the twist of its last sweep as its own.
-__device__ __forceinline__ void advance_body(const StepArgs &a, DevBody &B) {
+// Pose of a body after the step: p += dt v, q <- exp(dt w / 2) q (in registers).
+__device__ __forceinline__ void advance_pose(float dt, float p[3], float q[4], const float v[3], const float w[3]) {
 #pragma unroll
-  for (int k = 0; k < 3; ++k) B.p[k] += a.dt * B.v[k];
-  const float tx = a.dt * B.w[0], ty = a.dt * B.w[1], tz = a.dt * B.w[2];
+  for (int k = 0; k < 3; ++k) p[k] += dt * v[k];
+  const float tx = dt * w[0], ty = dt * w[1], tz = dt * w[2];
   const float ang = sqrtf(tx * tx + ty * ty + tz * tz);
   if (ang > 0.f) {
     float sh, ch;
     sincosf(0.5f * ang, &sh, &ch);
     const float sc = sh / ang;
     const float dw = ch, dx = tx * sc, dy = ty * sc, dz = tz * sc;
-    const float qw = B.q[0], qx = B.q[1], qy = B.q[2], qz = B.q[3];
-    float rw = dw * qw - dx * qx - dy * qy - dz * qz;
-    float rx = dw * qx + dx * qw + dy * qz - dz * qy;
-    float ry = dw * qy - dx * qz + dy * qw + dz * qx;
-    float rz = dw * qz + dx * qy - dy * qx + dz * qw;
+    const float qw = q[0], qx = q[1], qy = q[2], qz = q[3];
+    const float rw = dw * qw - dx * qx - dy * qy - dz * qz;
+    const float rx = dw * qx + dx * qw + dy * qz - dz * qy;
+    const float ry = dw * qy - dx * qz + dy * qw + dz * qx;
+    const float rz = dw * qz + dx * qy - dy * qx + dz * qw;
     const float inv = rsqrtf(rw * rw + rx * rx + ry * ry + rz * rz);
-    B.q[0] = rw * inv;
-    B.q[1] = rx * inv;
-    B.q[2] = ry * inv;
-    B.q[3] = rz * inv;
-  }
-  if (B.is_free) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      B.own_v[k] = B.v[k];
-      B.own_w[k] = B.w[k];
-    }
+    q[0] = rw * inv;
+    q[1] = rx * inv;
+    q[2] = ry * inv;
+    q[3] = rz * inv;
   }
 }
 
 // One warp per body: sum its environment's chunk partials in a fixed order
 // (lane-strided, then a fixed butterfly) into the wrench ring, then advance the body's
-// pose (no warp reads another body's pose).  The last block to finish advances the
-// step counter (every block read it first; no block waits for another).
+// pose (no warp reads another body's pose); a free body keeps the twist of its last
+// sweep as its own.  Every load a warp needs is issued before any of them is used (the
+// chunk range, the body's flags and pose, then the partials), so the kernel is a short
+// chain of memory round trips.  The last block to finish advances the step counter
+// (every block read it first; no block waits for another).
 __global__ void __launch_bounds__(256) k_wrench_bodies(StepArgs a) {
   pdl_enter();
   const uint32_t gb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1163,35 +1186,43 @@ __global__ void __launch_bounds__(256) k_wrench_bodies(StepArgs a) {
   const uint32_t nbt = a.n_envs * a.maxb;
   const uint32_t step = a.ctrl->step;
   if (gb < nbt) {
-    float *dst = a.wrench + ((size_t)(step % a.wrench_hist) * nbt + gb) * 6;
     DevBody &B = a.bodies[gb];
-    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (B.active) {
-      const uint32_t e = gb / a.maxb, lb = gb % a.maxb;
-      const DevEnv &E = a.envs[e];
-      for (uint32_t c = E.chunk0 + lane; c < E.chunk0 + E.nchunks; c += 32) {
-        const float *src = a.wpart + ((size_t)c * a.maxb + lb) * 6;
+    const uint32_t e = gb / a.maxb, lb = gb % a.maxb;
+    const uint32_t c0 = a.envs[e].chunk0, c1 = c0 + a.envs[e].nchunks;
+    const uint32_t active = B.active, is_free = B.is_free;
+    float p[3], q[4], bv[3], bw[3];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) v[k] += src[k];
-      }
+    for (int k = 0; k < 3; ++k) {
+      p[k] = B.p[k];
+      bv[k] = B.v[k];
+      bw[k] = B.w[k];
     }
 #pragma unroll
-    for (int k = 0; k < 6; ++k)
+    for (int k = 0; k < 4; ++k) q[k] = B.q[k];
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (uint32_t c = c0 + lane; c < c1; c += 32) {
+      const float *src = a.wpart + ((size_t)c * a.maxb + lb) * 6;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) v[k] += src[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      v[k] = active ? v[k] : 0.f;  // partials of an inactive slot are never written
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    if (lane == 0 && B.active && a.F) {  // free-box corners: +lambda on the box, -lambda on the other body
-      const uint32_t e = gb / a.maxb;
+    }
+    if (lane == 0 && active && a.F) {  // free-box corners: +lambda on the box, -lambda on the other body
       const float inv_dt = 1.0f / a.dt;
-      for (uint32_t lb = 0; lb < a.maxb; ++lb) {
-        const DevBody &Fb = a.bodies[e * a.maxb + lb];
+      for (uint32_t ob = 0; ob < a.maxb; ++ob) {
+        const DevBody &Fb = a.bodies[e * a.maxb + ob];
         if (!Fb.active || !Fb.is_free) continue;
         const CornerContact *cc = a.fcc + (size_t)Fb.fid * 8 * a.maxb;
         for (uint32_t t = 0; t < 8 * a.maxb; ++t) {
           if (!cc[t].valid) continue;
-          const float sg = (e * a.maxb + lb == gb) ? inv_dt : ((e * a.maxb + cc[t].o == gb) ? -inv_dt : 0.f);
+          const float sg = (e * a.maxb + ob == gb) ? inv_dt : ((e * a.maxb + cc[t].o == gb) ? -inv_dt : 0.f);
           if (sg == 0.f) continue;
           const float fx = sg * cc[t].lam[0], fy = sg * cc[t].lam[1], fz = sg * cc[t].lam[2];
-          const float rx = cc[t].xc[0] - B.p[0], ry = cc[t].xc[1] - B.p[1], rz = cc[t].xc[2] - B.p[2];
+          const float rx = cc[t].xc[0] - p[0], ry = cc[t].xc[1] - p[1], rz = cc[t].xc[2] - p[2];
           v[0] += fx;
           v[1] += fy;
           v[2] += fz;
@@ -1202,17 +1233,35 @@ __global__ void __launch_bounds__(256) k_wrench_bodies(StepArgs a) {
       }
     }
     if (lane == 0) {
+      float *dst = a.wrench + ((size_t)(step % a.wrench_hist) * nbt + gb) * 6;
 #pragma unroll
       for (int k = 0; k < 6; ++k) dst[k] = v[k];
-      if (B.active) advance_body(a, B);
+      if (active) {
+        advance_pose(a.dt, p, q, bv, bw);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) B.p[k] = p[k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) B.q[k] = q[k];
+        if (is_free) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            B.own_v[k] = bv[k];
+            B.own_w[k] = bw[k];
+          }
+        }
+      }
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&a.ctrl->blocks_done, 1u) == gridDim.x - 1) {
-      a.ctrl->blocks_done = 0;
+    if (gridDim.x == 1) {  // every warp of the only block has read the counter
       a.ctrl->step = step + 1;
+    } else {
+      __threadfence();
+      if (atomicAdd(&a.ctrl->blocks_done, 1u) == gridDim.x - 1) {
+        a.ctrl->blocks_done = 0;
+        a.ctrl->step = step + 1;
+      }
     }
   }
 }
@@ -1325,7 +1374,7 @@ static inline cudaError_t mark(cudaEvent_t *ev, int k, cudaStream_t st) {
 }
 
 uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls) {
-  uint32_t k = a.lists ? 3 : 5;  // key + list clear or scan x3, wrench sums + body poses
+  uint32_t k = a.lists ? 2 : 5;  // key (+ scan x3), wrench sums + body poses
   if (a.n) k += (a.lists ? 1 : 3) + (ls.half ? 1 : 0) + ((ls.fused_grid && !a.F) ? 1 : ls.iters);  // (scatter, reorder,) contacts, pja
   if (a.n_chunks) k += 1;  // integrate + wrench partials
   if (a.F) k += 1 + ls.iters;  // free_prep, free_update x I
@@ -1355,8 +1404,7 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
   } while (0)
   GG_MARK(0);
   if (a.lists) {
-    GG_LAUNCH(k_list_clear, dim3(std::min<uint32_t>(grid_for(a.nh_total, 256), 4096u)), 256, 0, a);
-    GG_LAUNCH(k_key, dim3(grid_for(nk, 256)), 256, 0, a);
+    GG_LAUNCH(k_key, dim3(grid_for(nk, 256)), 256, 0, a);  // the lists were emptied by the last step
   } else {
     GG_LAUNCH(k_key, dim3(grid_for(nk, 256)), 256, 0, a);
     const uint32_t nblk = a.nh_pad / kScanTile;
@@ -1417,7 +1465,10 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
     }
     if (a.F) GG_LAUNCH(k_free_update, dim3(a.F), 256, 0, a);
   }
-  if (tp) return cudaGetLastError();
+  if (tp) {  // the taped step ends here; empty the lists it filled
+    if (a.lists) GG_LAUNCH(k_list_clear, dim3(std::min<uint32_t>(grid_for(a.nh_total, 256), 4096u)), 256, 0, a);
+    return cudaGetLastError();
+  }
   GG_MARK(3);
   if (a.n_chunks) GG_LAUNCH(k_integrate_wrench, dim3(a.n_chunks), kIntegrateThreads, 0, a, (int)(ls.iters & 1));
   GG_LAUNCH(k_wrench_bodies, dim3(grid_for(nbt * 32, 256)), 256, 0, a);
