@@ -54,11 +54,17 @@ def workload_config(sc, workload="column"):
             "bodies": "ground plane"}
 
 
+def hash_kw(args):
+    """Hash table size: autotuned among 2n, 4n, 8n (results do not depend on it), or the
+    fixed factor given on the command line (2: the paper's table size)."""
+    return dict(hash_factor=args.hash_factor) if args.hash_factor else dict(hash_tune=1)
+
+
 def setup_workload(args, scenes, gg, rank, stream):
     """(scene, simulation, untimed steps before the warm-up) of the timed workload."""
     if args.workload == "column":
         sc = scenes.column_collapse(seed=1001 + rank)
-        sim = gg.Sim.from_scene(sc, tuning=args.tuning)
+        sim = gg.Sim.from_scene(sc, tuning=args.tuning, **hash_kw(args))
         preroll = max(0, (COLLAPSE_STEPS - args.steps) // 2 - args.warmup)
         if preroll:
             sim.step(preroll, stream=stream)
@@ -73,7 +79,7 @@ def setup_workload(args, scenes, gg, rank, stream):
         settle = 1500
     parked = scenes.Scene(sc.name, sc.pos_r, sc.vel, sc.mass, sc.bodies, sc.params, sc.n_steps,
                           env_offsets=sc.env_offsets, body_offsets=sc.body_offsets)
-    sim = gg.Sim.from_scene(parked, tuning=args.tuning)
+    sim = gg.Sim.from_scene(parked, tuning=args.tuning, **hash_kw(args))
     sim.step(settle, stream=stream)       # the bed settles, then the tools start digging
     sim.autotune(stream)                  # the settled bed, not the lattice, decides the launch shapes
     bo = sc.body_offsets
@@ -364,7 +370,7 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
                           "kinetic_energy_j": ke}
     # small settle: 4,096 spheres in an open box, 200 steps (the oracle runs it whole)
     ss = scenes.settle_box(n=4096, n_steps=200)
-    sim = gg.Sim.from_scene(ss)
+    sim = gg.Sim.from_scene(ss, hash_tune=1)
     sim.step(3, stream=stream)
     sim.set_particles(ss.pos_r, ss.vel, stream=stream)
     ms = _timed_steps(sim, 200, stream, torch)
@@ -380,7 +386,7 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
     sc = scenes.batched_beds(n_envs=256, n_steps=steps_batched + 10)
     parked = scenes.Scene(sc.name, sc.pos_r, sc.vel, sc.mass, sc.bodies, sc.params, sc.n_steps,
                           env_offsets=sc.env_offsets, body_offsets=sc.body_offsets)
-    sim = gg.Sim.from_scene(parked)
+    sim = gg.Sim.from_scene(parked, hash_tune=1)
     sim.step(settle_steps, stream=stream)
     sim.autotune(stream)
     bo = sc.body_offsets
@@ -405,7 +411,7 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
         es = scenes.Scene("env", settled_pos[o0:o1], settled_vel[o0:o1], sc.mass[o0:o1], sc.bodies[b0:b1],
                           sc.params, sc.n_steps,
                           twist={gb - b0: t[3:] for gb, t in sc.twist.items() if b0 <= gb < b1})
-        one = gg.Sim.from_scene(es)
+        one = gg.Sim.from_scene(es, hash_tune=1)
         one.step(3, stream=stream)
         per_env_ms.append(_timed_steps(one, 20, stream, torch) / 20)
         one.close()
@@ -508,7 +514,7 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
     if time.perf_counter() - t_start < seconds_cap:
         ex = scenes.excavation(n=1048576, n_steps=steps_exc + 20)
         parked = scenes.Scene(ex.name, ex.pos_r, ex.vel, ex.mass, ex.bodies, ex.params, ex.n_steps)
-        sim = gg.Sim.from_scene(parked, wrench_history=steps_exc)
+        sim = gg.Sim.from_scene(parked, wrench_history=steps_exc, hash_tune=1)
         sim.step(settle_steps_exc, stream=stream)   # the bed settles under the parked scoop
         sim.autotune(stream)
         sim.set_trajectory(1, ex.twist[1])
@@ -665,11 +671,14 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_extras and args.workload == "column":
         xtra = extras(torch, dev, stream)
 
+    n_env0 = int(sc.env_offsets[1]) if sc.env_offsets is not None else sc.n
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {**workload_config(sc, args.workload), "replicas": world, "tuning_set": sim.tuning_selected,
+                           "hash_table": f"n_h = {sim.hash_size(0) / n_env0:.0f} n per environment "
+                                         f"({'fixed' if args.hash_factor else 'autotuned among 2n, 4n, 8n'})",
                            "timed_steps": window},
                 "roofline": roof_main, "roofline_next": roof_other, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "steps": e2e_steps,
@@ -694,6 +703,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gg", "reference"], default="gg")
     ap.add_argument("--tuning", type=int, default=0)
+    ap.add_argument("--hash-factor", type=int, default=0,
+                    help="fixed n_h = F n per environment (2: the paper's); 0: the autotuner picks 2n, 4n or 8n")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -120,6 +120,11 @@ typedef struct {
   uint32_t wait_limit_us;    /* bound of every device-side wait (the grid barrier of the fused
                                 sweep), microseconds at the SM's maximum clock; past it the step
                                 reports GG_ERR_DEVICE_TIMEOUT.  0 -> 500,000 */
+  uint32_t hash_tune;        /* 1 (with hash_size = hash_factor = 0): the autotuner also picks n_h
+                                among 2n, 4n and 8n per environment (tables sized for 8n).
+                                Positions, velocities and contacts do not depend on n_h; the
+                                bucket keys and the sort-order readbacks are those of the n_h
+                                in use (gg_hash_size).  0: n_h fixed as above */
 } gg_params;
 
 typedef struct {
@@ -331,6 +336,10 @@ GG_API gg_status gg_tape_reserve(gg_sim *sim, uint32_t n_steps, uint32_t checkpo
 GG_API gg_status gg_step_taped(gg_sim *sim, uint32_t tool_body, uint32_t n_steps, void *stream);
 GG_API gg_status gg_backward(gg_sim *sim, const float *dL_dpos, const float *dL_dvel, const float *dL_dpose,
                              float *dL_dtwist, float *dL_dmu, int on_device, void *stream);
+
+/* Hash table size n_h in use for environment `env` (Eq. 6's modulus); 0 for a bad
+ * argument. */
+GG_API uint32_t gg_hash_size(const gg_sim *sim, uint32_t env);
 
 /* Number of fixed launch-shape sets accepted by gg_params.tuning, and the set chosen. */
 GG_API uint32_t gg_tuning_count(void);

@@ -36,6 +36,10 @@ const gg::LaunchShape kShapes[] = {{0, 256, 0, 0, 0, 0, 0},    {0, 128, 0, 0, 0,
                                    {0, 256, 0, 0, 0, 0, 1}};
 constexpr uint32_t kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
+// n_h factors the autotuner tries when gg_params.hash_tune is set (the paper's 2n first)
+constexpr uint32_t kHashFactors[] = {2, 4, 8};
+constexpr uint32_t kNumHashFactors = sizeof(kHashFactors) / sizeof(kHashFactors[0]);
+
 constexpr uint32_t kStateMagic = 0x31534747u;  // "GGS1"
 
 struct StateHeader {
@@ -51,6 +55,8 @@ struct gg_sim {
   gg_params p{};
   uint32_t n = 0, n_envs = 0, maxb = 0, K = 0, Kb = 0, H = 1;
   uint32_t nh_total = 0, nh_pad = 0, n_chunks = 0;
+  uint32_t nh_cap = 0;   // buckets allocated (nh_pad at the largest n_h factor tried)
+  uint32_t hf = 2;       // n_h factor in use (hash_size = 0)
   std::vector<DevEnv> envs;
   std::vector<uint32_t> nbodies;
   std::vector<float *> traj;  // per body slot
@@ -250,6 +256,58 @@ gg_status capture(gg_sim *s);
 // tuning == 0: time every launch-shape set on the current state (3 steps each, after
 // one untimed step), restoring the state before each trial and at the end, and keep
 // the fastest.  Every set gives bit-identical results, so the choice cannot change them.
+// Bucket ranges of every environment for n_h = factor x n_env (or the fixed hash_size):
+// the host table, the totals and the step arguments.  Does not touch the device.
+gg_status layout_hash(gg_sim *s, uint32_t factor) {
+  uint64_t hb = 0;
+  for (DevEnv &E : s->envs) {
+    uint64_t nh = s->p.hash_size ? s->p.hash_size : (uint64_t)factor * E.n;
+    if (nh == 0) nh = 1;
+    E.hbase = (uint32_t)hb;
+    E.nh = (uint32_t)nh;
+    E.nh_magic = gg::remainder_magic(E.nh);
+    hb += nh;
+    if (hb > 0xF0000000ull) return fail(s, GG_ERR_INVALID_ARG, "hash tables exceed 2^32 buckets");
+  }
+  uint32_t pad = (uint32_t)(((hb + gg::kScanTile - 1) / gg::kScanTile) * gg::kScanTile);
+  if (pad == 0) pad = gg::kScanTile;
+  if (s->nh_cap && pad > s->nh_cap) return fail(s, GG_ERR_INVALID_ARG, "n_h factor beyond the allocated tables");
+  s->nh_total = (uint32_t)hb;
+  s->nh_pad = pad;
+  s->a.nh_total = s->nh_total;
+  s->a.nh_pad = s->nh_pad;
+  s->hf = factor;
+  return GG_OK;
+}
+
+// Switch the n_h factor between steps: new bucket ranges on the device (ordered on
+// `st`), graphs recaptured on the next step.  Every list is empty and every histogram
+// count zero between steps over the whole allocation, so nothing else changes.
+gg_status set_hash_factor(gg_sim *s, uint32_t factor, cudaStream_t st) {
+  if (factor == s->hf) return GG_OK;
+  gg_status rc = layout_hash(s, factor);
+  if (rc != GG_OK) return rc;
+  GG_CUDA(s, cudaMemcpyAsync(s->a.envs, s->envs.data(), sizeof(DevEnv) * s->n_envs, cudaMemcpyHostToDevice, st));
+  GG_CUDA(s, cudaStreamSynchronize(st));  // the host table may change again before the copy would run
+  free_graph(s);
+  return GG_OK;
+}
+
+// Time the current graph: one untimed step, then 3 (state restored first).
+gg_status time_trial(gg_sim *s, const char *saved, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st, float *ms) {
+  gg_status rc = capture(s);
+  if (rc != GG_OK) return rc;
+  if ((rc = restore_state(s, saved, st)) != GG_OK) return rc;
+  cudaError_t ce = cudaGraphLaunch(s->exec[s->timing], st);
+  if (ce == cudaSuccess) ce = cudaEventRecord(e0, st);
+  for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = cudaGraphLaunch(s->exec[s->timing], st);
+  if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+  if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+  if (ce == cudaSuccess) ce = cudaEventElapsedTime(ms, e0, e1);
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "autotune trial");
+  return GG_OK;
+}
+
 gg_status autotune(gg_sim *s, cudaStream_t st) {
   s->tuned = true;
   if (s->p.tuning || !s->n) return GG_OK;
@@ -265,30 +323,36 @@ gg_status autotune(gg_sim *s, cudaStream_t st) {
   gg_status rc = save_state(s, saved, st);
   if (rc == GG_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
     rc = cuda_fail(s, cudaGetLastError(), "cudaEventCreate");
+  // launch-shape sets at the n_h in use, then (hash_tune) the n_h factors with the
+  // chosen set
+  const bool tune_nh = s->p.hash_tune && !s->p.hash_size && !s->p.hash_factor;
+  uint32_t best_f = s->hf;
+  if (tune_nh) rc = rc == GG_OK ? set_hash_factor(s, kHashFactors[0], st) : rc;
   bool first = true;
   for (uint32_t k = 1; rc == GG_OK && k <= kNumShapes; ++k) {
     if (!shape_allowed(s, k)) continue;
     if ((rc = set_shape(s, k)) != GG_OK || (kShapes[k - 1].fused_block && !s->ls.fused_grid)) continue;
-    if ((rc = capture(s)) != GG_OK) break;
-    if ((rc = restore_state(s, saved, st)) != GG_OK) break;
     float ms = 0.f;
-    cudaError_t ce = cudaGraphLaunch(s->exec[s->timing], st);
-    if (ce == cudaSuccess) ce = cudaEventRecord(e0, st);
-    for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = cudaGraphLaunch(s->exec[s->timing], st);
-    if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
-    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
-    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
-    if (ce != cudaSuccess) {
-      rc = cuda_fail(s, ce, "autotune trial");
-      break;
-    }
+    if ((rc = time_trial(s, saved, e0, e1, st, &ms)) != GG_OK) break;
     if (first || ms < best) {
       best = ms;
       best_k = k;
+      best_f = s->hf;
       first = false;
     }
   }
+  if (rc == GG_OK && tune_nh) rc = set_shape(s, best_k);
+  for (uint32_t f = 1; rc == GG_OK && tune_nh && f < kNumHashFactors; ++f) {
+    float ms = 0.f;
+    if ((rc = set_hash_factor(s, kHashFactors[f], st)) != GG_OK) break;
+    if ((rc = time_trial(s, saved, e0, e1, st, &ms)) != GG_OK) break;
+    if (ms < best) {
+      best = ms;
+      best_f = kHashFactors[f];
+    }
+  }
   if (rc == GG_OK) rc = restore_state(s, saved, st);
+  if (rc == GG_OK) rc = set_hash_factor(s, best_f, st);
   if (rc == GG_OK) rc = set_shape(s, best_k);
   if (rc == GG_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = cuda_fail(s, cudaGetLastError(), "autotune");
   if (e0) cudaEventDestroy(e0);
@@ -343,6 +407,8 @@ const char *gg_status_string(gg_status s) {
 const char *gg_last_error(const gg_sim *sim) { return sim ? sim->err.c_str() : "null simulation"; }
 
 uint32_t gg_tuning_count(void) { return kNumShapes; }
+
+uint32_t gg_hash_size(const gg_sim *s, uint32_t env) { return (s && env < s->n_envs) ? s->envs[env].nh : 0; }
 
 uint32_t gg_tuning_flags(uint32_t k) {
   if (k < 1 || k > kNumShapes) return 0;
@@ -480,7 +546,6 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
   }
   // environments: cell size, hash range, wrench chunks
   s->envs.resize(n_envs);
-  uint64_t hb = 0;
   uint32_t chunks = 0;
   for (uint32_t e = 0; e < n_envs; ++e) {
     DevEnv &E = s->envs[e];
@@ -496,21 +561,17 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
       return bail(fail(s, GG_ERR_INVALID_ARG, "cell_size must be >= 2 r_max of every environment"));
     if (!(c > 0.f)) c = 1.0f;
     E.inv_cell = (float)(1.0 / (double)c);
-    uint64_t nh = P.hash_size ? P.hash_size : (uint64_t)(P.hash_factor ? P.hash_factor : 2) * E.n;
-    if (nh == 0) nh = 1;
-    E.hbase = (uint32_t)hb;
-    E.nh = (uint32_t)nh;
-    E.nh_magic = gg::remainder_magic(E.nh);
-    hb += nh;
-    if (hb > 0xF0000000ull) return bail(fail(s, GG_ERR_INVALID_ARG, "hash tables exceed 2^32 buckets"));
     E.nbodies = 0;
     E.chunk0 = chunks;
     E.nchunks = (E.n + gg::kWrenchChunk - 1) / gg::kWrenchChunk;
     chunks += E.nchunks;
   }
-  s->nh_total = (uint32_t)hb;
-  s->nh_pad = (uint32_t)(((hb + gg::kScanTile - 1) / gg::kScanTile) * gg::kScanTile);
-  if (s->nh_pad == 0) s->nh_pad = gg::kScanTile;
+  const uint32_t hf0 = P.hash_factor ? P.hash_factor : 2;
+  const bool tune_nh = P.hash_tune && !P.hash_size && !P.hash_factor;
+  if (P.hash_tune > 1) return bail(GG_ERR_INVALID_ARG);
+  if ((rc = layout_hash(s, tune_nh ? kHashFactors[kNumHashFactors - 1] : hf0)) != GG_OK) return bail(rc);
+  s->nh_cap = s->nh_pad;  // allocation for the largest factor; then the factor in use
+  if ((rc = layout_hash(s, hf0)) != GG_OK) return bail(rc);
   s->n_chunks = chunks;
   const uint32_t nbt = n_envs * s->maxb;
   s->nbodies.assign(n_envs, 0);
@@ -542,8 +603,8 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
   for (int k = 0; k < 3; ++k) a.g[k] = P.gravity[k];
   const size_t nK = (size_t)n * s->K, nKb = (size_t)n * s->Kb;
   if ((rc = dalloc(s, &a.pos_id, n)) || (rc = dalloc(s, &a.vel_id, n)) || (rc = dalloc(s, &a.env_of, n)) ||
-      (rc = dalloc(s, &a.key_id, n)) || (rc = dalloc(s, &a.cnt, s->nh_pad)) ||
-      (rc = dalloc(s, &a.start, (size_t)s->nh_pad + 4)) || (rc = dalloc(s, &a.range, s->nh_pad)) || (rc = dalloc(s, &a.bsum, s->nh_pad / gg::kScanTile)) ||
+      (rc = dalloc(s, &a.key_id, n)) || (rc = dalloc(s, &a.cnt, s->nh_cap)) ||
+      (rc = dalloc(s, &a.start, (size_t)s->nh_cap + 4)) || (rc = dalloc(s, &a.range, s->nh_cap)) || (rc = dalloc(s, &a.bsum, s->nh_cap / gg::kScanTile)) ||
       (rc = dalloc(s, &a.sid_tmp, n)) || (rc = dalloc(s, &a.sid, n)) || (rc = dalloc(s, &a.pos_s, n)) || (rc = dalloc(s, &a.U[0], n)) ||
       (rc = dalloc(s, &a.U[1], n)) || (rc = dalloc(s, &a.ccount, n)) || (rc = dalloc(s, &a.cj, nK)) ||
       (rc = dalloc(s, &a.cn, nK)) || (rc = dalloc(s, &a.clam, 3 * nK)) || (rc = dalloc(s, &a.bj, nKb)) ||
@@ -555,7 +616,7 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
       (rc = dalloc(s, &a.fcount, s->F)) || (rc = dalloc(s, &a.flist, (size_t)s->F * s->Lcap)) ||
       (rc = dalloc(s, &a.fgb, s->F)) || (rc = dalloc(s, &a.fcc, (size_t)s->F * 8 * s->maxb)))
     return bail(rc);
-  if ((rc = dalloc(s, &a.head, s->nh_pad)) || (rc = dalloc(s, &a.next, n)) || (rc = dalloc(s, &a.pcnt, n)) ||
+  if ((rc = dalloc(s, &a.head, s->nh_cap)) || (rc = dalloc(s, &a.next, n)) || (rc = dalloc(s, &a.pcnt, n)) ||
       (rc = dalloc(s, &a.pscr, (size_t)2 * s->K * n)))
     return bail(rc);
   a.F = s->F;
@@ -576,13 +637,13 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
   GG_UP(a.envs, s->envs.data(), sizeof(DevEnv) * n_envs);
   GG_UP(a.chunk_env, h_chunk_env.data(), sizeof(uint32_t) * h_chunk_env.size());
 #undef GG_UP
-  if ((e = cudaMemset(a.cnt, 0, sizeof(uint32_t) * s->nh_pad)) != cudaSuccess ||
-      (e = cudaMemset(a.start, 0, sizeof(uint32_t) * ((size_t)s->nh_pad + 4))) != cudaSuccess ||
+  if ((e = cudaMemset(a.cnt, 0, sizeof(uint32_t) * s->nh_cap)) != cudaSuccess ||
+      (e = cudaMemset(a.start, 0, sizeof(uint32_t) * ((size_t)s->nh_cap + 4))) != cudaSuccess ||
       (e = cudaMemset(a.bodies, 0, sizeof(DevBody) * nbt)) != cudaSuccess ||
       (e = cudaMemset(a.wrench, 0, sizeof(float) * s->H * nbt * 6)) != cudaSuccess ||
       (e = cudaMemset(a.ccount, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
       (e = cudaMemset(a.pcnt, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
-      (e = cudaMemset(a.head, 0xff, sizeof(uint32_t) * s->nh_pad)) != cudaSuccess ||  // every list empty
+      (e = cudaMemset(a.head, 0xff, sizeof(uint32_t) * s->nh_cap)) != cudaSuccess ||  // every list empty
       (e = cudaMemset(a.sid, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
       (e = cudaMemset(a.key_id, 0, sizeof(uint32_t) * std::max(n, 1u))) != cudaSuccess ||
       (e = cudaMemset(a.ctrl, 0, sizeof(DevCtrl))) != cudaSuccess ||

@@ -1172,46 +1172,46 @@ __device__ __forceinline__ void advance_pose(float dt, float p[3], float q[4], c
   }
 }
 
-// One warp per body: sum its environment's chunk partials in a fixed order
-// (lane-strided, then a fixed butterfly) into the wrench ring, then advance the body's
-// pose (no warp reads another body's pose); a free body keeps the twist of its last
-// sweep as its own.  Every load a warp needs is issued before any of them is used (the
-// chunk range, the body's flags and pose, then the partials), so the kernel is a short
-// chain of memory round trips.  The last block to finish advances the step counter
-// (every block read it first; no block waits for another).
-__global__ void __launch_bounds__(256) k_wrench_bodies(StepArgs a) {
+// One block per body slot: sum its environment's chunk partials in a fixed order (a
+// thread per chunk, strided, then the block's fixed tree) into the wrench ring, then
+// advance the body's pose (no block reads another body's pose); a free body keeps the
+// twist of its last sweep as its own.  A block's loads are all issued before any is
+// used, so the kernel is one memory round trip deep (a warp per body walking the
+// chunks in turn was eight round trips deep on a 256-chunk environment: 10 us).  The
+// last block to finish advances the step counter (every block read it first; no block
+// waits for another).
+constexpr int kWrenchBodyThreads = 256;
+
+__global__ void __launch_bounds__(kWrenchBodyThreads) k_wrench_bodies(StepArgs a) {
   pdl_enter();
-  const uint32_t gb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const uint32_t gb = blockIdx.x;
   const uint32_t nbt = a.n_envs * a.maxb;
   const uint32_t step = a.ctrl->step;
-  if (gb < nbt) {
-    DevBody &B = a.bodies[gb];
-    const uint32_t e = gb / a.maxb, lb = gb % a.maxb;
-    const uint32_t c0 = a.envs[e].chunk0, c1 = c0 + a.envs[e].nchunks;
-    const uint32_t active = B.active, is_free = B.is_free;
-    float p[3], q[4], bv[3], bw[3];
+  DevBody &B = a.bodies[gb];
+  const uint32_t e = gb / a.maxb, lb = gb % a.maxb;
+  const uint32_t c0 = a.envs[e].chunk0, c1 = c0 + a.envs[e].nchunks;
+  const uint32_t active = B.active, is_free = B.is_free;
+  float p[3], q[4], bv[3], bw[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      p[k] = B.p[k];
-      bv[k] = B.v[k];
-      bw[k] = B.w[k];
-    }
+  for (int k = 0; k < 3; ++k) {
+    p[k] = B.p[k];
+    bv[k] = B.v[k];
+    bw[k] = B.w[k];
+  }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) q[k] = B.q[k];
-    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (uint32_t c = c0 + lane; c < c1; c += 32) {
+  for (int k = 0; k < 4; ++k) q[k] = B.q[k];
+  float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (active) {  // the partials of an inactive slot are never written
+#pragma unroll 4
+    for (uint32_t c = c0 + threadIdx.x; c < c1; c += kWrenchBodyThreads) {
       const float *src = a.wpart + ((size_t)c * a.maxb + lb) * 6;
 #pragma unroll
       for (int k = 0; k < 6; ++k) v[k] += src[k];
     }
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      v[k] = active ? v[k] : 0.f;  // partials of an inactive slot are never written
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    }
-    if (lane == 0 && active && a.F) {  // free-box corners: +lambda on the box, -lambda on the other body
+  }
+  block_sum6<kWrenchBodyThreads>(v);
+  if (threadIdx.x == 0) {
+    if (active && a.F) {  // free-box corners: +lambda on the box, -lambda on the other body
       const float inv_dt = 1.0f / a.dt;
       for (uint32_t ob = 0; ob < a.maxb; ++ob) {
         const DevBody &Fb = a.bodies[e * a.maxb + ob];
@@ -1232,29 +1232,25 @@ __global__ void __launch_bounds__(256) k_wrench_bodies(StepArgs a) {
         }
       }
     }
-    if (lane == 0) {
-      float *dst = a.wrench + ((size_t)(step % a.wrench_hist) * nbt + gb) * 6;
+    float *dst = a.wrench + ((size_t)(step % a.wrench_hist) * nbt + gb) * 6;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) dst[k] = v[k];
-      if (active) {
-        advance_pose(a.dt, p, q, bv, bw);
+    for (int k = 0; k < 6; ++k) dst[k] = v[k];
+    if (active) {
+      advance_pose(a.dt, p, q, bv, bw);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) B.p[k] = p[k];
+      for (int k = 0; k < 3; ++k) B.p[k] = p[k];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) B.q[k] = q[k];
-        if (is_free) {
+      for (int k = 0; k < 4; ++k) B.q[k] = q[k];
+      if (is_free) {
 #pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            B.own_v[k] = bv[k];
-            B.own_w[k] = bw[k];
-          }
+        for (int k = 0; k < 3; ++k) {
+          B.own_v[k] = bv[k];
+          B.own_w[k] = bw[k];
         }
       }
     }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (gridDim.x == 1) {  // every warp of the only block has read the counter
+    // every thread of this block read the counter before block_sum6's barrier
+    if (gridDim.x == 1) {
       a.ctrl->step = step + 1;
     } else {
       __threadfence();
@@ -1471,7 +1467,7 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
   }
   GG_MARK(3);
   if (a.n_chunks) GG_LAUNCH(k_integrate_wrench, dim3(a.n_chunks), kIntegrateThreads, 0, a, (int)(ls.iters & 1));
-  GG_LAUNCH(k_wrench_bodies, dim3(grid_for(nbt * 32, 256)), 256, 0, a);
+  GG_LAUNCH(k_wrench_bodies, dim3(nbt), kWrenchBodyThreads, 0, a);
   GG_MARK(4);
 #undef GG_LAUNCH
 #undef GG_MARK

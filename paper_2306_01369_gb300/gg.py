@@ -42,6 +42,7 @@ SIGNATURES = {
     "gg_readback": (C.c_int, [_P, C.c_int, _P, C.c_size_t, C.c_int, _P]),
     "gg_set_state": (C.c_int, [_P, _P, C.c_size_t, C.c_int, _P]),
     "gg_tuning_count": (C.c_uint32, []),
+    "gg_hash_size": (C.c_uint32, [_P, C.c_uint32]),
     "gg_tuning_flags": (C.c_uint32, [C.c_uint32]),
     "gg_enable_timing": (C.c_int, [_P, C.c_int]),
     "gg_stage_ms": (C.c_int, [_P, C.POINTER(C.c_float)]),
@@ -63,7 +64,8 @@ class GGParams(C.Structure):
                 ("max_body_contacts", C.c_uint32), ("max_bodies", C.c_uint32), ("density", C.c_float),
                 ("tuning", C.c_uint32), ("wrench_history", C.c_uint32), ("max_free_bodies", C.c_uint32),
                 ("free_contact_capacity", C.c_uint32), ("barrier_test_phantoms", C.c_uint32),
-                ("binning", C.c_uint32), ("cyclic_z", C.c_float * 2), ("wait_limit_us", C.c_uint32)]
+                ("binning", C.c_uint32), ("cyclic_z", C.c_float * 2), ("wait_limit_us", C.c_uint32),
+                ("hash_tune", C.c_uint32)]
 
 
 class GGBody(C.Structure):
@@ -158,7 +160,7 @@ def _stream(stream):
 
 
 def make_params(p, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0, max_free_bodies=0,
-                barrier_test_phantoms=0, binning=0, wait_limit_us=0) -> GGParams:
+                barrier_test_phantoms=0, binning=0, wait_limit_us=0, hash_tune=0) -> GGParams:
     q = GGParams()
     q.struct_size = C.sizeof(GGParams)
     q.dt = p.dt
@@ -181,6 +183,7 @@ def make_params(p, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0, max_
     q.barrier_test_phantoms = barrier_test_phantoms
     q.binning = binning
     q.wait_limit_us = wait_limit_us
+    q.hash_tune = hash_tune
     cz = getattr(p, "cyclic_z", (0.0, 0.0))
     q.cyclic_z[0], q.cyclic_z[1] = cz[0], cz[1]
     return q
@@ -210,12 +213,12 @@ class Sim:
 
     def __init__(self, pos_r, vel=None, mass=None, params=None, env_offsets=None, tuning=0, wrench_history=1,
                  max_bodies=8, hash_factor=0, max_free_bodies=0, barrier_test_phantoms=0, binning=0,
-                 wait_limit_us=0):
+                 wait_limit_us=0, hash_tune=0):
         L = load()
         self._L = L
         self.params = params
         self.gp = make_params(params, tuning, wrench_history, max_bodies, hash_factor, max_free_bodies,
-                              barrier_test_phantoms, binning, wait_limit_us)
+                              barrier_test_phantoms, binning, wait_limit_us, hash_tune)
         n = int(pos_r.shape[0])
         self.n = n
         pp, dev = _ptr(pos_r)
@@ -281,12 +284,12 @@ class Sim:
 
     @classmethod
     def from_scene(cls, scene, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0, device_inputs=None,
-                   binning=0):
+                   binning=0, hash_tune=0):
         args = (scene.pos_r, scene.vel, scene.mass) if device_inputs is None else device_inputs
         n_free = sum(1 for b in scene.bodies if b.is_free)
         sim = cls(*args, params=scene.params, env_offsets=scene.env_offsets, tuning=tuning,
                   wrench_history=wrench_history, max_bodies=max_bodies, hash_factor=hash_factor,
-                  max_free_bodies=n_free, binning=binning)
+                  max_free_bodies=n_free, binning=binning, hash_tune=hash_tune)
         if scene.body_offsets is None:
             if scene.bodies:
                 sim.set_bodies(scene.bodies, 0)
@@ -338,10 +341,16 @@ class Sim:
 
     # ------------------------------------------------------------------ readback
     def field_bytes(self, field):
-        nb = self._field_bytes.get(field)   # fixed for the simulation's lifetime
+        if field == "CELL_START":   # n_h + 1 entries: changes when the autotuner picks n_h
+            return self._L.gg_field_bytes(self.h, FIELD[field])
+        nb = self._field_bytes.get(field)   # the others are fixed for the simulation's lifetime
         if nb is None:
             nb = self._field_bytes[field] = self._L.gg_field_bytes(self.h, FIELD[field])
         return nb
+
+    def hash_size(self, env=0):
+        """n_h in use for environment `env` (Eq. 6's modulus)."""
+        return self._L.gg_hash_size(self.h, env)
 
     def read(self, field, dtype=np.float32, shape=None, out=None, stream=None, check=True):
         nb = self.field_bytes(field)

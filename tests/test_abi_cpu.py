@@ -67,7 +67,7 @@ def test_tuning_sets_cover_every_variant():
 def test_struct_sizes_match_header():
     """The ctypes mirrors must have the C layout (4-byte fields and arrays)."""
     from paper_2306_01369_gb300 import gg
-    assert ctypes.sizeof(gg.GGParams) == 4 * 24
+    assert ctypes.sizeof(gg.GGParams) == 4 * 25
     assert ctypes.sizeof(gg.GGBody) == 4 * (2 + 12 + 3 + 4 + 3 + 3 + 1 + 3)
     assert ctypes.sizeof(gg.GGStats) == 8 + 4 * 6
     assert ctypes.sizeof(gg.GGCamera) == 4 * 20

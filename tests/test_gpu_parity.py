@@ -274,6 +274,36 @@ def test_autotuner_picks_a_set_and_changes_nothing(gg):
     assert ref.tuning_selected == 1
 
 
+@pytest.mark.parametrize("binning", [1, 2])
+def test_autotuned_table_size_changes_nothing_but_the_keys(gg, orc, binning):
+    """hash_tune: the autotuner also picks n_h among 2n, 4n, 8n (twice here, once at the
+    first step and once mid-run, so the tables change size between steps).  The state
+    matches a fixed 2n table bit-exactly; the keys and the bucket table are Eq. 6's
+    under the n_h in use."""
+    sc = squeezed_box(4096)
+    ref = gg.Sim.from_scene(sc, tuning=1)
+    ref.step(9)
+    auto = gg.Sim.from_scene(sc, hash_tune=1, binning=binning)
+    auto.step(5)
+    assert auto.hash_size() in (2 * sc.n, 4 * sc.n, 8 * sc.n)
+    auto.autotune()
+    auto.step(3)
+    pos_before = auto.pos()
+    auto.step(1)
+    nh = auto.hash_size()
+    assert nh in (2 * sc.n, 4 * sc.n, 8 * sc.n)
+    assert np.array_equal(auto.pos(), ref.pos()) and np.array_equal(auto.vel(), ref.vel())
+    cs = orc.default_cell_size(float(sc.pos_r[:, 3].max()))
+    keys = orc.cell_keys(pos_before[:, :3].astype(np.float64), cs, nh)
+    assert np.array_equal(auto.cell_keys(), keys)
+    assert np.array_equal(auto.sort_perm(), orc.sort_perm(keys))
+    start = np.zeros(nh + 1, np.uint32)
+    np.add.at(start, keys.astype(np.int64) + 1, 1)
+    assert np.array_equal(auto.cell_start(), np.cumsum(start).astype(np.uint32))
+    auto.close()
+    ref.close()
+
+
 def test_grid_barrier_wait_runs_out_and_reports(gg):
     """The fused sweep's grid barrier waits are bounded: with a phantom participant
     (a flag that nothing sets) every wait runs out, the step reports
