@@ -74,6 +74,7 @@ struct gg_sim {
   uint64_t steps = 0;
   void *staging = nullptr;
   size_t staging_bytes = 0;
+  DevCtrl *ctrl_host = nullptr;  // pinned mirror of the control word (status reads)
   float *vel3 = nullptr;  // n*3 staging for velocity upload / readback
   uint32_t *render_img = nullptr;  // gg_render scratch (ordered bits per pixel) and ...
   float *render_out = nullptr;     // ... device image for host destinations, ...
@@ -137,9 +138,12 @@ gg_status status_from_flags(gg_sim *s, uint32_t f) {
   return GG_OK;
 }
 
+// The control word after the work queued on `st` (one copy into pinned memory, one wait).
 gg_status read_ctrl(gg_sim *s, DevCtrl *out, cudaStream_t st) {
-  GG_CUDA(s, cudaMemcpyAsync(out, s->a.ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, st));
+  if (!s->ctrl_host) GG_CUDA(s, cudaHostAlloc(reinterpret_cast<void **>(&s->ctrl_host), sizeof(DevCtrl), 0));
+  GG_CUDA(s, cudaMemcpyAsync(s->ctrl_host, s->a.ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, st));
   GG_CUDA(s, cudaStreamSynchronize(st));
+  *out = *s->ctrl_host;
   return GG_OK;
 }
 
@@ -459,6 +463,7 @@ void gg_destroy(gg_sim *sim) {
   for (float *g : sim->grids)
     if (g) cudaFree(g);
   if (sim->staging) cudaFree(sim->staging);
+  if (sim->ctrl_host) cudaFreeHost(sim->ctrl_host);
   if (sim->render_img) cudaFree(sim->render_img);
   if (sim->render_out) cudaFree(sim->render_out);
   if (sim->render_rays) cudaFree(sim->render_rays);
