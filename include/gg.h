@@ -355,7 +355,8 @@ GG_API uint32_t gg_tuning_flags(uint32_t k);
 
 /* Time every launch-shape set gg_params.binning allows on the current state (3 steps
  * each, the state restored bit-exactly before each trial and at the end) and keep the
- * fastest.  gg_step does this once, on its first call, when gg_params.tuning = 0; call
+ * fastest; with gg_params.hash_tune, then time that set at n_h = 4n and 8n as well and
+ * keep the fastest table size.  gg_step does this once, on its first call, when gg_params.tuning = 0; call
  * it again when the workload changes character (a bed that has settled, a tool that
  * starts digging).  A no-op when gg_params.tuning fixes the set.  Waits for `stream`;
  * allocates a state copy for the duration of the call. */
