@@ -411,10 +411,13 @@ __device__ void left_jacobian(float3 phi, float J[9]) {
 
 // Sums the partials in a fixed order (thread-strided over the (sweep, block) vectors,
 // a fixed butterfly in each warp, then the warps in index order), and thread 0 runs
-// the tool pose chain of step k.
+// the tool pose chain of step k.  k is the step counter less the one saved with the
+// taped run's first checkpoint (`ctrl0`), so one captured graph serves every step.
 constexpr int kToolThreads = 256;
-__global__ void __launch_bounds__(kToolThreads) k_adj_tool(StepArgs a, AdjArgs d, uint32_t k_local) {
+__global__ void __launch_bounds__(kToolThreads) k_adj_tool(StepArgs a, AdjArgs d, const DevCtrl *ctrl0,
+                                                          uint32_t n_taped) {
   pdl_enter();
+  const uint32_t k_local = a.ctrl->step - ctrl0->step;
   double v[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = 0.0;
@@ -446,7 +449,7 @@ __global__ void __launch_bounds__(kToolThreads) k_adj_tool(StepArgs a, AdjArgs d
     v[q] = t;
   }
   d.mubar[0] += v[9];
-  if (d.tool == 0xffffffffu) return;
+  if (d.tool == 0xffffffffu || k_local >= n_taped) return;
   const DevBody &B = a.bodies[d.tool];
   const float3 W = make_float3(B.w[0], B.w[1], B.w[2]);
   const float3 pb1 = make_float3(d.pose_bar[0], d.pose_bar[1], d.pose_bar[2]);
@@ -480,7 +483,8 @@ uint32_t adjoint_blocks(uint32_t n) { return blocks(n); }
 
 // The step's adjoint kernels, chained with programmatic dependent launch (every one
 // begins with pdl_enter); the first follows the taped forward's last sweep.
-cudaError_t enqueue_adjoint_step(const StepArgs &a, const AdjArgs &d, uint32_t k_local, cudaStream_t st) {
+cudaError_t enqueue_adjoint_step(const StepArgs &a, const AdjArgs &d, const DevCtrl *ctrl0, uint32_t n_taped,
+                                 cudaStream_t st) {
   const dim3 g(blocks(a.n));
   cudaError_t e;
   if (a.n) {
@@ -493,7 +497,7 @@ cudaError_t enqueue_adjoint_step(const StepArgs &a, const AdjArgs &d, uint32_t k
     cur ^= 1;
   }
   if ((e = launch(true, k_adj_geom, g, kAdjThreads, 0, st, a, d, cur)) != cudaSuccess) return e;
-  return launch(true, k_adj_tool, dim3(1), kToolThreads, 0, st, a, d, k_local);
+  return launch(true, k_adj_tool, dim3(1), kToolThreads, 0, st, a, d, ctrl0, n_taped);
 }
 
 }  // namespace gg

@@ -1210,6 +1210,32 @@ gg_status gg_backward(gg_sim *s, const float *dL_dpos, const float *dL_dvel, con
     gg_status rc = capture(s);
     if (rc != GG_OK) return rc;
   }
+  // one step of the reverse pass (the taped forward of the step, then its adjoint) as
+  // a graph: the work does not depend on the step index (the adjoint reads it from the
+  // step counter restored with the state), so it is captured once per call
+  cudaGraphExec_t bexec = nullptr;
+  {
+    const gg::DevCtrl *ctrl0 = reinterpret_cast<const gg::DevCtrl *>(
+        s->ad.ckpt + (size_t)n * 32 + (size_t)s->n_envs * s->maxb * sizeof(DevBody));
+    GG_CUDA(s, cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = gg::enqueue_step(s->a, s->ls, s->cap, nullptr, &s->ad.tp);
+    if (e1 == cudaSuccess) e1 = gg::enqueue_adjoint_step(s->a, d, ctrl0, N, s->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
+    if (e1 == cudaSuccess && e2 == cudaSuccess) e1 = cudaGraphInstantiate(&bexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return cuda_fail(s, e1 != cudaSuccess ? e1 : e2, "capturing the reverse step");
+  }
+  struct ExecGuard {  // the graph is destroyed on every return below, after its launches
+    cudaGraphExec_t *x;
+    cudaStream_t st;
+    ~ExecGuard() {
+      if (*x) {
+        cudaStreamSynchronize(st);
+        cudaGraphExecDestroy(*x);
+      }
+    }
+  } guard{&bexec, st};
   const uint32_t nseg = (N + K - 1) / K;
   for (int seg = (int)nseg - 1; seg >= 0; --seg) {
     const uint32_t k0 = (uint32_t)seg * K, k1 = std::min(k0 + K, N);
@@ -1219,12 +1245,12 @@ gg_status gg_backward(gg_sim *s, const float *dL_dpos, const float *dL_dvel, con
       if ((rc = save_state(s, s->ad.seg + (size_t)(k - k0) * s->ad.state_bytes, st)) != GG_OK) return rc;
       if (k + 1 < k1) GG_CUDA(s, cudaGraphLaunch(s->exec[s->timing], st));
     }
-    for (int k = (int)k1 - 1; k >= (int)k0; --k) {  // reverse the steps
+    for (int k = (int)k1 - 1; k >= (int)k0; --k) {  // reverse the steps: taped forward + adjoint
       if ((rc = restore_state(s, s->ad.seg + (size_t)(k - k0) * s->ad.state_bytes, st)) != GG_OK) return rc;
-      GG_CUDA(s, gg::enqueue_step(s->a, s->ls, st, nullptr, &s->ad.tp));
-      GG_CUDA(s, gg::enqueue_adjoint_step(s->a, d, (uint32_t)k, st));
+      GG_CUDA(s, cudaGraphLaunch(bexec, st));
     }
   }
+
   gg_status rc = restore_state(s, s->ad.fin, st);
   if (rc != GG_OK) return rc;
   GG_CUDA(s, cudaMemcpyAsync(dL_dtwist, d.dtwist, sizeof(float) * 6 * N, x2h, st));

@@ -49,7 +49,11 @@ uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls);
 // the step bins by linked lists)
 cudaError_t enqueue_sort_from_keys(const StepArgs &a, cudaStream_t st);
 // reverse of one taped step (after enqueue_step with a tape, which stops after the sweeps)
-cudaError_t enqueue_adjoint_step(const StepArgs &a, const AdjArgs &d, uint32_t k_local, cudaStream_t st);
+// The adjoint of one step (after that step's taped forward); the step index is the
+// device step counter less ctrl0->step (the counter saved with the taped run's first
+// checkpoint), so the enqueued work does not depend on it.
+cudaError_t enqueue_adjoint_step(const StepArgs &a, const AdjArgs &d, const DevCtrl *ctrl0, uint32_t n_taped,
+                                 cudaStream_t st);
 uint32_t adjoint_blocks(uint32_t n);
 // Depth observation (gg_render): everything the kernels need, precomputed on the host.
 struct RenderArgs {
