@@ -207,7 +207,8 @@ __device__ __forceinline__ float4 complete_ubar(const StepArgs &a, const AdjArgs
                                                 const float *ub) {
   const size_t n = a.n, KN = (size_t)a.K * n;
   const uint32_t npp = a.ccount[i] & 0xffu;
-  for (uint32_t c = 0; c < npp; ++c) {
+#pragma unroll 4
+  for (uint32_t c = 0; c < npp; ++c) {  // loads only: four contacts' gathers in flight
     const size_t o = (size_t)c * n + i;
     const size_t ot = (size_t)d.twin[o] * n + a.cj[o];
     U.x -= ub[ot];
@@ -239,24 +240,41 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_iter(StepArgs a, AdjArgs d,
     const uint32_t npp = cc & 0xffu, nbc = (cc >> 8) & 0xffu;
     float3 S = make_float3(0.f, 0.f, 0.f);
     float mub = 0.f;
-    for (uint32_t c = 0; c < npp; ++c) {
-      const size_t o = (size_t)c * n + i;
-      const uint32_t j = a.cj[o];
-      const float4 nn = a.cn[o];
+    // Reverse of one contact update, from its loaded inputs; stores its adjoints.
+    const float4 *Uh = d.tp.Uh + (size_t)s * n;
+    auto contact = [&](size_t o, float4 nn, float3 lam, float3 Lb, float psb, float3 nbo, float4 Uj) {
       const float3 nv = f3(nn);
-      const float4 Uj = d.tp.Uh[(size_t)s * n + j];
       const float w = 1.0f / (Ui.w + Uj.w);
       const float bias = a.ab * nn.w;
-      const float3 z = pja_pre(ld3(lh, o, KN), make_float3(Ui.x - Uj.x, Ui.y - Uj.y, Ui.z - Uj.z), nv, bias, w);
-      const float3 abar = add(mul(invm, f3(Un)), ld3(d.Lbar, o, KN));
+      const float3 z = pja_pre(lam, make_float3(Ui.x - Uj.x, Ui.y - Uj.y, Ui.z - Uj.z), nv, bias, w);
+      const float3 abar = add(mul(invm, f3(Un)), Lb);
       float3 nb = make_float3(0.f, 0.f, 0.f);
       const float3 zb = cone_adjoint(z, nv, a.mu, abar, &nb, &mub);
       st3(d.Lbar, o, KN, zb);
       const float3 ub = mul(-w, zb);
       st3(ubar, o, KN, ub);
       S = add(S, ub);
-      d.psibar[o] += w * a.ab * dot(nv, zb);
-      acc3(d.nbar, o, KN, add(mul(w * bias, zb), nb));
+      d.psibar[o] = psb + w * a.ab * dot(nv, zb);
+      st3(d.nbar, o, KN, add(nbo, add(mul(w * bias, zb), nb)));
+    };
+    // two contacts per round: both contacts' loads are issued before either's stores
+    uint32_t c = 0;
+    for (; c + 1 < npp; c += 2) {
+      const size_t o0 = (size_t)c * n + i, o1 = o0 + n;
+      const uint32_t j0 = a.cj[o0], j1 = a.cj[o1];
+      const float4 nn0 = a.cn[o0], nn1 = a.cn[o1];
+      const float3 lm0 = ld3(lh, o0, KN), lm1 = ld3(lh, o1, KN);
+      const float3 Lb0 = ld3(d.Lbar, o0, KN), Lb1 = ld3(d.Lbar, o1, KN);
+      const float ps0 = d.psibar[o0], ps1 = d.psibar[o1];
+      const float3 nb0 = ld3(d.nbar, o0, KN), nb1 = ld3(d.nbar, o1, KN);
+      const float4 Uj0 = Uh[j0], Uj1 = Uh[j1];
+      contact(o0, nn0, lm0, Lb0, ps0, nb0, Uj0);
+      contact(o1, nn1, lm1, Lb1, ps1, nb1, Uj1);
+    }
+    if (c < npp) {
+      const size_t o = (size_t)c * n + i;
+      const uint32_t j = a.cj[o];
+      contact(o, a.cn[o], ld3(lh, o, KN), ld3(d.Lbar, o, KN), d.psibar[o], ld3(d.nbar, o, KN), Uh[j]);
     }
     for (uint32_t c = 0; c < nbc; ++c) {
       const size_t o = (size_t)c * n + i;
@@ -409,45 +427,53 @@ __device__ void left_jacobian(float3 phi, float J[9]) {
     }
 }
 
-// Sums the partials in a fixed order (thread-strided over the (sweep, block) vectors,
-// a fixed butterfly in each warp, then the warps in index order), and thread 0 runs
-// the tool pose chain of step k.  k is the step counter less the one saved with the
-// taped run's first checkpoint (`ctrl0`), so one captured graph serves every step.
-constexpr int kToolThreads = 256;
+// Sums the partials in a fixed order (thread-strided over the (sweep, block) vectors in
+// float, a fixed butterfly in each warp, then the warps in index order in double), and
+// thread 0 runs the tool pose chain of step k.  k is the step counter less the one saved
+// with the taped run's first checkpoint (`ctrl0`), so one captured graph serves every
+// step.  (Double accumulation per thread cost 29 us per step on GB300's FP64 rate.)
+constexpr int kToolThreads = 512;
 __global__ void __launch_bounds__(kToolThreads) k_adj_tool(StepArgs a, AdjArgs d, const DevCtrl *ctrl0,
                                                           uint32_t n_taped) {
   pdl_enter();
   const uint32_t k_local = a.ctrl->step - ctrl0->step;
-  double v[16];
+  float f[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = 0.0;
+  for (int q = 0; q < 16; ++q) f[q] = 0.f;
   const uint32_t I = d.I, nb = d.nblk;
+#pragma unroll 2
   for (uint32_t t = threadIdx.x; t < I * nb; t += kToolThreads) {  // t = s * nblk + b
     const float *p = d.part + (size_t)t * kPart;
 #pragma unroll
-    for (int q = 0; q < kPart; ++q) v[q] += p[q];
+    for (int q = 0; q < kPart; ++q) f[q] += p[q];
   }
   for (uint32_t b = threadIdx.x; b < nb; b += kToolThreads) {
     const float *g = d.part + ((size_t)I * nb + b) * kPart;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) v[10 + q] += g[q];
+    for (int q = 0; q < 6; ++q) f[10 + q] += g[q];
   }
 #pragma unroll
   for (int q = 0; q < 16; ++q)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-  __shared__ double sm[kToolThreads / 32][16];
+    for (int o = 16; o > 0; o >>= 1) f[q] += __shfl_xor_sync(0xffffffffu, f[q], o);
+  __shared__ float sm[kToolThreads / 32][16];
+  __shared__ double tot[16];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0)
 #pragma unroll
-    for (int q = 0; q < 16; ++q) sm[wid][q] = v[q];
+    for (int q = 0; q < 16; ++q) sm[wid][q] = f[q];
+  __syncthreads();
+  if (threadIdx.x < 16) {  // one component per thread, warps in index order
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kToolThreads / 32; ++w) t += (double)sm[w][threadIdx.x];
+    tot[threadIdx.x] = t;
+  }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  for (int q = 0; q < 16; ++q) {
-    double t = sm[0][q];
-    for (int w = 1; w < kToolThreads / 32; ++w) t += sm[w][q];
-    v[q] = t;
-  }
+  double v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = tot[q];
   d.mubar[0] += v[9];
   if (d.tool == 0xffffffffu || k_local >= n_taped) return;
   const DevBody &B = a.bodies[d.tool];
