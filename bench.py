@@ -13,8 +13,11 @@ stream the library launches on, with an L2 flush (a 512 MiB write) between timed
 steps, outside the events.  The dominant kernel (the PJA sweep) is timed by
 events recorded inside the step graph.  Multi-GPU: one process per GPU
 (torchrun); each rank steps its own replica of the column (the single-scene
-path does not shard), barrier + max over ranks.  `--impl reference` times the
-FP64 CPU oracle on a bounded sample of the same workload.
+path does not shard), barrier + max over ranks.  End to end ("e2e"): a second
+simulation set up the same way steps over the same window through the public API
+with host buffers (positions and velocities copied in from pinned memory, stepped,
+copied back, every step).  `--impl reference` times the FP64 CPU oracle on a bounded
+sample of the same workload.
 """
 from __future__ import annotations
 
@@ -648,8 +651,13 @@ def run_gpu(args):
     roof_main, roof_other = roofs
 
     # end to end through the public API with host buffers: H2D of the state, one
-    # step, D2H of the new state, every step
-    e2e_steps = min(args.steps, args.e2e_steps)
+    # step, D2H of the new state, every step; on the same window of the workload as the
+    # timed steps (a second simulation set up the same way, from the same inputs)
+    tuning_sel, nh0, kps = sim.tuning_selected, sim.hash_size(0), sim.kernels_per_step
+    sim.close()
+    e2e_steps = min(args.steps, args.e2e_steps or args.steps)
+    _, sim, _ = setup_workload(args, scenes, gg, rank, stream)
+    sim.step(max(args.warmup, 2), stream=stream)
     state_h = torch.empty(7 * sc.n, dtype=torch.float32).pin_memory()   # positions (n, 4), velocities (n, 3)
     sim.read("POS_VEL", out=state_h, stream=stream)
     pos_h, vel_h = state_h[:4 * sc.n].view(sc.n, 4), state_h[4 * sc.n:].view(sc.n, 3)
@@ -676,14 +684,14 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {**workload_config(sc, args.workload), "replicas": world, "tuning_set": sim.tuning_selected,
-                           "hash_table": f"n_h = {sim.hash_size(0) / n_env0:.0f} n per environment "
+                "config": {**workload_config(sc, args.workload), "replicas": world, "tuning_set": tuning_sel,
+                           "hash_table": f"n_h = {nh0 / n_env0:.0f} n per environment "
                                          f"({'fixed' if args.hash_factor else 'autotuned among 2n, 4n, 8n'})",
                            "timed_steps": window},
                 "roofline": roof_main, "roofline_next": roof_other, "cpu_baseline": cpu,
-                "e2e": {"value": e2e_val, "unit": UNIT, "steps": e2e_steps,
+                "e2e": {"value": e2e_val, "unit": UNIT, "steps": e2e_steps, "window": [window[0], window[0] + e2e_steps],
                         "h2d_bytes_per_step": sc.n * (16 + 12), "d2h_bytes_per_step": sc.n * (16 + 12)},
-                "gpu_launches": sim.kernels_per_step * args.steps, "clocks": clk,
+                "gpu_launches": kps * args.steps, "clocks": clk,
                 "stage_ms_last_sampled_step": st,
                 "contacts_last_step": {"n_pp": stats["n_pp"], "n_body": stats["n_body"],
                                        "mean_pp_per_particle": stats["n_pp"] / sc.n},
@@ -705,7 +713,8 @@ def main(argv=None):
     ap.add_argument("--tuning", type=int, default=0)
     ap.add_argument("--hash-factor", type=int, default=0,
                     help="fixed n_h = F n per environment (2: the paper's); 0: the autotuner picks 2n, 4n or 8n")
-    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="end-to-end steps (0: as many as the timed steps, over the same window)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / adjoint / excavation figures")
