@@ -513,6 +513,22 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
                          "contacts_us": 1e3 * stg["contacts"]}
         out["ablations"] = {"workload": "column collapse 262,144, steps 1000-1100; stage times from one "
                                         "instrumented step after the timed ones", "configs": abl}
+        # the hash-table-size experiment at the sizes of Fig. hashtable-benchmark: columns
+        # of 1k-65k spheres after 1,000 steps, step time at n_h = 1n .. 8n, both binnings
+        curve = {}
+        for nc in (1024, 4096, 16384, 65536):
+            colc = scenes.column_collapse(n=nc)
+            for name, tuning in (("sort", 1), ("lists", 7)):
+                row = {}
+                for hf in (1, 2, 4, 8):
+                    sim = gg.Sim.from_scene(colc, tuning=tuning, hash_factor=hf)
+                    sim.step(1000, stream=stream)
+                    row[f"nh{hf}n"] = _timed_steps(sim, 200, stream, torch) / 200
+                    sim.close()
+                curve[f"{name}_n{nc}"] = {"ms_per_step": row,
+                                          "speedup_vs_2n": {k: row["nh2n"] / v for k, v in row.items()}}
+        out["hashtable_sizes"] = {"workload": "columns of 1,024-65,536 spheres (same recipe), steps 1000-1200, "
+                                               "fixed launch shapes (sets 1 and 7)", "configs": curve}
     # excavation: 1,048,576 spheres, scoop, two free cubes, I = 30
     if time.perf_counter() - t_start < seconds_cap:
         ex = scenes.excavation(n=1048576, n_steps=steps_exc + 20)
