@@ -61,7 +61,8 @@ typedef enum {
   GG_ERR_UNSUPPORTED = 7,       /* valid request the library does not implement */
   GG_ERR_NO_DEVICE = 8,         /* no usable CUDA device */
   GG_ERR_INTERNAL = 9           /* a device-side invariant failed (a bucket list walk longer
-                                   than the particle count); the walk was cut short */
+                                   than the particle count, or, in a library built with
+                                   -DGG_DEBUG, an index check); the access was skipped */
 } gg_status;
 
 /* Rigid-body geometry as signed distance functions (Sec. II-C): closed forms, or

@@ -210,7 +210,9 @@ __device__ __forceinline__ float4 complete_ubar(const StepArgs &a, const AdjArgs
 #pragma unroll 4
   for (uint32_t c = 0; c < npp; ++c) {  // loads only: four contacts' gathers in flight
     const size_t o = (size_t)c * n + i;
-    const size_t ot = (size_t)d.twin[o] * n + a.cj[o];
+    const uint32_t tw = d.twin[o], jt = a.cj[o];
+    if (!GG_GUARD(a.ctrl, tw < a.K && jt < a.n)) continue;
+    const size_t ot = (size_t)tw * n + jt;
     U.x -= ub[ot];
     U.y -= ub[ot + KN];
     U.z -= ub[ot + 2 * KN];
@@ -261,7 +263,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_iter(StepArgs a, AdjArgs d,
     uint32_t c = 0;
     for (; c + 1 < npp; c += 2) {
       const size_t o0 = (size_t)c * n + i, o1 = o0 + n;
-      const uint32_t j0 = a.cj[o0], j1 = a.cj[o1];
+      uint32_t j0 = a.cj[o0], j1 = a.cj[o1];
+      if (!GG_GUARD(a.ctrl, j0 < a.n && j1 < a.n)) j0 = j1 = i;
       const float4 nn0 = a.cn[o0], nn1 = a.cn[o1];
       const float3 lm0 = ld3(lh, o0, KN), lm1 = ld3(lh, o1, KN);
       const float3 Lb0 = ld3(d.Lbar, o0, KN), Lb1 = ld3(d.Lbar, o1, KN);
@@ -273,7 +276,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_iter(StepArgs a, AdjArgs d,
     }
     if (c < npp) {
       const size_t o = (size_t)c * n + i;
-      const uint32_t j = a.cj[o];
+      uint32_t j = a.cj[o];
+      if (!GG_GUARD(a.ctrl, j < a.n)) j = i;
       contact(o, a.cn[o], ld3(lh, o, KN), ld3(d.Lbar, o, KN), d.psibar[o], ld3(d.nbar, o, KN), Uh[j]);
     }
     for (uint32_t c = 0; c < nbc; ++c) {

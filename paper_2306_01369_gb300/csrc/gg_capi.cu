@@ -132,6 +132,8 @@ gg_status status_from_flags(gg_sim *s, uint32_t f) {
   if (f & gg::kFlagTimeout) return fail(s, GG_ERR_DEVICE_TIMEOUT, "a grid barrier wait gave up (bounded wait)");
   if (f & gg::kFlagListBound)
     return fail(s, GG_ERR_INTERNAL, "a bucket list walk passed the particle count (cut short)");
+  if (f & gg::kFlagDebugCheck)
+    return fail(s, GG_ERR_INTERNAL, "a device-side index check of the GG_DEBUG build failed (access skipped)");
   if (f & gg::kFlagNonFinite) return fail(s, GG_ERR_NONFINITE, "a particle position or velocity became non-finite");
   if (f & (gg::kFlagPPOverflow | gg::kFlagBodyOverflow))
     return fail(s, GG_ERR_CONTACT_OVERFLOW, "a particle exceeded its contact capacity (flags " + std::to_string(f) + ")");

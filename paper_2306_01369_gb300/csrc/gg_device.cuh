@@ -20,6 +20,7 @@ constexpr uint32_t kFlagBodyOverflow = 2u;
 constexpr uint32_t kFlagNonFinite = 4u;
 constexpr uint32_t kFlagTimeout = 8u;    // a bounded device-side wait gave up
 constexpr uint32_t kFlagListBound = 16u; // a bucket list walk passed n entries (lists not emptied)
+constexpr uint32_t kFlagDebugCheck = 32u; // an index check of the GG_DEBUG build failed
 
 constexpr uint32_t kListEnd = 0xffffffffu;  // end of a bucket's linked list
 constexpr int kMaxK = 32;   // particle-particle capacity limit
@@ -96,6 +97,21 @@ struct DevCtrl {
   uint32_t bar_extra;     // phantom arrivals a barrier waits for (0; tests set it to force a timeout)
   uint32_t blocks_done;     // k_wrench_bodies: blocks finished this step (0 between steps)
 };
+
+// Index checks of the debug build (-DGG_DEBUG): GG_GUARD(ctrl, cond) is `cond`, and a
+// false `cond` also latches kFlagDebugCheck (the step then reports GG_ERR_INTERNAL);
+// callers skip the access it guards.  In the release build it is `true` and costs
+// nothing.  (compute-sanitizer is not available to this build's tests; these checks
+// and the invariance tests stand in for it.)
+#ifdef GG_DEBUG
+__device__ __forceinline__ bool gg_guard(DevCtrl *c, bool ok) {
+  if (!ok) atomicOr(&c->status, kFlagDebugCheck);
+  return ok;
+}
+#define GG_GUARD(ctrl, cond) ::gg::gg_guard((ctrl), (cond))
+#else
+#define GG_GUARD(ctrl, cond) true
+#endif
 
 // Everything a step's kernels read or write; passed by value to each kernel.
 struct StepArgs {

@@ -124,6 +124,7 @@ __global__ void k_key(StepArgs a) {
     int32_t k0 = cell_of(p.x, E.inv_cell), k1 = cell_of(p.y, E.inv_cell), k2 = cell_of(p.z, E.inv_cell);
     uint32_t key = E.hbase + hash_cell_fm(k0, k1, k2, E);
     a.key_id[i] = key;
+    if (!GG_GUARD(a.ctrl, key - E.hbase < E.nh && key < a.nh_total)) return;
     if (a.lists)
       a.next[i] = atomicExch(&a.head[key], i);  // lock-free push onto the bucket's list (Alg. 2)
     else
@@ -535,10 +536,12 @@ __global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
         bool any = false;
 #pragma unroll
         for (int q = 0; q < kWalkGroup; ++q)
-          if (jn[q] != kListEnd) {
+          if (jn[q] != kListEnd && GG_GUARD(a.ctrl, jn[q] < a.n)) {
             any = true;
             pc[q] = a.pos_id[jn[q]];
             nx[q] = a.next[jn[q]];
+          } else {
+            jn[q] = kListEnd;
           }
         if (!any) break;
         if (round >= a.n) {
@@ -644,10 +647,12 @@ __global__ void __launch_bounds__(kContactsBlock, 9) k_pairs_half(StepArgs a) {
         bool any = false;
 #pragma unroll
         for (int q = 0; q < kWalkGroup; ++q)
-          if (jn[q] != kListEnd) {
+          if (jn[q] != kListEnd && GG_GUARD(a.ctrl, jn[q] < a.n)) {
             any = true;
             pc[q] = a.pos_id[jn[q]];
             nx[q] = a.next[jn[q]];
+          } else {
+            jn[q] = kListEnd;
           }
         if (!any) break;
         if (round >= a.n) {
@@ -728,8 +733,14 @@ __global__ void __launch_bounds__(kContactsBlock) k_pairs_finish(StepArgs a) {
     const uint32_t cnt = a.pcnt[i];
     const uint32_t nfw = cnt >> 16, nbw = cnt & 0xffffu;
     bool ovf = nfw > K || nbw > K;  // entries were lost: the list may be incomplete
-    for (uint32_t p = 0; p < min(nfw, K); ++p) insert_partner(fid, S, K, a.pscr[(size_t)p * a.n + i], npp, ovf);
-    for (uint32_t p = 0; p < min(nbw, K); ++p) insert_partner(fid, S, K, a.pscr[(size_t)(K + p) * a.n + i], npp, ovf);
+    for (uint32_t p = 0; p < min(nfw, K); ++p) {
+      const uint32_t j = a.pscr[(size_t)p * a.n + i];
+      if (GG_GUARD(a.ctrl, j < a.n && j != i)) insert_partner(fid, S, K, j, npp, ovf);
+    }
+    for (uint32_t p = 0; p < min(nbw, K); ++p) {
+      const uint32_t j = a.pscr[(size_t)(K + p) * a.n + i];
+      if (GG_GUARD(a.ctrl, j < a.n && j != i)) insert_partner(fid, S, K, j, npp, ovf);
+    }
     a.pcnt[i] = 0;  // ready for the next step
     contact_records(a, i, pi, e, E, fid, S, K, npp, ovf, nbc, psi_max);
   }
@@ -763,7 +774,8 @@ __device__ __forceinline__ void pja_particle(const StepArgs &a, uint32_t i, int 
   uint32_t c = 0;
   for (; c + 1 < npp; c += 2) {
     const size_t o0 = (size_t)c * n + i, o1 = o0 + n;
-    const uint32_t j0 = cj[o0], j1 = cj[o1];
+    uint32_t j0 = cj[o0], j1 = cj[o1];
+    if (!GG_GUARD(a.ctrl, j0 < a.n && j1 < a.n)) j0 = j1 = i;  // debug build: never gather out of range
     const float4 n0 = cn[o0], n1 = cn[o1];
     const float3 la0 = make_float3(clam[o0], clam[o0 + KN], clam[o0 + 2 * KN]);
     const float3 la1 = make_float3(clam[o1], clam[o1 + KN], clam[o1 + 2 * KN]);
@@ -797,7 +809,8 @@ __device__ __forceinline__ void pja_particle(const StepArgs &a, uint32_t i, int 
   }
   if (c < npp) {
     const size_t o = (size_t)c * n + i;
-    const uint32_t j = cj[o];
+    uint32_t j = cj[o];
+    if (!GG_GUARD(a.ctrl, j < a.n)) j = i;
     const float4 nn = cn[o];
     const float4 uj = LDCG ? __ldcg(Uin + j) : Uin[j];
     const float3 lam = make_float3(clam[o], clam[o + KN], clam[o + 2 * KN]);
@@ -819,7 +832,9 @@ __device__ __forceinline__ void pja_particle(const StepArgs &a, uint32_t i, int 
   const size_t KbN = (size_t)a.Kb * n;
   for (uint32_t c = 0; c < nbc; ++c) {
     const size_t o = (size_t)c * n + i;
-    const DevBody &B = a.bodies[a.bj[o]];
+    const uint32_t gbo = a.bj[o];
+    if (!GG_GUARD(a.ctrl, gbo < a.n_envs * a.maxb)) continue;
+    const DevBody &B = a.bodies[gbo];
     const float4 nn = a.bn[o];
     const float4 xc = a.bxc[o];
     const float3 lam = make_float3(a.blam[o], a.blam[o + KbN], a.blam[o + 2 * KbN]);
@@ -833,7 +848,7 @@ __device__ __forceinline__ void pja_particle(const StepArgs &a, uint32_t i, int 
       const float t0 = B.R[0] * cx + B.R[3] * cy + B.R[6] * cz;
       const float t1 = B.R[1] * cx + B.R[4] * cy + B.R[7] * cz;
       const float t2 = B.R[2] * cx + B.R[5] * cy + B.R[8] * cz;
-      invb = (float)a.ncb[a.bj[o]] * (1.0f / B.mass + t0 * t0 / B.inertia[0] + t1 * t1 / B.inertia[1] +
+      invb = (float)a.ncb[gbo] * (1.0f / B.mass + t0 * t0 / B.inertia[0] + t1 * t1 / B.inertia[1] +
                                       t2 * t2 / B.inertia[2]);
     }
     const float w = 1.0f / (ui.w + invb);

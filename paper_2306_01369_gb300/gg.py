@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libgg.so")
+# GG_DEBUG=1 in the environment loads the checked build (libgg_debug.so: device-side
+# index checks that report GG_ERR_INTERNAL instead of touching memory out of range)
+LIB_PATH = os.path.join(_PKG, "libgg_debug.so" if os.environ.get("GG_DEBUG") == "1" else "libgg.so")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_CONTACT_OVERFLOW, ERR_DEVICE_TIMEOUT, ERR_NONFINITE, \
     ERR_UNSUPPORTED, ERR_NO_DEVICE = range(9)
