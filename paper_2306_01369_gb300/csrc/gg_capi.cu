@@ -1190,12 +1190,10 @@ gg_status gg_backward(gg_sim *s, const float *dL_dpos, const float *dL_dvel, con
     float g7[7];
     GG_CUDA(s, cudaMemcpyAsync(g7, dL_dpose, sizeof(g7), h2x == cudaMemcpyHostToDevice ? cudaMemcpyHostToHost
                                                                                      : cudaMemcpyDeviceToHost, st));
-    DevBody tb;
-    const size_t nbt = (size_t)s->n_envs * s->maxb;
+    DevBody tb;  // the tool's final pose, from the final state (bodies follow the 32 n bytes of particles)
     GG_CUDA(s, cudaMemcpyAsync(&tb, s->ad.fin + (size_t)n * 32 + (size_t)s->ad.tool * sizeof(DevBody), sizeof(DevBody),
                                cudaMemcpyDeviceToHost, st));
     GG_CUDA(s, cudaStreamSynchronize(st));
-    (void)nbt;
     const float w = tb.q[0], x = tb.q[1], y = tb.q[2], z = tb.q[3];
     const float *gq = g7 + 3;
     pose6[0] = g7[0];
