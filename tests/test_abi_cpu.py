@@ -81,3 +81,16 @@ def test_create_rejects_bad_params_before_touching_a_device(lib):
     h = ctypes.c_void_p()
     assert lib.gg_create(ctypes.byref(p), 0, None, None, None, 0, ctypes.byref(h)) == gg.ERR_INVALID_ARG
     assert lib.gg_create(None, 0, None, None, None, 0, ctypes.byref(h)) == gg.ERR_INVALID_ARG
+
+
+def test_checked_build_exports_the_same_symbols():
+    """libgg_debug.so (-DGG_DEBUG, device-side index checks) builds without a GPU and
+    exports exactly the release library's ABI."""
+    import subprocess
+    from paper_2306_01369_gb300 import _build
+
+    def exported(path):
+        out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+        return {l.split()[-1] for l in out.splitlines() if " T " in l}
+
+    assert exported(_build.build(debug=True)) == exported(_build.build()) == set(_declared())

@@ -1,0 +1,33 @@
+"""Host logic of bench.py that needs no GPU: the kernels a launch-shape set runs, the
+profile lookup (digest match), the algorithmic byte counts, the hash-table option."""
+import argparse
+
+import bench
+
+
+def test_stage_kernels_follow_the_tuning_flags():
+    assert bench.stage_kernels(set()) == ("k_pja", "k_contacts")
+    assert bench.stage_kernels({"lists", "half"}) == ("k_pja", "k_pairs_half+k_pairs_finish")
+    assert bench.stage_kernels({"lean"})[0] == "k_pja_lean"
+    assert bench.stage_kernels({"fused"})[0] == "k_pja_fused"
+
+
+def test_profile_traffic_needs_the_current_digest(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "k_pja_column_collapse.txt").write_text("# c\nkernel_digest: abc\ndram_bytes_per_launch: 1234\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profile_traffic("k_pja", "column", "abc") == 1234.0
+    assert bench.profile_traffic("k_pja", "column", "other") is None
+    assert bench.profile_traffic("k_pja", "excavation", "abc") is None   # no such file
+
+
+def test_algorithmic_bytes():
+    assert bench.pja_bytes(10, 0, 0) == 520
+    assert bench.pja_bytes(0, 1, 1) == 44 + 60
+    assert bench.contacts_bytes(10, 2, 1, 20) == 600 + 80 + 64 + 48
+
+
+def test_hash_option():
+    assert bench.hash_kw(argparse.Namespace(hash_factor=0)) == {"hash_tune": 1}
+    assert bench.hash_kw(argparse.Namespace(hash_factor=2)) == {"hash_factor": 2}
