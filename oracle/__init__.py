@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
 class OrcParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("gravity", C.c_double * 3), ("mu", C.c_double), ("alpha", C.c_double),
                 ("pja_iters", C.c_int32), ("n_threads", C.c_int32), ("cell_size", C.c_float),
-                ("hash_size", C.c_uint32), ("cyclic_z", C.c_double * 2)]
+                ("hash_size", C.c_uint32), ("cyclic_z", C.c_double * 2), ("pja_weight", C.c_int32)]
 
 
 class OrcBody(C.Structure):
@@ -126,6 +126,7 @@ def make_params(params, n: int, r_max: float, n_threads: int = 1) -> OrcParams:
     p.hash_size = params.hash_size if params.hash_size > 0 else max(1, 2 * n)
     cz = getattr(params, "cyclic_z", (0.0, 0.0))
     p.cyclic_z[0], p.cyclic_z[1] = _f32(cz[0]), _f32(cz[1])
+    p.pja_weight = int(getattr(params, "pja_weight", 0))
     return p
 
 
@@ -276,6 +277,8 @@ class Sim:
                             _p(self.r, C.c_double), _p(self.m, C.c_double), self.nb, self.bodies,
                             _p(tw, C.c_double), _p(self.wrench, C.c_double), _p(pp_lam, C.c_double),
                             _p(bc_lam, C.c_double), C.byref(self.stats))
+            if rc == -2:
+                raise RuntimeError("oracle step: pja_weight = 1 (Alg. 1 as printed) with a free body")
             if rc != 0:
                 raise RuntimeError("oracle step failed (contact overflow)")
             self.step_index += 1

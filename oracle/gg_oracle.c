@@ -855,6 +855,9 @@ static void quat_integrate(double *q, const double *w, double dt) {
 int orc_step(const orc_params *p, uint32_t n, double *x, double *v, const double *r, const double *m,
              uint32_t nb, orc_body *bodies, const double *twist, double *wrench, double *pp_lam,
              double *bc_lam, orc_stats *st) {
+  if (p->pja_weight)
+    for (uint32_t b = 0; b < nb; ++b)
+      if (bodies[b].is_free) return -2;
   contacts C;
   if (build_contacts(p, n, x, r, nb, bodies, 0, &C) != 0) {
     contacts_free(&C);
@@ -908,7 +911,8 @@ int orc_step(const orc_params *p, uint32_t n, double *x, double *v, const double
         uint32_t j = C.pp_j[c];
         double u[3];
         for (int k = 0; k < 3; ++k) u[k] = U[3 * i + k] - U[3 * j + k];
-        double w = 1.0 / (nci[i] + nci[j]);
+        /* mass splitting; or Alg. 1 as printed, where i takes the whole correction */
+        double w = p->pja_weight ? m[i] : 1.0 / (nci[i] + nci[j]);
         pja_update(lp + 3 * c, u, C.pp_n + 3 * c, ab * C.pp_psi[c], w, mu);
         for (int k = 0; k < 3; ++k) S[k] += lp[3 * c + k];
       }
@@ -917,7 +921,7 @@ int orc_step(const orc_params *p, uint32_t n, double *x, double *v, const double
         double ub[3], u[3];
         point_vel(Vb + 6 * b, Vb + 6 * b + 3, bodies[b].pos, C.bc_xc + 3 * c, ub);
         for (int k = 0; k < 3; ++k) u[k] = U[3 * i + k] - ub[k];
-        double inv = nci[i];
+        double inv = p->pja_weight ? 1.0 / m[i] : nci[i];
         if (bodies[b].is_free) {
           double a[3] = {C.bc_xc[3 * c] - bodies[b].pos[0], C.bc_xc[3 * c + 1] - bodies[b].pos[1],
                          C.bc_xc[3 * c + 2] - bodies[b].pos[2]};

@@ -29,6 +29,11 @@ typedef struct {
   uint32_t hash_size; /* n_h of Eq. 6 */
   double cyclic_z[2]; /* cyclic vertical boundary (gear tower, Sec. III): if cyclic_z[1] > cyclic_z[0], a
                          particle below cyclic_z[0] after a step moves up by cyclic_z[1] - cyclic_z[0] */
+  int32_t pja_weight; /* effective mass of a contact update: 0 = mass splitting, w = 1 / (n_i/m_i + n_j/m_j)
+                         (the reading of Alg. 1 used throughout); 1 = Alg. 1 as printed, where particle i
+                         adds the whole projected correction J b to its own velocity: w = m_i for every
+                         contact, nothing shared with the partner or among i's contacts (an ablation;
+                         free bodies are not supported with it) */
 } orc_params;
 
 enum { ORC_PLANE = 0, ORC_BOX = 1, ORC_BOX_MINUS_BOX = 2, ORC_OPEN_BOX = 3, ORC_GRID = 4, ORC_TUBE = 5 };
@@ -94,7 +99,8 @@ int orc_contacts(const orc_params *p, uint32_t n, const double *x, const double 
  * overrides the twist of kinematic bodies for this step.  wrench (n_bodies*6,
  * may be NULL) receives force and torque on each body, = -(sum of impulses
  * given to its contact partners) / dt.  pp_lam / bc_lam (3 per contact, CSR
- * order of orc_contacts, may be NULL) receive the final impulses.  Returns 0.
+ * order of orc_contacts, may be NULL) receive the final impulses.  Returns 0, -1 on a
+ * contact-capacity failure, -2 for pja_weight = 1 with a free body.
  */
 int orc_step(const orc_params *p, uint32_t n, double *x, double *v, const double *r,
              const double *m, uint32_t n_bodies, orc_body *bodies, const double *twist,

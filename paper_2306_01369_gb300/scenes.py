@@ -116,6 +116,7 @@ class Params:
     max_contacts: int = 16      # particle-particle capacity per particle
     max_body_contacts: int = 4  # particle-body capacity per particle
     cyclic_z: tuple = (0.0, 0.0)  # cyclic vertical boundary (bottom, top); off when equal
+    pja_weight: int = 0         # 0 mass splitting; 1 Alg. 1 as printed (w = m_i), an ablation
 
 
 @dataclass

@@ -386,6 +386,51 @@ def test_kinematic_body_pose_closed_form(orc):
     assert np.allclose(pose[3:], [math.cos(ang / 2), 0, 0, math.sin(ang / 2)], atol=1e-14)
 
 
+def _quat_mul(a, b):
+    """Hamilton product a (x) b of (w, x, y, z) quaternions."""
+    aw, ax, ay, az = a
+    bw, bx, by, bz = b
+    return np.array([aw * bw - ax * bx - ay * by - az * bz, aw * bx + ax * bw + ay * bz - az * by,
+                     aw * by - ax * bz + ay * bw + az * bx, aw * bz + ax * by - ay * bx + az * bw])
+
+
+def _quat_matrix(q):
+    q = np.asarray(q, np.float64) / np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+@pytest.mark.parametrize("omega", [(0.0, 0.0, 30.0), (10.0, -20.0, 5.0)])
+def test_kinematic_pose_world_frame_twist_from_tilted_start(orc, omega):
+    """Sec. II: a driven body's twist lives in se(3) with its angular part in the world
+    frame.  A body tilted 90 degrees about x that spins at a constant world omega has,
+    after k steps, the orientation exp(k dt omega / 2) (x) q0 exactly (one axis, so the
+    increments commute).  The frame mistake q0 (x) exp(...) gives another rotation
+    here, which scipy's independent rotation composition tells apart."""
+    from scipy.spatial.transform import Rotation
+    q0 = (math.cos(math.pi / 4), math.sin(math.pi / 4), 0.0, 0.0)
+    body = S.Body(kind=S.BOX, shape=(0.01, 0.01, 0.01), pos=(0.0, 0.0, 1.0), quat=q0, ang_vel=omega)
+    s = orc.Sim(np.zeros((0, 4), F32), np.zeros((0, 3), F32), np.zeros(0, F32), [body], _params())
+    k = 53
+    s.step(k)
+    dt = float(F32(1e-4))
+    th = k * dt * np.array([float(F32(w)) for w in omega])
+    q0f = np.array([float(F32(v)) for v in q0])
+    r0 = Rotation.from_quat([q0f[1], q0f[2], q0f[3], q0f[0]])          # scipy: (x, y, z, w)
+    want_world = (Rotation.from_rotvec(th) * r0).as_matrix()            # world-frame increment
+    want_body = (r0 * Rotation.from_rotvec(th)).as_matrix()             # body-frame increment
+    got = _quat_matrix(s.body_pose(0)[3:])
+    assert np.abs(got - want_world).max() < 1e-12
+    assert np.abs(want_body - want_world).max() > 1e-3                 # the two frames differ here
+    # and the closed form in quaternions: exp(k dt omega / 2) (x) q0, up to sign
+    ang = float(np.linalg.norm(th))
+    e = np.concatenate([[math.cos(ang / 2)], math.sin(ang / 2) * th / ang])
+    qk = _quat_mul(e, q0f / np.linalg.norm(q0f))
+    assert abs(abs(float(np.dot(qk, s.body_pose(0)[3:]))) - 1.0) < 1e-12
+
+
 def test_free_body_central_hit_inelastic(orc):
     """A sphere hitting a free box through its centre: both end with m v / (m + M)."""
     M = 2.0
@@ -418,6 +463,49 @@ def test_mass_splitting_weight_three_in_a_row(orc):
     s = orc.Sim(pr, vel, np.full(3, 2.0, F32), [], _params(pja_iters=1, cell_size=2.2))
     s.step(1)
     assert np.allclose(s.v[:, 0], [2.0 / 3.0, 0.0, -2.0 / 3.0], atol=1e-15)
+
+
+@pytest.mark.parametrize("iters", [1, 2, 3, 4, 5])
+def test_literal_alg1_weight_two_spheres_oscillate(orc, iters):
+    """Alg. 1 as printed (pja_weight = 1): each particle adds the whole projected
+    correction to its own velocity (w = m_i), whatever the masses.  For two touching
+    spheres approaching head-on (psi = 0, gravity off) the first iteration makes each
+    take the other's normal velocity; the next finds them separating and takes the
+    impulse back to zero, so the iterates alternate: after an odd number of
+    iterations the velocities are exchanged, after an even number unchanged.  (With
+    mass splitting they stick at the momentum-weighted mean.)"""
+    pr = np.array([[0.0, 0.0, 0.0, 0.5], [1.0, 0.0, 0.0, 0.5]], F32)
+    vel = np.array([[0.75, 0.1, 0.0], [-0.25, 0.0, 0.0]], F32)
+    m = np.array([1.0, 3.0], F32)
+    s = orc.Sim(pr, vel, m, [], _params(pja_iters=iters, pja_weight=1, mu=0.0, cell_size=1.2))
+    s.step(1)
+    want = vel.astype(np.float64)
+    if iters % 2:
+        want[0, 0], want[1, 0] = want[1, 0], want[0, 0]      # normal components exchanged
+    assert np.abs(s.v - want).max() < 1e-14, (iters, s.v)
+
+
+@pytest.mark.parametrize("iters", [1, 3])
+def test_literal_alg1_weight_three_in_a_row(orc, iters):
+    """Alg. 1 as printed on three equal touching spheres in a row, the outer ones
+    approaching the middle at v: each outer sphere removes its whole approach speed
+    (stops), the middle takes +v from one side and -v from the other (stays): all at
+    rest after the first iteration, and later iterations find nothing to correct.
+    (Mass splitting gives 2v/3, 0, -2v/3 after one iteration.)"""
+    pr = np.array([[-1.0, 0, 0, 0.5], [0.0, 0, 0, 0.5], [1.0, 0, 0, 0.5]], F32)
+    vel = np.array([[1.0, 0, 0], [0, 0, 0], [-1.0, 0, 0]], F32)
+    s = orc.Sim(pr, vel, np.full(3, 2.0, F32), [], _params(pja_iters=iters, pja_weight=1, cell_size=2.2))
+    s.step(1)
+    assert np.abs(s.v).max() < 1e-15
+
+
+def test_literal_alg1_weight_rejects_free_bodies(orc):
+    cube = S.Body(kind=S.BOX, shape=(0.25, 0.25, 0.25), pos=(0.75, 0.0, 0.0), is_free=1, mass=2.0,
+                  inertia=(0.1,) * 3)
+    s = orc.Sim(np.array([[0.0, 0.0, 0.0, 0.5]], F32), np.zeros((1, 3), F32), np.array([1.0], F32), [cube],
+                _params(pja_weight=1, cell_size=1.2))
+    with pytest.raises(RuntimeError):
+        s.step(1)
 
 
 def test_free_body_angular_momentum_frictionless(orc):
