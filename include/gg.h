@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define GG_ABI_VERSION 1u
+#define GG_ABI_VERSION 2u
 
 /* Only the functions declared here are exported from libgg.so. */
 #if defined(__GNUC__)
@@ -91,7 +91,11 @@ typedef struct {
                                 per environment; otherwise must be >= 2 r_max of every environment */
   uint32_t hash_factor;      /* hash table size n_h = hash_factor * n_env (Sec. II-B proposes 2);
                                 0 -> 2; ignored when hash_size != 0 */
-  uint32_t hash_size;        /* explicit n_h for every environment (tests); 0 -> hash_factor * n_env */
+  uint32_t hash_size;        /* explicit n_h for every environment (tests); 0 -> hash_factor * n_env.
+                                A bucket may hold at most 1024 particles (its own cell's and those
+                                of cells sharing its Eq. 6 value): a step whose binning crowds one
+                                bucket beyond that (a cell far above 2 r_max, a table far below n)
+                                cuts that bucket's walks short and reports GG_ERR_INVALID_ARG */
   uint32_t max_contacts;     /* particle-particle contact capacity per particle, 1..32; 0 -> 16 */
   uint32_t max_body_contacts;/* particle-body contact capacity per particle, 1..8; 0 -> 4 */
   uint32_t max_bodies;       /* bodies per environment, 1..64; 0 -> 8 */
@@ -101,7 +105,9 @@ typedef struct {
                                 the fastest; k >= 1: fixed set k (see gg_tuning_count; sets 7-9,
                                 11-12 bin by linked lists, sets 9, 10, 12 cap the sweep at 40
                                 registers, sets 11-13 find pairs over half the stencil and mirror
-                                them).  Results do not depend on it. */
+                                them, sets 14-15 (sort, lists) run detection and every sweep in one
+                                cooperative launch, sets 16-18 (sort, lists, lists with the half
+                                stencil) reverse every other sweep).  Results do not depend on it. */
   uint32_t wrench_history;   /* per-step body wrenches kept for readback; 0 -> 1 */
   uint32_t max_free_bodies;  /* free rigid bodies over all environments (beyond the paper's
                                 kinematic bodies, Sec. V two-way coupling); 0 -> none */
@@ -122,10 +128,19 @@ typedef struct {
                                 sweep), microseconds at the SM's maximum clock; past it the step
                                 reports GG_ERR_DEVICE_TIMEOUT.  0 -> 500,000 */
   uint32_t hash_tune;        /* 1 (with hash_size = hash_factor = 0): the autotuner also picks n_h
-                                among 2n, 4n and 8n per environment (tables sized for 8n).
-                                Positions, velocities and contacts do not depend on n_h; the
-                                bucket keys and the sort-order readbacks are those of the n_h
-                                in use (gg_hash_size).  0: n_h fixed as above */
+                                among 2n, 4n and 8n per environment (tables sized for 8n), then,
+                                when cell_size = 0, the cell edge among 2.002, 2.2 and 2.5 r_max.
+                                Positions, velocities and contacts depend on neither; the bucket
+                                keys and the sort-order readbacks are those of the n_h and cell
+                                edge in use (gg_hash_size, gg_cell_size).  0: both fixed as above */
+  uint32_t pja_weight;       /* effective mass of a contact update (Alg. 1): 0 = mass splitting,
+                                w = 1 / (n_i/m_i + n_j/m_j) with n_i the contact count of particle i
+                                (the library's reading, whose fixed point solves Eq. 1-3); 1 = Alg. 1
+                                as printed, where each particle adds the whole projected correction
+                                to its own velocity, w = m_i (an ablation: it over-corrects and an
+                                isolated pair alternates between bouncing and passing through with
+                                the iteration count).  1 is not supported with free bodies or
+                                differentiation (GG_ERR_UNSUPPORTED) */
 } gg_params;
 
 typedef struct {
@@ -331,7 +346,10 @@ GG_API uint32_t gg_kernels_per_step(const gg_sim *sim);
  *   NULL = 0), N = the end of the taped run.  Writes dL/dtwist (float[n_steps][6]:
  *   d/dlin_vel, d/dang_vel, world frame) and dL/dmu (float[1]).  Inputs and outputs
  *   on the device when on_device != 0.  Re-runs the forward from the checkpoints and
- *   leaves the simulation in its end-of-run state.  Synchronises `stream`.
+ *   leaves the simulation in its end-of-run state, also when it returns an error
+ *   partway through the reverse pass (the end state is copied back before the return;
+ *   after a GG_ERR_CUDA that copy may itself have failed, and the state is then
+ *   undefined).  Synchronises `stream`.
  */
 GG_API gg_status gg_tape_reserve(gg_sim *sim, uint32_t n_steps, uint32_t checkpoint_every);
 GG_API gg_status gg_step_taped(gg_sim *sim, uint32_t tool_body, uint32_t n_steps, void *stream);
@@ -341,6 +359,10 @@ GG_API gg_status gg_backward(gg_sim *sim, const float *dL_dpos, const float *dL_
 /* Hash table size n_h in use for environment `env` (Eq. 6's modulus); 0 for a bad
  * argument. */
 GG_API uint32_t gg_hash_size(const gg_sim *sim, uint32_t env);
+
+/* Cell edge c in use for environment `env` (Eq. 6's 2r, the grid the keys are computed
+ * on); 0 for a bad argument. */
+GG_API float gg_cell_size(const gg_sim *sim, uint32_t env);
 
 /* Number of fixed launch-shape sets accepted by gg_params.tuning, and the set chosen. */
 GG_API uint32_t gg_tuning_count(void);
@@ -352,6 +374,12 @@ GG_API uint32_t gg_tuning_selected(const gg_sim *sim);
 #define GG_TUNE_FUSED 2u /* all sweeps in one cooperative launch with grid barriers */
 #define GG_TUNE_LEAN 4u  /* the sweep capped at 40 registers */
 #define GG_TUNE_HALF 8u  /* pair search over half the stencil, then a mirroring pass */
+#define GG_TUNE_DETECT 16u /* detection and all sweeps in one cooperative launch, a grid barrier
+                              between them (the paper's TwoLoopsFused, Sec. II-D); without free
+                              bodies (with them the set runs the split launches) */
+#define GG_TUNE_SERP 32u   /* serpentine sweeps: every other sweep visits the particles in reverse,
+                              starting on the data the previous stage left in L2 */
+
 GG_API uint32_t gg_tuning_flags(uint32_t k);
 
 /* Time every launch-shape set gg_params.binning allows on the current state (3 steps
@@ -384,6 +412,11 @@ GG_API void gg_destroy(gg_sim *sim);
  * uint32[n_h + 1]; all caller-owned, on the current device; enqueued on `stream`.
  * Limits: n <= GG_NOALLOC_MAX_PARTICLES, 1 <= n_h <= GG_NOALLOC_MAX_BUCKETS, else
  * GG_ERR_INVALID_ARG (nothing is enqueued).  Calls no cudaMalloc or cudaFree.
+ * Bucket occupancy: ordering a bucket by id costs its occupancy per particle, so a
+ * bucket holding more than GG_NOALLOC_MAX_OCCUPANCY particles is not ordered: its
+ * ids appear in perm in an unspecified order (still exactly the bucket's members;
+ * keys and cell_start stay exact, and cell_start shows which buckets these are).
+ * With cell_size near 2 r_max and n_h >= n a bucket holds a few particles.
  * Scratch: a fixed static device array of about 12.6 MB that every GPU which loads
  * libgg.so holds until the process exits; every call on a device reuses it and
  * clears its histogram first, so calls that overlap on the GPU (other streams,
@@ -393,6 +426,7 @@ GG_API void gg_destroy(gg_sim *sim);
  */
 #define GG_NOALLOC_MAX_PARTICLES (1u << 20)
 #define GG_NOALLOC_MAX_BUCKETS (1u << 21)
+#define GG_NOALLOC_MAX_OCCUPANCY 1024u
 GG_API gg_status gg_bin_sort_noalloc(const float *pos_radius, uint32_t n, float cell_size, uint32_t n_h,
                                      uint32_t *keys, uint32_t *perm, uint32_t *cell_start, void *stream);
 

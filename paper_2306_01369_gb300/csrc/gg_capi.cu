@@ -28,17 +28,22 @@ namespace {
 
 // Launch-shape sets accepted by gg_params.tuning (index k-1).
 // (iters, per-launch sweep block, fused sweep block, fused grid, binning by lists, lean sweeps,
-//  half-stencil pair search)
+//  half-stencil pair search, detection and sweeps in one cooperative launch, serpentine sweeps)
 const gg::LaunchShape kShapes[] = {{0, 256, 0, 0, 0, 0, 0},    {0, 128, 0, 0, 0, 0, 0}, {0, 512, 0, 0, 0, 0, 0},
                                    {0, 64, 0, 0, 0, 0, 0},     {0, 256, 1024, 0, 0, 0, 0}, {0, 256, 512, 0, 0, 0, 0},
                                    {0, 256, 0, 0, 1, 0, 0},    {0, 128, 0, 0, 1, 0, 0}, {0, 256, 0, 0, 1, 1, 0},
                                    {0, 256, 0, 0, 0, 1, 0},    {0, 256, 0, 0, 1, 0, 1}, {0, 256, 0, 0, 1, 1, 1},
-                                   {0, 256, 0, 0, 0, 0, 1}};
+                                   {0, 256, 0, 0, 0, 0, 1},    {0, 256, 0, 0, 0, 0, 0, 1}, {0, 256, 0, 0, 1, 0, 0, 1},
+                                   {0, 128, 0, 0, 0, 0, 0, 0, 1}, {0, 128, 0, 0, 1, 0, 0, 0, 1},
+                                   {0, 128, 0, 0, 1, 0, 1, 0, 1}};
 constexpr uint32_t kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 // n_h factors the autotuner tries when gg_params.hash_tune is set (the paper's 2n first)
 constexpr uint32_t kHashFactors[] = {2, 4, 8};
 constexpr uint32_t kNumHashFactors = sizeof(kHashFactors) / sizeof(kHashFactors[0]);
+// cell edges (x r_max of each environment) it then tries when the cell size is not fixed
+constexpr double kCellFactors[] = {2.002, 2.2, 2.5};
+constexpr uint32_t kNumCellFactors = sizeof(kCellFactors) / sizeof(kCellFactors[0]);
 
 constexpr uint32_t kStateMagic = 0x31534747u;  // "GGS1"
 
@@ -57,6 +62,8 @@ struct gg_sim {
   uint32_t nh_total = 0, nh_pad = 0, n_chunks = 0;
   uint32_t nh_cap = 0;   // buckets allocated (nh_pad at the largest n_h factor tried)
   uint32_t hf = 2;       // n_h factor in use (hash_size = 0)
+  uint32_t cf = 0;       // cell edge in use: kCellFactors[cf] r_max per environment (cell_size = 0)
+  std::vector<float> rmax;  // largest radius of each environment
   std::vector<DevEnv> envs;
   std::vector<uint32_t> nbodies;
   std::vector<float *> traj;  // per body slot
@@ -134,6 +141,10 @@ gg_status status_from_flags(gg_sim *s, uint32_t f) {
     return fail(s, GG_ERR_INTERNAL, "a bucket list walk passed the particle count (cut short)");
   if (f & gg::kFlagDebugCheck)
     return fail(s, GG_ERR_INTERNAL, "a device-side index check of the GG_DEBUG build failed (access skipped)");
+  if (f & gg::kFlagBucketBound)
+    return fail(s, GG_ERR_INVALID_ARG,
+                "a hash bucket held more than " + std::to_string(gg::kMaxBucket) +
+                    " particles (cell_size far above 2 r_max, or hash_size far below n); its walks were cut short");
   if (f & gg::kFlagNonFinite) return fail(s, GG_ERR_NONFINITE, "a particle position or velocity became non-finite");
   if (f & (gg::kFlagPPOverflow | gg::kFlagBodyOverflow))
     return fail(s, GG_ERR_CONTACT_OVERFLOW, "a particle exceeded its contact capacity (flags " + std::to_string(f) + ")");
@@ -238,10 +249,11 @@ void rot_from_quat(const float *q, float *R) {
 gg_status set_shape(gg_sim *s, uint32_t k) {
   gg::LaunchShape ls = kShapes[k - 1];
   ls.iters = s->p.pja_iters;
-  if (ls.fused_block) {
+  if (ls.fused_block || ls.detect) {
     int nsm = 0;
     GG_CUDA(s, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device));
-    const int per = gg::fused_pja_blocks_per_sm(ls.fused_block);
+    const int per = ls.detect ? gg::detect_sweeps_blocks_per_sm(ls.lists != 0, s->K)
+                              : gg::fused_pja_blocks_per_sm(ls.fused_block);
     ls.fused_grid = per > 0 ? (uint32_t)(per * nsm) : 0;
   }
   s->ls = ls;
@@ -299,6 +311,23 @@ gg_status set_hash_factor(gg_sim *s, uint32_t factor, cudaStream_t st) {
   return GG_OK;
 }
 
+// Switch the cell edge of every environment to kCellFactors[f] r_max between steps (no
+// effect when gg_params.cell_size fixes it): new reciprocals on the device (ordered on
+// `st`), graphs recaptured.  Contacts and dynamics do not depend on it (the pair test is
+// exact and every cell within reach is walked); the bucket keys do.
+gg_status set_cell_factor(gg_sim *s, uint32_t f, cudaStream_t st) {
+  if (s->p.cell_size > 0.f || f == s->cf) return GG_OK;
+  for (uint32_t e = 0; e < s->n_envs; ++e) {
+    const float c = s->envs[e].n ? (float)(kCellFactors[f] * (double)s->rmax[e]) : 1.0f;
+    s->envs[e].inv_cell = (float)(1.0 / (double)c);
+  }
+  s->cf = f;
+  GG_CUDA(s, cudaMemcpyAsync(s->a.envs, s->envs.data(), sizeof(DevEnv) * s->n_envs, cudaMemcpyHostToDevice, st));
+  GG_CUDA(s, cudaStreamSynchronize(st));
+  free_graph(s);
+  return GG_OK;
+}
+
 // Time the current graph: one untimed step, then 3 (state restored first).
 gg_status time_trial(gg_sim *s, const char *saved, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st, float *ms) {
   gg_status rc = capture(s);
@@ -337,7 +366,9 @@ gg_status autotune(gg_sim *s, cudaStream_t st) {
   bool first = true;
   for (uint32_t k = 1; rc == GG_OK && k <= kNumShapes; ++k) {
     if (!shape_allowed(s, k)) continue;
-    if ((rc = set_shape(s, k)) != GG_OK || (kShapes[k - 1].fused_block && !s->ls.fused_grid)) continue;
+    if ((rc = set_shape(s, k)) != GG_OK ||
+        ((kShapes[k - 1].fused_block || kShapes[k - 1].detect) && !s->ls.fused_grid))
+      continue;
     float ms = 0.f;
     if ((rc = time_trial(s, saved, e0, e1, st, &ms)) != GG_OK) break;
     if (first || ms < best) {
@@ -357,8 +388,25 @@ gg_status autotune(gg_sim *s, cudaStream_t st) {
       best_f = kHashFactors[f];
     }
   }
+  // then the cell edge, with the chosen set and table
+  uint32_t best_c = s->cf;
+  if (rc == GG_OK && tune_nh && s->p.cell_size <= 0.f) {
+    rc = set_hash_factor(s, best_f, st);
+    if (rc == GG_OK) rc = set_shape(s, best_k);
+    for (uint32_t f = 0; rc == GG_OK && f < kNumCellFactors; ++f) {
+      if (f == best_c) continue;
+      float ms = 0.f;
+      if ((rc = set_cell_factor(s, f, st)) != GG_OK) break;
+      if ((rc = time_trial(s, saved, e0, e1, st, &ms)) != GG_OK) break;
+      if (ms < best) {
+        best = ms;
+        best_c = f;
+      }
+    }
+  }
   if (rc == GG_OK) rc = restore_state(s, saved, st);
   if (rc == GG_OK) rc = set_hash_factor(s, best_f, st);
+  if (rc == GG_OK) rc = set_cell_factor(s, best_c, st);
   if (rc == GG_OK) rc = set_shape(s, best_k);
   if (rc == GG_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = cuda_fail(s, cudaGetLastError(), "autotune");
   if (e0) cudaEventDestroy(e0);
@@ -416,11 +464,17 @@ uint32_t gg_tuning_count(void) { return kNumShapes; }
 
 uint32_t gg_hash_size(const gg_sim *s, uint32_t env) { return (s && env < s->n_envs) ? s->envs[env].nh : 0; }
 
+float gg_cell_size(const gg_sim *s, uint32_t env) {
+  if (!s || env >= s->n_envs) return 0.f;
+  if (s->p.cell_size > 0.f) return s->p.cell_size;
+  return s->envs[env].n ? (float)(kCellFactors[s->cf] * (double)s->rmax[env]) : 1.0f;
+}
+
 uint32_t gg_tuning_flags(uint32_t k) {
   if (k < 1 || k > kNumShapes) return 0;
   const gg::LaunchShape &ls = kShapes[k - 1];
   return (ls.lists ? GG_TUNE_LISTS : 0u) | (ls.fused_block ? GG_TUNE_FUSED : 0u) | (ls.lean ? GG_TUNE_LEAN : 0u) |
-         (ls.half ? GG_TUNE_HALF : 0u);
+         (ls.half ? GG_TUNE_HALF : 0u) | (ls.detect ? GG_TUNE_DETECT : 0u) | (ls.serp ? GG_TUNE_SERP : 0u);
 }
 
 uint32_t gg_kernels_per_step(const gg_sim *sim) { return sim ? gg::kernels_per_step(sim->a, sim->ls) : 0; }
@@ -514,6 +568,9 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
   if (P.binning > 2 || !std::isfinite(P.cyclic_z[0]) || !std::isfinite(P.cyclic_z[1]) ||
       (P.cyclic_z[1] < P.cyclic_z[0]))
     return bail(GG_ERR_INVALID_ARG);
+  if (P.pja_weight > 1) return bail(GG_ERR_INVALID_ARG);
+  if (P.pja_weight && P.max_free_bodies)
+    return bail(fail(s, GG_ERR_UNSUPPORTED, "pja_weight = 1 (Alg. 1 as printed) does not support free bodies"));
   s->F = P.max_free_bodies;
   s->Lcap = P.free_contact_capacity ? P.free_contact_capacity : 4096;
   if (s->F > 4096 || s->Lcap > 8192) return bail(GG_ERR_INVALID_ARG);
@@ -563,6 +620,7 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
       rmax = std::max(rmax, h_pos[i].w);
       h_env[i] = e;
     }
+    s->rmax.push_back(rmax);
     float c = P.cell_size > 0.f ? P.cell_size : (float)(2.002 * (double)rmax);
     if (E.n && !(c >= 2.0f * rmax))
       return bail(fail(s, GG_ERR_INVALID_ARG, "cell_size must be >= 2 r_max of every environment"));
@@ -599,6 +657,7 @@ gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const uint32
   a.dt = P.dt;
   a.mu = P.mu;
   a.ab = P.alpha / P.dt;
+  a.lit = P.pja_weight;
   {
     int khz = 0;
     if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, s->device) != cudaSuccess || khz <= 0) khz = 2000000;
@@ -710,6 +769,9 @@ gg_status gg_set_bodies(gg_sim *s, uint32_t env, uint32_t n_bodies, const gg_bod
     const bool unit = std::fabs(qn - 1.0) < 1e-6;
     for (int k = 0; k < 4; ++k) o.q[k] = unit ? in.quat[k] : (float)(in.quat[k] / qn);
     rot_from_quat(o.q, o.R);  // valid before the first step (gg_render); each step recomputes it
+    if (in.kind == GG_BODY_BOX || in.kind == GG_BODY_BOX_MINUS_BOX)  // the solid lies inside box A
+      o.bound_r = (float)std::sqrt((double)in.shape[0] * in.shape[0] + (double)in.shape[1] * in.shape[1] +
+                                   (double)in.shape[2] * in.shape[2]);
     o.mass = in.mass;
     o.env = env;
     o.active = 1;
@@ -808,6 +870,12 @@ gg_status gg_set_body_grid(gg_sim *s, uint32_t env, uint32_t body, const uint32_
   hb.shape[3] = spacing;
   hb.shape[4] = (float)(1.0 / (double)spacing);
   hb.grid = g;
+  double far2 = 0.0;  // the sampled box's farthest corner from the body origin (no contact beyond the box)
+  for (int k = 0; k < 3; ++k) {
+    const double lo = origin[k], hi = origin[k] + (double)spacing * (dims[k] - 1);
+    far2 += std::max(lo * lo, hi * hi);
+  }
+  hb.bound_r = (float)std::sqrt(far2);
   GG_CUDA(s, cudaMemcpy(s->a.bodies + gb, &hb, sizeof(DevBody), cudaMemcpyHostToDevice));
   return GG_OK;
 }
@@ -1105,6 +1173,7 @@ gg_status gg_tape_reserve(gg_sim *s, uint32_t n_steps, uint32_t K) {
   if (!s) return GG_ERR_INVALID_ARG;
   if (s->n_envs != 1) return fail(s, GG_ERR_UNSUPPORTED, "differentiation needs a single environment");
   if (s->F) return fail(s, GG_ERR_UNSUPPORTED, "differentiation of free rigid bodies is not supported");
+  if (s->a.lit) return fail(s, GG_ERR_UNSUPPORTED, "differentiation with pja_weight = 1 is not supported");
   if (n_steps == 0 || K == 0) return fail(s, GG_ERR_INVALID_ARG, "gg_tape_reserve: n_steps and K must be > 0");
   GG_CUDA(s, cudaDeviceSynchronize());
   for (void *p : s->ad.allocs) cudaFree(p);
@@ -1236,6 +1305,17 @@ gg_status gg_backward(gg_sim *s, const float *dL_dpos, const float *dL_dvel, con
       }
     }
   } guard{&bexec, st};
+  // An error inside the segment loop would leave the simulation at an intermediate
+  // checkpoint: put the end state of the taped run back on every return before the
+  // loop completes (destroyed before `guard`, so the copy is queued before its wait).
+  struct FinGuard {
+    gg_sim *s;
+    cudaStream_t st;
+    bool done;
+    ~FinGuard() {
+      if (!done) (void)restore_state(s, s->ad.fin, st);
+    }
+  } fin_guard{s, st, false};
   const uint32_t nseg = (N + K - 1) / K;
   for (int seg = (int)nseg - 1; seg >= 0; --seg) {
     const uint32_t k0 = (uint32_t)seg * K, k1 = std::min(k0 + K, N);
@@ -1251,6 +1331,7 @@ gg_status gg_backward(gg_sim *s, const float *dL_dpos, const float *dL_dvel, con
     }
   }
 
+  fin_guard.done = true;
   gg_status rc = restore_state(s, s->ad.fin, st);
   if (rc != GG_OK) return rc;
   GG_CUDA(s, cudaMemcpyAsync(dL_dtwist, d.dtwist, sizeof(float) * 6 * N, x2h, st));

@@ -21,6 +21,15 @@ constexpr uint32_t kFlagNonFinite = 4u;
 constexpr uint32_t kFlagTimeout = 8u;    // a bounded device-side wait gave up
 constexpr uint32_t kFlagListBound = 16u; // a bucket list walk passed n entries (lists not emptied)
 constexpr uint32_t kFlagDebugCheck = 32u; // an index check of the GG_DEBUG build failed
+constexpr uint32_t kFlagBucketBound = 64u; // a bucket held more than kMaxBucket particles
+
+// Most particles one bucket may hold.  With cells of about 2 r_max a bucket holds a
+// particle or two (its own cell's, plus those of cells that share its Eq. 6 value);
+// only a cell size far above 2 r_max or a table far smaller than n crowds one.  The
+// in-bucket ordering and every bucket walk stop at this many entries and latch
+// kFlagBucketBound, so a crowded bucket costs at most this much work per particle
+// and the step reports an error instead of running for minutes.
+constexpr uint32_t kMaxBucket = 1024;
 
 constexpr uint32_t kListEnd = 0xffffffffu;  // end of a bucket's linked list
 constexpr int kMaxK = 32;   // particle-particle capacity limit
@@ -66,6 +75,10 @@ struct DevBody {
   // spacing h, shape[4] float(1 / h)
   const float *grid;
   uint32_t gn[3];
+  // radius about p outside which the body's SDF exceeds the distance beyond this radius
+  // (closed solids: box, box minus box, sampled grids; 0 for unbounded bodies): a
+  // particle farther than bound_r + r from p cannot touch it, so its SDF is not evaluated
+  float bound_r;
 };
 
 // Programmatic dependent launch (sm_90 and later).  A kernel launched with programmatic
@@ -121,6 +134,8 @@ struct StepArgs {
   float cyc_lo, cyc_h;    // cyclic vertical boundary: z < cyc_lo moves up by cyc_h (cyc_h > 0), else off
   long long wait_cycles;  // bound of device-side waits (SM clock cycles)
   uint32_t lists;         // binning: 0 counting sort (contiguous buckets), 1 linked lists (Alg. 2)
+  uint32_t lit;           // contact weight: 0 mass splitting (U.w = n_i / m_i, w = 1 / (U_i.w + U_j.w));
+                          // 1 Alg. 1 as printed (U.w = 1 / m_i, w = 1 / U_i.w = m_i)
   uint32_t *head;         // lists: first particle of each bucket (kListEnd: empty), nh_pad entries
   uint32_t *next;         // lists: next particle of the same bucket, [n]
   uint32_t *pcnt;         // half-stencil pair search: entries per particle (0 between steps), [n]

@@ -36,8 +36,11 @@ struct LaunchShape {
   uint32_t lean;        // per-launch sweeps capped at 40 registers (more resident warps: pays
                         // when the working set spills out of L2, costs when it fits)
   uint32_t half;        // pair search over half the stencil in two passes instead of k_contacts
+  uint32_t detect;      // detection and all sweeps in one cooperative launch (fused_grid blocks)
+  uint32_t serp;        // serpentine sweeps: every other per-launch sweep runs its blocks in reverse
 };
 int fused_pja_blocks_per_sm(int block);
+int detect_sweeps_blocks_per_sm(bool lists, uint32_t K);
 
 // ev (optional): 5 events recorded at the stage boundaries of the step.
 // tape (optional): keep every sweep's iterates and stop after the sweeps (no

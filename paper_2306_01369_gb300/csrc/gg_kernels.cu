@@ -123,8 +123,11 @@ __global__ void k_key(StepArgs a) {
     const DevEnv &E = a.envs[a.env_of[i]];
     int32_t k0 = cell_of(p.x, E.inv_cell), k1 = cell_of(p.y, E.inv_cell), k2 = cell_of(p.z, E.inv_cell);
     uint32_t key = E.hbase + hash_cell_fm(k0, k1, k2, E);
+    // checked build: a key outside the environment's range is replaced by an in-range
+    // one before it is stored, so the scatter, reorder and walks that index with the
+    // stored key stay in bounds while the failed check is latched
+    if (!GG_GUARD(a.ctrl, key - E.hbase < E.nh && key < a.nh_total)) key = E.hbase < a.nh_total ? E.hbase : 0u;
     a.key_id[i] = key;
-    if (!GG_GUARD(a.ctrl, key - E.hbase < E.nh && key < a.nh_total)) return;
     if (a.lists)
       a.next[i] = atomicExch(&a.head[key], i);  // lock-free push onto the bucket's list (Alg. 2)
     else
@@ -267,7 +270,12 @@ __global__ void k_reorder(StepArgs a) {
   const uint2 rg = a.range[key];
   const uint32_t b0 = rg.x, b1 = rg.y;
   uint32_t rank = 0;
-  for (uint32_t t = b0; t < b1; ++t) rank += (a.sid_tmp[t] < id) ? 1u : 0u;
+  if (b1 - b0 > kMaxBucket) {  // too crowded to rank: keep the scatter's order, report
+    flag(a.ctrl, kFlagBucketBound);
+    rank = s - b0;
+  } else {
+    for (uint32_t t = b0; t < b1; ++t) rank += (a.sid_tmp[t] < id) ? 1u : 0u;
+  }
   a.sid[b0 + rank] = id;
   a.pos_s[b0 + rank] = a.pos_id[id];
 }
@@ -300,6 +308,15 @@ __device__ __forceinline__ void insert_partner(uint32_t *fid, uint32_t S, uint32
   }
   for (uint32_t q2 = npp - 1; q2 > p; --q2) fid[q2 * S] = fid[(q2 - 1) * S];
   fid[p * S] = jid;
+}
+
+// A bucket's (start, end), cut to kMaxBucket entries (the cut is reported).
+__device__ __forceinline__ uint2 bounded_range(const StepArgs &a, uint2 rg) {
+  if (rg.y - rg.x > kMaxBucket) {
+    flag(a.ctrl, kFlagBucketBound);
+    rg.y = rg.x + kMaxBucket;
+  }
+  return rg;
 }
 
 constexpr int kWalkGroup = 3;       // buckets of a row (dx = -1, 0, 1), walked together
@@ -339,6 +356,11 @@ __device__ __forceinline__ void contact_records(const StepArgs &a, uint32_t i, f
     for (uint32_t b = 0; b < E.nbodies; ++b) {
       const uint32_t gb = e * a.maxb + b;
       const DevBody &B = a.bodies[gb];
+      if (B.bound_r > 0.f) {  // outside the bounding sphere (with a margin far above rounding): no contact
+        const float dx = xi.x - B.p[0], dy = xi.y - B.p[1], dz = xi.z - B.p[2];
+        const float rb = B.bound_r + pi.w;
+        if (dx * dx + dy * dy + dz * dz > 1.0001f * rb * rb) continue;
+      }
       const float3 y = world_to_body(B, xi);
       int br;
       const float f = body_sdf(B, y, &br);
@@ -371,7 +393,7 @@ __device__ __forceinline__ void contact_records(const StepArgs &a, uint32_t i, f
     if (ovf) flag(a.ctrl, kFlagPPOverflow);
     a.ccount[i] = npp | (nbc << 8);
     const float4 sb = base_velocity(a, a.vel_id[i]);
-    a.U[0][i] = make_float4(sb.x, sb.y, sb.z, (float)(npp + nbc) * sb.w);
+    a.U[0][i] = make_float4(sb.x, sb.y, sb.z, (float)(a.lit ? 1u : npp + nbc) * sb.w);
   }
 
 // Per-step statistics (integer atomics: order-independent); every thread of the warp calls.
@@ -399,20 +421,16 @@ __device__ __forceinline__ void contact_stats(const StepArgs &a, uint32_t npp, u
 // in shared memory, slot p of thread t at [p * blockDim.x + t] (conflict-free): an
 // array indexed at run time in registers would go to local memory, which at full
 // occupancy does not fit in L1.  Dynamic shared memory: K * blockDim.x words.
+// Detection of particle i (Sec. II-B 27-cell query, Sec. II-C SDF tests): its partner
+// list in the thread's shared-memory column fid (stride S), then its contact records.
 template <bool LISTS>
-__global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
-  pdl_enter();
-  extern __shared__ uint32_t s_fid[];
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t npp = 0, nbc = 0;
-  float psi_max = 0.f;
-  if (i < a.n) {
+__device__ __forceinline__ void detect_particle(const StepArgs &a, uint32_t i, uint32_t *fid, uint32_t S,
+                                                uint32_t &npp, uint32_t &nbc, float &psi_max) {
+  {
     const float4 pi = a.pos_id[i];
     const uint32_t e = a.env_of[i];
     const DevEnv E = a.envs[e];
     const int32_t k0 = cell_of(pi.x, E.inv_cell), k1 = cell_of(pi.y, E.inv_cell), k2 = cell_of(pi.z, E.inv_cell);
-    uint32_t *fid = s_fid + threadIdx.x;
-    const uint32_t S = blockDim.x;
     const uint32_t K = a.K;
     bool ovf = false;
     // Eq. 6 terms of the three cells along each axis, combined 27 ways below
@@ -459,7 +477,7 @@ __global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
     for (int q = 0; q < kWalkGroup; ++q) {
       n0[q] = n1[q] = 0u;
       if (g2x[q] + g2y[0] + g2z[0] <= reach) {
-        const uint2 rg = a.range[E.hbase + mod_nh(hx[q] ^ hy[0] ^ hz[0], E)];
+        const uint2 rg = bounded_range(a, a.range[E.hbase + mod_nh(hx[q] ^ hy[0] ^ hz[0], E)]);
         n0[q] = rg.x;
         n1[q] = rg.y;
       }
@@ -481,7 +499,7 @@ __global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
         for (int q = 0; q < kWalkGroup; ++q) {
           n0[q] = n1[q] = 0u;
           if (g2x[q] + g2yz <= reach) {
-            const uint2 rg = a.range[E.hbase + mod_nh(hx[q] ^ hyz, E)];
+            const uint2 rg = bounded_range(a, a.range[E.hbase + mod_nh(hx[q] ^ hyz, E)]);
             n0[q] = rg.x;
             n1[q] = rg.y;
           }
@@ -548,6 +566,10 @@ __global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
           flag(a.ctrl, kFlagListBound);
           break;
         }
+        if (round >= kMaxBucket) {
+          flag(a.ctrl, kFlagBucketBound);
+          break;
+        }
 #pragma unroll
         for (int q = 0; q < kWalkGroup; ++q) {
           if (jn[q] == kListEnd) continue;
@@ -561,6 +583,16 @@ __global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
     }
     contact_records(a, i, pi, e, E, fid, S, K, npp, ovf, nbc, psi_max);
   }
+}
+
+template <bool LISTS>
+__global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
+  pdl_enter();
+  extern __shared__ uint32_t s_fid[];
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t npp = 0, nbc = 0;
+  float psi_max = 0.f;
+  if (i < a.n) detect_particle<LISTS>(a, i, s_fid + threadIdx.x, blockDim.x, npp, nbc, psi_max);
   contact_stats(a, npp, nbc, psi_max);
 }
 
@@ -659,6 +691,10 @@ __global__ void __launch_bounds__(kContactsBlock, 9) k_pairs_half(StepArgs a) {
           flag(a.ctrl, kFlagListBound);
           break;
         }
+        if (round >= kMaxBucket) {
+          flag(a.ctrl, kFlagBucketBound);
+          break;
+        }
 #pragma unroll
         for (int q = 0; q < kWalkGroup; ++q) {
           if (jn[q] == kListEnd) continue;
@@ -676,7 +712,7 @@ __global__ void __launch_bounds__(kContactsBlock, 9) k_pairs_half(StepArgs a) {
       for (int q = 0; q < kWalkGroup; ++q) {
         r0[q] = r1[q] = 0u;
         if (((mask >> q) & 1u) && g2x[q] + g2yz <= reach) {
-          const uint2 rg = a.range[E.hbase + mod_nh(hx[q] ^ hyz, E)];
+          const uint2 rg = bounded_range(a, a.range[E.hbase + mod_nh(hx[q] ^ hyz, E)]);
           r0[q] = rg.x;
           r1[q] = rg.y;
         }
@@ -769,6 +805,7 @@ __device__ __forceinline__ void pja_particle(const StepArgs &a, uint32_t i, int 
   float sx = 0.f, sy = 0.f, sz = 0.f;
   const size_t KN = (size_t)a.K * n;
   const float mu = a.mu, ab = a.ab;
+  const float pw = a.lit ? 0.f : 1.f;  // partner's share of the effective mass (exact 0 or 1)
   // two contacts per round: both rounds' loads issue before either update is stored;
   // the impulses are still added in contact order
   uint32_t c = 0;
@@ -782,9 +819,9 @@ __device__ __forceinline__ void pja_particle(const StepArgs &a, uint32_t i, int 
     const float4 u0 = LDCG ? __ldcg(Uin + j0) : Uin[j0];
     const float4 u1 = LDCG ? __ldcg(Uin + j1) : Uin[j1];
     const float3 l0 = pja_project(la0, make_float3(ui.x - u0.x, ui.y - u0.y, ui.z - u0.z), make_float3(n0.x, n0.y, n0.z),
-                                  ab * n0.w, 1.0f / (ui.w + u0.w), mu);
+                                  ab * n0.w, 1.0f / (ui.w + pw * u0.w), mu);
     const float3 l1 = pja_project(la1, make_float3(ui.x - u1.x, ui.y - u1.y, ui.z - u1.z), make_float3(n1.x, n1.y, n1.z),
-                                  ab * n1.w, 1.0f / (ui.w + u1.w), mu);
+                                  ab * n1.w, 1.0f / (ui.w + pw * u1.w), mu);
     clam[o0] = l0.x;
     clam[o0 + KN] = l0.y;
     clam[o0 + 2 * KN] = l0.z;
@@ -815,7 +852,7 @@ __device__ __forceinline__ void pja_particle(const StepArgs &a, uint32_t i, int 
     const float4 uj = LDCG ? __ldcg(Uin + j) : Uin[j];
     const float3 lam = make_float3(clam[o], clam[o + KN], clam[o + 2 * KN]);
     const float3 l = pja_project(lam, make_float3(ui.x - uj.x, ui.y - uj.y, ui.z - uj.z), make_float3(nn.x, nn.y, nn.z),
-                                 ab * nn.w, 1.0f / (ui.w + uj.w), mu);
+                                 ab * nn.w, 1.0f / (ui.w + pw * uj.w), mu);
     clam[o] = l.x;
     clam[o + KN] = l.y;
     clam[o + 2 * KN] = l.z;
@@ -872,20 +909,35 @@ __device__ __forceinline__ void pja_particle(const StepArgs &a, uint32_t i, int 
   if (TAPE) tp.Uh[(size_t)(it + 1) * n + i] = un;
 }
 
+// Blocks are dispatched in index order, and the caches keep what was touched last.
+// With rev set, a sweep runs over the particles from the last block to the first: the
+// serpentine launch shapes reverse every other sweep, starting with the first, so that
+// each sweep starts on the particles whose data the stage before it (the contact
+// build, or the previous sweep) touched last, while they are still in L2.  That pays
+// when the sweep's working set is larger than L2 (a 1M-sphere bed: 41.7 -> 35.1 us per
+// sweep) and costs when it fits and the work is uneven (the collapsing column, whose
+// contacts sit in its low ids: a reversed sweep dispatches its heavy blocks last, 3.3
+// -> 3.7 us), so it is a launch shape the autotuner chooses.  A sweep's order does not
+// change its results (Jacobi).
+__device__ __forceinline__ uint32_t sweep_particle(int rev) {
+  const uint32_t blk = rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+  return blk * blockDim.x + threadIdx.x;
+}
+
 // One sweep per launch.
 template <bool TAPE>
-__global__ void __launch_bounds__(512) k_pja(StepArgs a, int s, Tape tp, int it) {
+__global__ void __launch_bounds__(512) k_pja(StepArgs a, int s, Tape tp, int it, int rev) {
   pdl_enter();
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t i = sweep_particle(rev);
   if (i < a.n) pja_particle<TAPE, false>(a, i, s, tp, it);
 }
 
 // One sweep per launch with at most 40 registers per thread (62.5 % -> 75 % occupancy
 // at 256-thread blocks, at the price of a few spilled values): the autotuner's choice
 // when the sweep's working set streams from DRAM.
-__global__ void __maxnreg__(40) k_pja_lean(StepArgs a, int s, int it) {
+__global__ void __maxnreg__(40) k_pja_lean(StepArgs a, int s, int it, int rev) {
   pdl_enter();
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t i = sweep_particle(rev);
   const Tape none{};
   if (i < a.n) pja_particle<false, false>(a, i, s, none, it);
 }
@@ -930,6 +982,39 @@ __global__ void __launch_bounds__(1024) k_pja_fused(StepArgs a, uint32_t iters) 
   const Tape none{};
   for (uint32_t it = 0; it < iters; ++it) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x)
+      pja_particle<false, true>(a, i, (int)(it & 1), none, (int)it);
+    if (it + 1 < iters) grid_barrier(a.ctrl, a.wait_cycles);
+  }
+}
+
+// Detection and all I sweeps in one persistent cooperative launch (no free bodies):
+// the paper's TwoLoopsFused (Sec. II-D, Fig. warp-divergence-performance), the
+// collision loop and the impulse loop kept as two loops of one kernel.  A sweep needs
+// the contact count of every partner (the mass-splitting weight) and the partner's
+// first velocity estimate, so a grid barrier separates detection from the first sweep,
+// and each sweep from the next.  Each thread handles the same particles in both loops
+// (grid-stride), so its own contact records are read back by the SM that wrote them;
+// partners' estimates are read through L2.  Same per-particle arithmetic as
+// k_contacts + k_pja, so results are bit-identical to the split launches.
+constexpr int kDetectSweepBlock = 256;
+
+template <bool LISTS>
+__global__ void __launch_bounds__(kDetectSweepBlock) k_detect_sweeps(StepArgs a, uint32_t iters) {
+  pdl_enter();
+  extern __shared__ uint32_t s_fid[];
+  const Tape none{};
+  const uint32_t stride = gridDim.x * blockDim.x;
+  // every thread of a block runs the same rounds, so the warp-level statistics see all lanes
+  for (uint32_t base = blockIdx.x * blockDim.x; base < a.n; base += stride) {
+    const uint32_t i = base + threadIdx.x;
+    uint32_t npp = 0, nbc = 0;
+    float psi_max = 0.f;
+    if (i < a.n) detect_particle<LISTS>(a, i, s_fid + threadIdx.x, blockDim.x, npp, nbc, psi_max);
+    contact_stats(a, npp, nbc, psi_max);
+  }
+  grid_barrier(a.ctrl, a.wait_cycles);
+  for (uint32_t it = 0; it < iters; ++it) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
       pja_particle<false, true>(a, i, (int)(it & 1), none, (int)it);
     if (it + 1 < iters) grid_barrier(a.ctrl, a.wait_cycles);
   }
@@ -1112,9 +1197,11 @@ __device__ __forceinline__ void integrate_particle(const StepArgs &a, int s, uin
 
 constexpr int kIntegrateThreads = kWrenchChunk;  // one particle of the chunk per thread
 
-__global__ void __launch_bounds__(kIntegrateThreads) k_integrate_wrench(StepArgs a, int s) {
+__global__ void __launch_bounds__(kIntegrateThreads) k_integrate_wrench(StepArgs a, int s, int rev) {
   pdl_enter();
-  const uint32_t c = blockIdx.x;
+  // rev: the last sweep ran forward in a serpentine launch shape, so start from the last
+  // chunk, on the estimates still in L2 (the partials are per chunk: order changes nothing)
+  const uint32_t c = rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
   const uint32_t e = a.chunk_env[c];
   const DevEnv &E = a.envs[e];
   const uint32_t s0 = E.off + (c - E.chunk0) * kWrenchChunk;
@@ -1386,7 +1473,10 @@ static inline cudaError_t mark(cudaEvent_t *ev, int k, cudaStream_t st) {
 
 uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls) {
   uint32_t k = a.lists ? 2 : 5;  // key (+ scan x3), wrench sums + body poses
-  if (a.n) k += (a.lists ? 1 : 3) + (ls.half ? 1 : 0) + ((ls.fused_grid && !a.F) ? 1 : ls.iters);  // (scatter, reorder,) contacts, pja
+  if (a.n && ls.detect && ls.fused_grid && !a.F)
+    k += (a.lists ? 0 : 2) + 1;  // (scatter, reorder,) detection + sweeps
+  else if (a.n)
+    k += (a.lists ? 1 : 3) + (ls.half ? 1 : 0) + ((ls.fused_grid && !a.F) ? 1 : ls.iters);  // (scatter, reorder,) contacts, pja
   if (a.n_chunks) k += 1;  // integrate + wrench partials
   if (a.F) k += 1 + ls.iters;  // free_prep, free_update x I
   return k;
@@ -1428,7 +1518,26 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
     }
   }
   GG_MARK(1);
-  if (a.n) {
+  // detection and the sweeps in one cooperative launch (not with free bodies, whose
+  // updates run between sweeps, nor taped)
+  const bool detect_fused = ls.detect && ls.fused_grid && !a.F && !tp && a.n;
+  if (detect_fused) {
+    GG_MARK(2);  // the contact stage is inside the sweeps' launch: its interval stays empty
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ls.fused_grid);
+    cfg.blockDim = dim3(kDetectSweepBlock);
+    cfg.dynamicSmemBytes = (size_t)a.K * kDetectSweepBlock * sizeof(uint32_t);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if ((e = cudaLaunchKernelEx(&cfg, a.lists ? k_detect_sweeps<true> : k_detect_sweeps<false>, a, ls.iters)) !=
+        cudaSuccess)
+      return e;
+    after_kernel = true;
+  } else if (a.n) {
     const size_t smem = (size_t)a.K * kContactsBlock * sizeof(uint32_t);
     const dim3 g(grid_for(a.n, kContactsBlock));
     if (ls.half) {
@@ -1444,7 +1553,7 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
     }
   }
   if (a.F) GG_LAUNCH(k_free_prep, dim3(a.F), 1024, 0, a);
-  GG_MARK(2);
+  if (!detect_fused) GG_MARK(2);
   if (tp && a.n) {  // U^0 and lambda^0 = 0 open the tape
     if ((e = cudaMemcpyAsync(tp->Uh, a.U[0], sizeof(float4) * a.n, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(tp->lamh, 0, sizeof(float) * 3 * (size_t)a.K * a.n, st)) != cudaSuccess) return e;
@@ -1452,7 +1561,9 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
     after_kernel = false;
   }
   const Tape none{};
-  if (!tp && ls.fused_grid && !a.F && a.n) {
+  if (detect_fused) {
+    // the sweeps ran in the detection launch
+  } else if (!tp && ls.fused_grid && !ls.detect && !a.F && a.n) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ls.fused_grid);
     cfg.blockDim = dim3(ls.fused_block);
@@ -1466,13 +1577,15 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
     after_kernel = true;
   } else
   for (uint32_t it = 0; it < ls.iters; ++it) {
+    const int rev = (ls.serp && !tp && it % 2 == 0) ? 1 : 0;  // serpentine: reverse sweeps 0, 2, 4, ...
     if (a.n) {
       if (tp)
-        GG_LAUNCH(k_pja<true>, dim3(grid_for(a.n, ls.pja_block)), ls.pja_block, 0, a, (int)(it & 1), *tp, (int)it);
+        GG_LAUNCH(k_pja<true>, dim3(grid_for(a.n, ls.pja_block)), ls.pja_block, 0, a, (int)(it & 1), *tp, (int)it, 0);
       else if (ls.lean)
-        GG_LAUNCH(k_pja_lean, dim3(grid_for(a.n, ls.pja_block)), ls.pja_block, 0, a, (int)(it & 1), (int)it);
+        GG_LAUNCH(k_pja_lean, dim3(grid_for(a.n, ls.pja_block)), ls.pja_block, 0, a, (int)(it & 1), (int)it, rev);
       else
-        GG_LAUNCH(k_pja<false>, dim3(grid_for(a.n, ls.pja_block)), ls.pja_block, 0, a, (int)(it & 1), none, (int)it);
+        GG_LAUNCH(k_pja<false>, dim3(grid_for(a.n, ls.pja_block)), ls.pja_block, 0, a, (int)(it & 1), none, (int)it,
+                  rev);
     }
     if (a.F) GG_LAUNCH(k_free_update, dim3(a.F), 256, 0, a);
   }
@@ -1481,7 +1594,9 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
     return cudaGetLastError();
   }
   GG_MARK(3);
-  if (a.n_chunks) GG_LAUNCH(k_integrate_wrench, dim3(a.n_chunks), kIntegrateThreads, 0, a, (int)(ls.iters & 1));
+  if (a.n_chunks)
+    GG_LAUNCH(k_integrate_wrench, dim3(a.n_chunks), kIntegrateThreads, 0, a, (int)(ls.iters & 1),
+              (int)(ls.serp && ls.iters % 2 == 0));
   GG_LAUNCH(k_wrench_bodies, dim3(nbt), kWrenchBodyThreads, 0, a);
   GG_MARK(4);
 #undef GG_LAUNCH
@@ -1505,6 +1620,17 @@ cudaError_t enqueue_sort_from_keys(const StepArgs &a, cudaStream_t st) {
 int fused_pja_blocks_per_sm(int block) {
   int per = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pja_fused, block, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return per;
+}
+
+int detect_sweeps_blocks_per_sm(bool lists, uint32_t K) {
+  int per = 0;
+  const size_t smem = (size_t)K * kDetectSweepBlock * sizeof(uint32_t);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, lists ? k_detect_sweeps<true> : k_detect_sweeps<false>,
+                                                    kDetectSweepBlock, smem) != cudaSuccess) {
     (void)cudaGetLastError();
     return 0;
   }

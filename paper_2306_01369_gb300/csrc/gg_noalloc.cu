@@ -122,15 +122,19 @@ __global__ void na_scatter(const uint32_t *key, uint32_t n, const uint32_t *star
   slots[start[k] + atomicSub(&cnt[k], 1u) - 1u] = i;
 }
 
-// ascending id inside each bucket
+// ascending id inside each bucket; a bucket above GG_NOALLOC_MAX_OCCUPANCY keeps the
+// scatter's order (the rank would cost its occupancy per member)
 __global__ void na_rank(const uint32_t *key, uint32_t n, const uint32_t *start, const uint32_t *slots, uint32_t *perm) {
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const uint32_t id = slots[s];
   const uint32_t k = key[id];
   const uint32_t b0 = start[k], b1 = start[k + 1];
-  uint32_t r = 0;
-  for (uint32_t t = b0; t < b1; ++t) r += slots[t] < id ? 1u : 0u;
+  uint32_t r = s - b0;
+  if (b1 - b0 <= GG_NOALLOC_MAX_OCCUPANCY) {
+    r = 0;
+    for (uint32_t t = b0; t < b1; ++t) r += slots[t] < id ? 1u : 0u;
+  }
   perm[b0 + r] = id;
 }
 

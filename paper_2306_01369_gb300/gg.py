@@ -45,6 +45,7 @@ SIGNATURES = {
     "gg_set_state": (C.c_int, [_P, _P, C.c_size_t, C.c_int, _P]),
     "gg_tuning_count": (C.c_uint32, []),
     "gg_hash_size": (C.c_uint32, [_P, C.c_uint32]),
+    "gg_cell_size": (C.c_float, [_P, C.c_uint32]),
     "gg_tuning_flags": (C.c_uint32, [C.c_uint32]),
     "gg_enable_timing": (C.c_int, [_P, C.c_int]),
     "gg_stage_ms": (C.c_int, [_P, C.POINTER(C.c_float)]),
@@ -67,7 +68,7 @@ class GGParams(C.Structure):
                 ("tuning", C.c_uint32), ("wrench_history", C.c_uint32), ("max_free_bodies", C.c_uint32),
                 ("free_contact_capacity", C.c_uint32), ("barrier_test_phantoms", C.c_uint32),
                 ("binning", C.c_uint32), ("cyclic_z", C.c_float * 2), ("wait_limit_us", C.c_uint32),
-                ("hash_tune", C.c_uint32)]
+                ("hash_tune", C.c_uint32), ("pja_weight", C.c_uint32)]
 
 
 class GGBody(C.Structure):
@@ -123,7 +124,7 @@ def load():
     return _lib
 
 
-TUNE_BITS = {"lists": 1, "fused": 2, "lean": 4, "half": 8}   # GG_TUNE_* of gg.h
+TUNE_BITS = {"lists": 1, "fused": 2, "lean": 4, "half": 8, "detect": 16, "serp": 32}   # GG_TUNE_* of gg.h
 
 
 def tuning_flags(k):
@@ -186,6 +187,7 @@ def make_params(p, tuning=0, wrench_history=1, max_bodies=8, hash_factor=0, max_
     q.binning = binning
     q.wait_limit_us = wait_limit_us
     q.hash_tune = hash_tune
+    q.pja_weight = int(getattr(p, "pja_weight", 0))
     cz = getattr(p, "cyclic_z", (0.0, 0.0))
     q.cyclic_z[0], q.cyclic_z[1] = cz[0], cz[1]
     return q
@@ -353,6 +355,10 @@ class Sim:
     def hash_size(self, env=0):
         """n_h in use for environment `env` (Eq. 6's modulus)."""
         return self._L.gg_hash_size(self.h, env)
+
+    def cell_size(self, env=0):
+        """Cell edge in use for environment `env` (the grid of Eq. 6's keys)."""
+        return float(self._L.gg_cell_size(self.h, env))
 
     def read(self, field, dtype=np.float32, shape=None, out=None, stream=None, check=True):
         nb = self.field_bytes(field)

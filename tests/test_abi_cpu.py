@@ -44,7 +44,7 @@ def test_library_exports_nothing_else():
 
 
 def test_host_only_calls(lib):
-    assert lib.gg_abi_version() == 1
+    assert lib.gg_abi_version() == 2
     assert lib.gg_status_string(0) == b"ok"
     assert lib.gg_status_string(4) == b"contact capacity overflow"
     assert lib.gg_tuning_count() >= 2
@@ -62,12 +62,14 @@ def test_tuning_sets_cover_every_variant():
     for v in ("lean", "half"):
         assert {v} in sets and {v, "lists"} in sets
     assert {"fused"} in sets
+    assert {"detect"} in sets and {"detect", "lists"} in sets
+    assert {"serp"} in sets and {"serp", "lists"} in sets and {"serp", "lists", "half"} in sets
 
 
 def test_struct_sizes_match_header():
     """The ctypes mirrors must have the C layout (4-byte fields and arrays)."""
     from paper_2306_01369_gb300 import gg
-    assert ctypes.sizeof(gg.GGParams) == 4 * 25
+    assert ctypes.sizeof(gg.GGParams) == 4 * 26
     assert ctypes.sizeof(gg.GGBody) == 4 * (2 + 12 + 3 + 4 + 3 + 3 + 1 + 3)
     assert ctypes.sizeof(gg.GGStats) == 8 + 4 * 6
     assert ctypes.sizeof(gg.GGCamera) == 4 * 20
