@@ -50,7 +50,9 @@ def workload_config(sc, workload="column"):
                 "bed": "128x128x64 sites, settled 3000 steps under the parked scoop",
                 "bodies": "container, kinematic scoop on 6 waypoints, 2 free 3 cm cubes"}
     if workload == "batched":
-        return {"workload": "batched_beds_256", **base, "envs": len(sc.env_offsets) - 1,
+        return {"workload": f"batched_beds_{sc.info.get('envs_total', len(sc.env_offsets) - 1)}", **base,
+                "envs": len(sc.env_offsets) - 1,
+                "envs_total": sc.info.get("envs_total", len(sc.env_offsets) - 1),
                 "bed": "16 layers per environment, settled 1500 steps under the parked tools",
                 "bodies": "container + scoop per environment"}
     return {"workload": WORKLOAD, **base, "radius_m": "2e-3 +-10%", "column_sites": "40x40x164",
@@ -63,7 +65,16 @@ def hash_kw(args):
     return dict(hash_factor=args.hash_factor) if args.hash_factor else dict(hash_tune=1)
 
 
-def setup_workload(args, scenes, gg, rank, stream):
+def batched_shard(scenes, world, rank, n_steps, n_envs=256):
+    """This rank's part of the batched workload: every rank builds the same 256 (or
+    n_envs) seeded environments and keeps the subset shard_envs gives it (balanced by
+    particle count); the environments never interact, so no collective touches the
+    data path."""
+    from paper_2306_01369_gb300.shard import shard_scene
+    return shard_scene(scenes.batched_beds(n_envs=n_envs, seed=1003, n_steps=n_steps), world, rank)
+
+
+def setup_workload(args, scenes, gg, rank, stream, world=1):
     """(scene, simulation, untimed steps before the warm-up) of the timed workload."""
     if args.workload == "column":
         sc = scenes.column_collapse(seed=1001 + rank)
@@ -78,7 +89,7 @@ def setup_workload(args, scenes, gg, rank, stream):
         sc = scenes.excavation(n=1048576, seed=1002 + rank, n_steps=n_run)
         settle = 3000
     else:
-        sc = scenes.batched_beds(n_envs=256, seed=1003 + rank, n_steps=n_run)
+        sc = batched_shard(scenes, world, rank, n_run, args.envs)
         settle = 1500
     parked = scenes.Scene(sc.name, sc.pos_r, sc.vel, sc.mass, sc.bodies, sc.params, sc.n_steps,
                           env_offsets=sc.env_offsets, body_offsets=sc.body_offsets)
@@ -228,6 +239,8 @@ PROFILE_WORKLOAD = {"column": "column_collapse", "excavation": "excavation", "ba
 def stage_kernels(flags):
     """(sweep kernel, contact-stage kernels) that a launch-shape set with GG_TUNE_* names
     `flags` runs."""
+    if "detect" in flags:                 # one launch holds the contact stage and the sweeps
+        return "k_detect_sweeps", "k_detect_sweeps"
     sweep = "k_pja_fused" if "fused" in flags else ("k_pja_lean" if "lean" in flags else "k_pja")
     contacts = "k_pairs_half+k_pairs_finish" if "half" in flags else "k_contacts"
     return sweep, contacts
@@ -238,6 +251,8 @@ def profile_traffic(kernel: str, workload: str, kernel_digest: str):
     committed profile summary ("key: value" lines) on this workload, if it was taken on
     the current kernel source (else None)."""
     stem = kernel.split("+")[0]
+    if workload not in PROFILE_WORKLOAD:
+        return None
     path = os.path.join(ROOT, "profiles", f"{stem}_{PROFILE_WORKLOAD[workload]}.txt")
     try:
         kv = {}
@@ -269,13 +284,29 @@ def kernel_digest() -> str:
 # arms
 # --------------------------------------------------------------------------- #
 
-def oracle_sample(sc, state_pos, state_vel, seconds=15.0, max_steps=2000, threads=None):
-    """Time the FP64 oracle, as it stands, on the workload: whole steps of all n
-    particles from the generator's initial state until `seconds` have passed (at
-    least one step).  Oracle inputs never come from the CUDA path."""
+ORACLE_BLOCK = 16384     # spheres of the column's bottom layers the oracle steps
+ORACLE_PREROLL = 800     # untimed oracle steps first: the block lands and its contacts form
+
+
+def column_block(sc, m=ORACLE_BLOCK):
+    """The lowest m spheres of the column (its bottom layers: the lattice is z-major),
+    as a scene of their own with the same recipe; the oracle's bounded sample."""
+    from paper_2306_01369_gb300 import scenes
+    return scenes.Scene(f"{sc.name}_bottom{m}", sc.pos_r[:m].copy(), sc.vel[:m].copy(), sc.mass[:m].copy(),
+                        sc.bodies, sc.params, sc.n_steps)
+
+
+def oracle_sample(sc, seconds=15.0, max_steps=4000, threads=None):
+    """Time the FP64 oracle, as it stands, on a bounded sample of the workload: the
+    column's bottom block, advanced ORACLE_PREROLL steps untimed from the generator's
+    state (it lands and packs against the ground), then whole steps until `seconds`
+    have passed.  Oracle inputs never come from the CUDA path."""
     import oracle
     threads = threads or os.cpu_count() or 1
-    o = oracle.Sim(state_pos, state_vel, sc.mass, sc.bodies, sc.params, n_threads=threads)
+    blk = column_block(sc)
+    o = oracle.Sim(blk.pos_r, blk.vel, blk.mass, blk.bodies, blk.params, n_threads=threads)
+    o.step(ORACLE_PREROLL)
+    x0, v0 = o.x.copy(), o.v.copy()
     steps, t0 = 0, time.perf_counter()
     while steps < max_steps:
         o.step(1)
@@ -283,11 +314,17 @@ def oracle_sample(sc, state_pos, state_vel, seconds=15.0, max_steps=2000, thread
         if time.perf_counter() - t0 >= seconds:
             break
     el = time.perf_counter() - t0
-    one = _oracle_rate(sc, state_pos, state_vel, 1, threads=1)
-    return {"value": sc.n * steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"the first {steps} time steps of {sc.name} ({sc.n} spheres) from its initial state "
-                      f"(FP64 C oracle, {threads} OpenMP threads); {el:.1f} s",
-            "single_core_value": one["value"], "single_core_sample": one["sample"]}
+    cbar = o.stats.n_pp / blk.n
+    o1 = oracle.Sim(blk.pos_r, blk.vel, blk.mass, blk.bodies, blk.params, n_threads=1)
+    o1.set_state(x0, v0)
+    t1 = time.perf_counter()
+    o1.step(5)
+    one = blk.n * 5 / (time.perf_counter() - t1)
+    return {"value": blk.n * steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{steps} time steps of the column's bottom {blk.n} spheres (same recipe) after "
+                      f"{ORACLE_PREROLL} untimed ones (landed; {cbar:.2f} pair contacts per sphere at the end), "
+                      f"FP64 C oracle, {threads} OpenMP threads; {el:.1f} s",
+            "single_core_value": one, "single_core_sample": "5 steps of the same block from the same state, 1 thread"}
 
 
 def _oracle_rate(sc, pos, vel, steps, threads=None):
@@ -312,12 +349,12 @@ def run_reference(args):
     oracle.build()
     sc = scenes.column_collapse()
     threads = os.cpu_count() or 1
-    # bounded sample per step: a contiguous block of the column (its lowest layers,
-    # where contacts form first), advanced one oracle time step
-    m = 16384
-    sub_pos = sc.pos_r[:m].copy()
-    sub_vel = sc.vel[:m].copy()
-    o = oracle.Sim(sub_pos, sub_vel, sc.mass[:m], sc.bodies, sc.params, n_threads=threads)
+    # bounded sample per step: the column's bottom block (same recipe), landed first
+    # (ORACLE_PREROLL untimed steps), then one oracle time step per step
+    blk = column_block(sc)
+    m = blk.n
+    o = oracle.Sim(blk.pos_r, blk.vel, blk.mass, blk.bodies, blk.params, n_threads=threads)
+    o.step(ORACLE_PREROLL)
     for _ in range(args.warmup):
         o.step(1)
     t0 = time.perf_counter()
@@ -325,13 +362,16 @@ def run_reference(args):
         o.step(1)
     el = time.perf_counter() - t0
     v = m * args.steps / el
+    cfg = workload_config(sc)
+    cfg.update(n_particles=m, sample=f"the column's bottom {m} spheres (of {sc.n}), landed: "
+                                     f"{ORACLE_PREROLL} untimed steps before the warm-up")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(sc),
+            "config": cfg, "contacts_per_particle": o.stats.n_pp / m,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"each step: one FP64 oracle time step of the lowest {m} spheres of the "
-                                       f"column (same recipe), {threads} OpenMP threads"},
+                             "sample": f"each step: one FP64 oracle time step of the column's bottom {m} spheres "
+                                       f"(same recipe, landed), {threads} OpenMP threads"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -356,21 +396,32 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
     from paper_2306_01369_gb300.autograd import rollout, scoop_mass
     out = {}
     t_start = time.perf_counter()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     # the column's pile: 262,144 spheres run for 20,000 steps (1 s; the collapse is still
-    # creeping then), repose angle and centre of mass of what it has become
+    # creeping then), repose angle and centre of mass of what it has become; then the
+    # throughput and rooflines of 200 steps of that densely packed pile
     from paper_2306_01369_gb300.stats import pile_statistics
     col = scenes.column_collapse()
-    sim = gg.Sim.from_scene(col)
+    sim = gg.Sim.from_scene(col, hash_tune=1)
     sim.step(20000, stream=stream)
     sim.sync(stream)
     pv = sim.pos_vel()
     ke = 0.5 * float((col.mass * (pv[1].astype(np.float64) ** 2).sum(1)).sum())
     angle, com, nbins = pile_statistics(pv[0][:, :3], col.mass, float(col.pos_r[:, 3].max()))
+    sim.autotune(stream)                  # the packed pile, not the lattice, decides
+    for w in range(4):
+        sim.enable_timing(w % 2 == 1)
+        sim.step(1, stream=stream)
+    md = measure(sim, col, 200, stream, torch, flush, workload="column_pile")
+    dense = {"particle_steps_per_s": col.n * 200 / (md["total_ms"] * 1e-3), "ms_per_step": md["total_ms"] / 200,
+             "contacts_per_particle": md["contacts_per_particle"], "tuning_set": sim.tuning_selected,
+             "hash_table": f"n_h = {sim.hash_size(0) / col.n:.0f} n", "roofline": md["roofline"],
+             "roofline_next": md["roofline_next"], "timed_steps": [20004, 20204]}
     sim.close()
     out["column_pile"] = {"workload": "column collapse 262,144, mu 0.6, after 20,000 steps (1 s)",
                           "repose_angle_deg": angle, "centre_of_mass_m": [float(c) for c in com],
                           "initial_height_m": float(col.pos_r[:, 2].max()), "fit_bins": nbins,
-                          "kinetic_energy_j": ke}
+                          "kinetic_energy_j": ke, "dense_steps": dense}
     # small settle: 4,096 spheres in an open box, 200 steps (the oracle runs it whole)
     ss = scenes.settle_box(n=4096, n_steps=200)
     sim = gg.Sim.from_scene(ss, hash_tune=1)
@@ -533,12 +584,19 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
     if time.perf_counter() - t_start < seconds_cap:
         ex = scenes.excavation(n=1048576, n_steps=steps_exc + 20)
         parked = scenes.Scene(ex.name, ex.pos_r, ex.vel, ex.mass, ex.bodies, ex.params, ex.n_steps)
-        sim = gg.Sim.from_scene(parked, wrench_history=steps_exc, hash_tune=1)
+        sim = gg.Sim.from_scene(parked, wrench_history=1, hash_tune=1)
         sim.step(settle_steps_exc, stream=stream)   # the bed settles under the parked scoop
         sim.autotune(stream)
         sim.set_trajectory(1, ex.twist[1])
-        sim.step(10, stream=stream)
-        ms = _timed_steps(sim, steps_exc, stream, torch)
+        for w in range(10):
+            sim.enable_timing(w % 2 == 1)
+            sim.step(1, stream=stream)
+        # every step: the step, then its body wrenches (force readback, Sec. III-C) copied
+        # into pinned host memory and waited for, as a controller reading forces would
+        wr_h = torch.empty(sim.n_envs * sim.max_bodies * 6, dtype=torch.float32).pin_memory()
+        me = measure(sim, ex, steps_exc, stream, torch, flush, workload="excavation",
+                     readback=lambda k: sim.read("BODY_WRENCH", out=wr_h, stream=stream))
+        ms = me["total_ms"]
         sim.sync(stream)
         st = sim.stats()
         # the observations of one step: sky camera over the whole bed, ego camera from the
@@ -565,10 +623,15 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
         cams = {"sky_72x36_us": 1e3 * e0.elapsed_time(e1) / 20, "ego_36x36_us": 1e3 * e1.elapsed_time(e2) / 20,
                 "ego_pixels_hit": int((img_e < 1.5).sum())}
         out["excavation"] = {"workload": f"1,048,576 spheres, scoop + 2 free cubes + container, I=30, bed settled "
-                                         f"for {settle_steps_exc} steps before the scoop digs", "cameras": cams,
+                                         f"for {settle_steps_exc} steps before the scoop digs; every timed step "
+                                         f"includes its wrench readback to pinned host memory (waited for)",
+                             "cameras": cams,
                              "particle_steps_per_s": ex.n * steps_exc / (ms * 1e-3), "ms_per_step": ms / steps_exc,
                              "timed_steps": [10, 10 + steps_exc], "n_pp_last": st["n_pp"], "n_body_last": st["n_body"],
-                             "mean_pp_per_particle": st["n_pp"] / ex.n}
+                             "contacts_per_particle": me["contacts_per_particle"], "tuning_set": sim.tuning_selected,
+                             "hash_table": f"n_h = {sim.hash_size(0) / ex.n:.0f} n",
+                             "roofline": me["roofline"], "roofline_next": me["roofline_next"],
+                             "wrench_readback_bytes_per_step": int(wr_h.numel() * 4)}
         sim.close()
         if time.perf_counter() - t_start < seconds_cap:   # the oracle on the generator's (unsettled) bed
             orc = _oracle_rate(ex, ex.pos_r, ex.vel, 2)
@@ -578,6 +641,73 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
 
 
 SAMPLE_EVERY = 10   # one timed step in ten carries the stage-timing events (they cost ~18 us)
+
+
+def table_buckets(sim, sc):
+    """Buckets of the hash tables in use (sum over environments)."""
+    E = len(sc.env_offsets) - 1 if sc.env_offsets is not None else 1
+    return sum(sim.hash_size(e) for e in range(E))
+
+
+def measure(sim, sc, steps, stream, torch, flush, workload="column", readback=None):
+    """Time `steps` steps of `sim` (events on the library's stream around each step, the
+    L2 flushed between steps outside them); every SAMPLE_EVERY-th step carries the stage
+    events, from which the sweep's and the contact stage's live durations and, with the
+    step's contact counts, their algorithmic bytes come.  readback(k), if given, runs
+    after each step inside its events (a per-step host readback).  Returns step times,
+    the roofline of the kernel with the larger share and of the other, and the mean
+    number of particle-particle contacts per particle over the sampled steps."""
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    pja_ms, pja_b, con_ms, con_b = 0.0, 0, 0.0, 0
+    sampled, cbar, st = [], [], None
+    H = table_buckets(sim, sc)
+    for k in range(steps):
+        inst = k % SAMPLE_EVERY == 0
+        sim.enable_timing(inst)                   # selects the step graph (both already captured)
+        flush.fill_(float(k))                     # evict L2 between timed steps (outside the events)
+        ev0[k].record(stream)
+        sim.step(1, stream=stream)
+        if readback is not None:
+            readback(k)
+        ev1[k].record(stream)
+        if inst:
+            st = sim.stage_ms()                   # waits for this step
+            pja_ms += st["pja"]
+            con_ms += st["contacts"]
+            c = sim.stats()
+            pja_b += sc.params.pja_iters * pja_bytes(sc.n, c["n_pp"], c["n_body"])
+            con_b += contacts_bytes(sc.n, c["n_pp"], c["n_body"], H)
+            cbar.append(c["n_pp"] / sc.n)
+            sampled.append(k)
+    torch.cuda.synchronize()
+    sim.enable_timing(False)
+    step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
+    sampled_ms = sum(step_ms[k] for k in sampled)
+    peak, peak_kind = measured_peaks()
+    digest = kernel_digest()
+
+    def roof(kernel, total_ms, total_bytes, launches):
+        avg_s = total_ms * 1e-3 / launches
+        per_launch = total_bytes / launches
+        achieved = per_launch / avg_s / 1e9
+        return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy), burst",
+                "traffic": profile_traffic(kernel, workload, digest), "bytes_per_launch": per_launch,
+                "avg_launch_us": avg_s * 1e6, "share_of_step": total_ms / sampled_ms,
+                "sampled_steps": len(sampled)}
+
+    sweep_kernel, contact_kernels = stage_kernels(sim.tuning_flags)
+    if sweep_kernel == contact_kernels:   # detection and sweeps in one launch per step
+        roofs = [roof(sweep_kernel, pja_ms + con_ms, pja_b + con_b, len(sampled)), None]
+    else:
+        sweep_launches = len(sampled) * (1 if sweep_kernel == "k_pja_fused" else sc.params.pja_iters)
+        roofs = [roof(sweep_kernel, pja_ms, pja_b, sweep_launches),
+                 roof(contact_kernels, con_ms, con_b, len(sampled))]
+        roofs.sort(key=lambda r: -r["share_of_step"])
+    return {"step_ms": step_ms, "total_ms": sum(step_ms), "roofline": roofs[0], "roofline_next": roofs[1],
+            "contacts_per_particle": float(np.mean(cbar)) if cbar else 0.0, "stage_ms_last_sampled_step": st,
+            "table_buckets": H}
 
 
 def run_gpu(args):
@@ -599,7 +729,7 @@ def run_gpu(args):
     # untimed pre-roll (the column: so that the timed window sits in the middle of the
     # 2000-step collapse; the beds: settling), then the warm-up, which alternates the
     # plain and the instrumented step graphs so that both are captured before timing
-    sc, sim, preroll = setup_workload(args, scenes, gg, rank, stream)
+    sc, sim, preroll = setup_workload(args, scenes, gg, rank, stream, world)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for w in range(max(args.warmup, 2)):
         sim.enable_timing(w % 2 == 1)
@@ -609,62 +739,20 @@ def run_gpu(args):
 
     clocks = ClockSampler(local)
     clocks.start()
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    step_ms, pja_ms, pja_bytes_tot, con_ms, con_bytes_tot = [], 0.0, 0, 0.0, 0
-    sampled = []   # timed steps that carry the stage events (every SAMPLE_EVERY-th)
-    st = None
     barrier(world)
     torch.cuda.synchronize(dev)
     torch.cuda.nvtx.range_push("timed")     # lets ncu --nvtx-include "timed/" select the timed steps
-    for k in range(args.steps):
-        inst = k % SAMPLE_EVERY == 0
-        sim.enable_timing(inst)                   # selects the step graph (both already captured)
-        flush.fill_(float(k))                     # evict L2 between timed steps (outside the events)
-        ev0[k].record(stream)
-        sim.step(1, stream=stream)
-        ev1[k].record(stream)
-        if inst:
-            st = sim.stage_ms()                   # waits for this step
-            pja_ms += st["pja"]
-            con_ms += st["contacts"]
-            s = sim.stats()
-            pja_bytes_tot += sc.params.pja_iters * pja_bytes(sc.n, s["n_pp"], s["n_body"])
-            con_bytes_tot += contacts_bytes(sc.n, s["n_pp"], s["n_body"], 2 * sc.n)
-            sampled.append(k)
-    torch.cuda.synchronize(dev)
+    m = measure(sim, sc, args.steps, stream, torch, flush, workload=args.workload)
     torch.cuda.nvtx.range_pop()
     barrier(world)
     clk = clocks.stop()
-    sim.enable_timing(False)
-    for k in range(args.steps):
-        step_ms.append(ev0[k].elapsed_time(ev1[k]))
-    sampled_ms = sum(step_ms[k] for k in sampled)
-    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    total_ms = max_over_ranks(m["total_ms"], world, dev)
     sim.sync(stream)
     stats = sim.stats()
     value = sum_over_ranks(float(sc.n * args.steps), world, dev) / (total_ms * 1e-3)
-
-    # roofline of the dominant kernel (largest share of the timed steps), the other beside it
-    peak, peak_kind = measured_peaks()
-    digest = kernel_digest()
-
-    def roof(kernel, total_ms, total_bytes, launches):
-        avg_s = total_ms * 1e-3 / launches
-        per_launch = total_bytes / launches
-        achieved = per_launch / avg_s / 1e9
-        return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy), burst",
-                "traffic": profile_traffic(kernel, args.workload, digest), "bytes_per_launch": per_launch,
-                "avg_launch_us": avg_s * 1e6, "share_of_step": total_ms / sampled_ms,
-                "sampled_steps": len(sampled)}
-
-    sweep_kernel, contact_kernels = stage_kernels(sim.tuning_flags)
-    sweep_launches = len(sampled) * (1 if sweep_kernel == "k_pja_fused" else sc.params.pja_iters)
-    roofs = [roof(sweep_kernel, pja_ms, pja_bytes_tot, sweep_launches),
-             roof(contact_kernels, con_ms, con_bytes_tot, len(sampled))]
-    roofs.sort(key=lambda r: -r["share_of_step"])
-    roof_main, roof_other = roofs
+    n_envs_rank = len(sc.env_offsets) - 1 if sc.env_offsets is not None else 1
+    env_steps = sum_over_ranks(float(n_envs_rank * args.steps), world, dev) / (total_ms * 1e-3)
+    roof_main, roof_other, st = m["roofline"], m["roofline_next"], m["stage_ms_last_sampled_step"]
 
     # end to end through the public API with host buffers: H2D of the state, one
     # step, D2H of the new state, every step; on the same window of the workload as the
@@ -672,7 +760,7 @@ def run_gpu(args):
     tuning_sel, nh0, kps = sim.tuning_selected, sim.hash_size(0), sim.kernels_per_step
     sim.close()
     e2e_steps = min(args.steps, args.e2e_steps or args.steps)
-    _, sim, _ = setup_workload(args, scenes, gg, rank, stream)
+    _, sim, _ = setup_workload(args, scenes, gg, rank, stream, world)
     sim.step(max(args.warmup, 2), stream=stream)
     state_h = torch.empty(7 * sc.n, dtype=torch.float32).pin_memory()   # positions (n, 4), velocities (n, 3)
     sim.read("POS_VEL", out=state_h, stream=stream)
@@ -690,7 +778,7 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and sc.env_offsets is None:
-        cpu = oracle_sample(sc, sc.pos_r, sc.vel, seconds=args.cpu_seconds)
+        cpu = oracle_sample(sc, seconds=args.cpu_seconds)
     xtra = None
     if rank == 0 and world == 1 and not args.no_extras and args.workload == "column":
         xtra = extras(torch, dev, stream)
@@ -700,13 +788,18 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {**workload_config(sc, args.workload), "replicas": world, "tuning_set": tuning_sel,
+                "config": {**workload_config(sc, args.workload),
+                           "parallelism": (f"environments sharded over {world} ranks (no data-path collective)"
+                                           if sc.env_offsets is not None else f"{world} independent replicas"),
+                           "tuning_set": tuning_sel,
                            "hash_table": f"n_h = {nh0 / n_env0:.0f} n per environment "
                                          f"({'fixed' if args.hash_factor else 'autotuned among 2n, 4n, 8n'})",
                            "timed_steps": window},
+                "contacts_per_particle": m["contacts_per_particle"],
                 "roofline": roof_main, "roofline_next": roof_other, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "steps": e2e_steps, "window": [window[0], window[0] + e2e_steps],
                         "h2d_bytes_per_step": sc.n * (16 + 12), "d2h_bytes_per_step": sc.n * (16 + 12)},
+                "env_steps_per_s": env_steps if sc.env_offsets is not None else None,
                 "gpu_launches": kps * args.steps, "clocks": clk,
                 "stage_ms_last_sampled_step": st,
                 "contacts_last_step": {"n_pp": stats["n_pp"], "n_body": stats["n_body"],
@@ -734,6 +827,8 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / adjoint / excavation figures")
+    ap.add_argument("--envs", type=int, default=256,
+                    help="environments of the batched workload (256; fewer only to profile a smaller case)")
     ap.add_argument("--workload", choices=["column", "excavation", "batched"], default="column",
                     help="the timed workload (column: the headline; the others for profiling at sizes that "
                          "do not fit in L2)")

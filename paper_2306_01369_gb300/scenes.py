@@ -271,6 +271,32 @@ def pile_column(member=-1, n=32768, dims=(24, 24, 57), mu=0.2, n_steps=20000):
     return sc
 
 
+def pour_pile(member=-1, n=32768, mu=0.6, n_steps=20000, spread=2.0, side=24, seed=1005):
+    """A pile poured onto a ground plane: n spheres (r = 2 mm +-10 %) scattered loosely
+    (a jittered lattice of pitch `spread` x 2.04 r_max, sites inside the inscribed
+    circle of a side x side footprint, z-major) fall, land over some 0.2 s and heap up
+    at the friction of the column workload (mu = 0.6); dt = 5e-5 s, 20 PJA iterations.
+    A column released at mu = 0.6 stands jammed for thousands of steps and creeps for
+    longer than the oracle can follow, while a loose rain of spheres forms a heap whose
+    slope has settled by 15,000 steps (0.75 s; the flank then creeps at ~2 mm/s, the
+    angle by about 0.1 degree per 5,000 steps).  Member k >= 0 moves the x of every
+    sphere with index % 8 == k by one float32 ulp towards +inf (-1: unperturbed)."""
+    r0, jit = 2e-3, 0.10
+    pitch = 2.0 * r0 * (1 + jit) * 1.02 * spread
+    nz = -(-2 * n // (side * side)) + 8
+    pr, _ = jittered_lattice((side, side, nz), side * side * nz, r0, jit, seed,
+                             origin=(-0.5 * side * pitch, -0.5 * side * pitch, 0.0), pitch=pitch)
+    rad = np.hypot(pr[:, 0], pr[:, 1])
+    pr = np.ascontiguousarray(pr[rad <= 0.5 * side * pitch - 0.5 * pitch][:n])
+    assert pr.shape[0] == n
+    if member >= 0:
+        sel = np.arange(n) % 8 == member
+        pr[sel, 0] = np.nextafter(pr[sel, 0], np.float32(np.inf))
+    ground = Body(kind=PLANE, pos=(0.0, 0.0, 0.0))
+    return Scene(f"pour_pile_{n}_m{member}", pr, np.zeros((n, 3), np.float32), sphere_mass(pr[:, 3]), [ground],
+                 Params(dt=5e-5, mu=mu, pja_iters=20), n_steps, info={"spread": spread, "side": side})
+
+
 def _bed_env(n, r0, jit, seed, side=None, layers=None, n_steps=500, dt=1e-4, scoop_scale=1.0,
              tool_seed=None, margin=0.005):
     """A bed of n spheres in an open container, plus a kinematic scoop on a seeded

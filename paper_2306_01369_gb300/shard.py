@@ -39,3 +39,31 @@ def subset_offsets(env_offsets, envs):
     sizes = [int(env_offsets[e + 1] - env_offsets[e]) for e in envs]
     offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint32)
     return idx, offs
+
+
+def shard_scene(sc, world: int, rank: int):
+    """The environments of a batched scene that rank `rank` of `world` steps: the
+    shard_envs subset, with its particles, bodies and tool trajectories compacted
+    into a batched scene of its own (every rank builds the same full scene from the
+    same seed, so the subsets partition it).  A scene without environments is
+    returned unchanged (it does not shard)."""
+    from . import scenes as S
+    if sc.env_offsets is None:
+        return sc
+    E = len(sc.env_offsets) - 1
+    sizes = np.diff(np.asarray(sc.env_offsets, np.int64))
+    envs = shard_envs(sizes, world)[rank]
+    idx, offs = subset_offsets(sc.env_offsets, envs)
+    bo = np.asarray(sc.body_offsets, np.int64)
+    bodies, boffs, twist = [], [0], {}
+    for e in envs:
+        b0, b1 = int(bo[e]), int(bo[e + 1])
+        for gb in range(b0, b1):
+            if gb in sc.twist:
+                twist[len(bodies) + gb - b0] = sc.twist[gb]
+        bodies.extend(sc.bodies[b0:b1])
+        boffs.append(len(bodies))
+    info = dict(sc.info)
+    info.update(envs=envs, shard=f"{rank}/{world}", envs_total=E)
+    return S.Scene(f"{sc.name}_shard{rank}of{world}", sc.pos_r[idx], sc.vel[idx], sc.mass[idx], bodies, sc.params,
+                   sc.n_steps, twist=twist, env_offsets=offs, body_offsets=np.asarray(boffs, np.uint32), info=info)

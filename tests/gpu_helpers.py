@@ -75,20 +75,79 @@ def lockstep_pair(gg, scene, k, n_threads=8, **sim_kw):
 EPS32 = 2.0 ** -24
 
 
-def vel_tol(scene, v_orc, length=None):
-    """Tolerance of one-step velocities, GPU (FP32) vs oracle (FP64), from the same
-    FP32 state: 1e-5 of the scene's velocity scale max(max_i |v_i|, g dt), plus the
-    FP32 floor of the Baumgarte bias.  psi = (r_i + r_j) - |x_i - x_j| evaluated in
-    FP32 carries up to ~8 eps32 * L of rounding (L = 2 r_max for particle pairs, the
-    body-frame coordinate scale for SDF contacts), which the bias alpha psi / dt turns
-    into (alpha / dt) 8 eps32 L of velocity."""
+def body_scale(body, x):
+    """Body-frame coordinate scale of a particle at x in contact with `body`: the size
+    of the FP32 numbers the SDF query rounds (|x - p|, plus a grid's sampled extent,
+    whose cell coordinates are measured from its origin)."""
+    L = float(np.linalg.norm(np.asarray(x, np.float64) - np.asarray(body.pos, np.float64)))
+    g = getattr(body, "grid", None)
+    if g is not None:
+        ext = float(np.linalg.norm(g.origin)) + float(g.spacing) * float(max(g.values.shape))
+        L += ext
+    return L
+
+
+def vel_tol(scene, v_orc, contacts, x=None, per_contact=False):
+    """Per-particle tolerance of one-step velocities, GPU (FP32) vs oracle (FP64), from
+    the same FP32 state: 1e-5 of the particle's own speed (at least g dt), plus the FP32
+    floor of the Baumgarte bias of the contacts it has.  psi evaluated in FP32 carries up
+    to ~8 eps32 L of rounding, L = the size of the coordinates it is computed from:
+    2 r_max for a particle pair (|x_i - x_j| <= r_i + r_j), the body-frame coordinate
+    scale for an SDF contact (particles with a body contact, and their direct partners);
+    the bias alpha psi / dt turns that into (alpha / dt) 8 eps32 L of velocity.
+    `contacts`: the oracle's contact lists of the step's start state; x: its positions.
+    per_contact: the floor once per contact of the particle (weightings that hand a
+    particle each contact's whole correction, Alg. 1 as printed)."""
     p = scene.params
-    vscale = max(float(np.abs(v_orc).max()), 9.81 * p.dt)
-    L = 2.0 * float(scene.pos_r[:, 3].max()) if length is None else length
-    return 1e-5 * vscale + (p.alpha / p.dt) * 8.0 * EPS32 * L
+    v_orc = np.asarray(v_orc, np.float64)
+    n = v_orc.shape[0]
+    x = scene.pos_r[:, :3] if x is None else x
+    scale = np.maximum(np.linalg.norm(v_orc, axis=1), 9.81 * p.dt)
+    Lb = np.full(n, 2.0 * float(scene.pos_r[:, 3].max()))
+    off, bb = contacts["bc_off"], contacts["bc_b"]
+    for i in np.nonzero(np.diff(off.astype(np.int64)))[0]:
+        for b in bb[off[i]:off[i + 1]]:
+            Lb[i] = max(Lb[i], body_scale(scene.bodies[int(b)], x[i]))
+    # a Jacobi sweep hands a particle part of each partner's estimate, so a partner's
+    # body-contact rounding reaches it too (attenuated by the mass-splitting weight, about
+    # 1 / (n_i + n_j) per hop): the floor of a particle is the largest of its own and its
+    # partners' scales (one hop)
+    L = Lb.copy()
+    po, pj = contacts["pp_off"].astype(np.int64), contacts["pp_j"].astype(np.int64)
+    has = np.diff(po) > 0
+    if has.any():
+        owner = np.repeat(np.arange(n), np.diff(po))
+        np.maximum.at(L, owner, Lb[pj])
+    floor = (p.alpha / p.dt) * 8.0 * EPS32 * L
+    if per_contact:
+        cnt = np.diff(contacts["pp_off"].astype(np.int64)) + np.diff(off.astype(np.int64))
+        floor = floor * np.maximum(cnt, 1)
+    return 1e-5 * scale + floor
 
 
-def vel_err(v_gpu, v_orc, scene, length=None):
-    """Largest one-step velocity difference as a fraction of vel_tol (pass: < 1)."""
-    return float(np.abs(v_gpu.astype(np.float64) - v_orc).max()) / vel_tol(scene, v_orc, length)
+def vel_err(v_gpu, v_orc, scene, contacts, x=None):
+    """Largest per-particle one-step velocity difference as a fraction of that particle's
+    vel_tol (pass: < 1); the worst particle is named in the message of check_vel."""
+    d = np.abs(np.asarray(v_gpu, np.float64) - np.asarray(v_orc, np.float64)).max(axis=1)
+    return float((d / vel_tol(scene, v_orc, contacts, x)).max())
 
+
+def check_vel(v_gpu, v_orc, scene, contacts, x=None, per_contact=False):
+    """Assert vel_err < 1 with a message that says which particle failed and why."""
+    tol = vel_tol(scene, v_orc, contacts, x, per_contact)
+    d = np.abs(np.asarray(v_gpu, np.float64) - np.asarray(v_orc, np.float64)).max(axis=1)
+    r = d / tol
+    i = int(np.argmax(r))
+    off, boff = contacts["pp_off"], contacts["bc_off"]
+    assert r[i] < 1, (f"particle {i}: |dv| {d[i]:.3e} > tol {tol[i]:.3e} (ratio {r[i]:.2f}); speed "
+                      f"{np.linalg.norm(v_orc[i]):.3e}, {int(off[i + 1] - off[i])} pair and "
+                      f"{int(boff[i + 1] - boff[i])} body contacts; "
+                      f"{int((r > 1).sum())} particles fail, median ratio {float(np.median(r)):.3f}")
+    return float(r[i])
+
+
+def pos_err(x_gpu, x_orc, L_scene):
+    """Per-particle one-step position difference over 1e-5 max(|x_i|, L_scene)."""
+    x_orc = np.asarray(x_orc, np.float64)
+    d = np.abs(np.asarray(x_gpu, np.float64) - x_orc).max(axis=1)
+    return float((d / (1e-5 * np.maximum(np.linalg.norm(x_orc, axis=1), L_scene))).max())

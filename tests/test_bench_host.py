@@ -10,6 +10,8 @@ def test_stage_kernels_follow_the_tuning_flags():
     assert bench.stage_kernels({"lists", "half"}) == ("k_pja", "k_pairs_half+k_pairs_finish")
     assert bench.stage_kernels({"lean"})[0] == "k_pja_lean"
     assert bench.stage_kernels({"fused"})[0] == "k_pja_fused"
+    assert bench.stage_kernels({"detect", "lists"}) == ("k_detect_sweeps", "k_detect_sweeps")
+    assert bench.profile_traffic("k_pja", "column_pile", "x") is None     # no profile kept for it
 
 
 def test_profile_traffic_needs_the_current_digest(tmp_path, monkeypatch):

@@ -4,8 +4,9 @@ adjoint behind torch.autograd.Function; beyond the paper, Sec. V future work).
 Scene: 512 spheres settled by the FP64 oracle around a stationary scoop (the
 oracle's FP32-rounded state is the common input), then 10 steps with the scoop
 on its seeded path.  Loss: the smooth mass inside the scoop's cavity.  The oracle
-gradient is the central finite difference of the FP64 oracle's loss (contact and
-active sets do not change under steps this small).
+gradient is the central finite difference of the FP64 oracle's loss; every
+difference step is checked to leave each step's contact set and each contact's
+projection branch as the unperturbed run has them.
 """
 import dataclasses
 
@@ -38,12 +39,40 @@ def scene():
                    twist={1: sc.twist[1]}, info=sc.info)
 
 
-def oracle_loss(scene, tw, mu):
+def oracle_run(scene, tw, mu):
+    """The FP64 oracle's loss after the T steps, and per step the contact lists and the
+    branch each contact's last projection took (0 separated, 1 sticking, 2 sliding):
+    what the piecewise-smooth step holds fixed."""
     import oracle
     p = dataclasses.replace(scene.params, mu=mu)
     o = oracle.Sim(scene.pos_r, scene.vel, scene.mass, scene.bodies, p, twist={1: tw}, n_threads=4)
-    o.step(tw.shape[0])
-    return o.scoop_loss(1, scene.info["eps"])
+    sets = []
+    for _ in range(tw.shape[0]):
+        c = o.contacts()
+        lam = np.zeros((int(c["pp_off"][-1]), 3))
+        blam = np.zeros((int(c["bc_off"][-1]), 3))
+        geom = np.concatenate([c["pp_geom"][:, :3], c["bc_geom"][:, :3]])
+        o.step(1, pp_lam=lam, bc_lam=blam)
+        lm = np.concatenate([lam, blam])
+        ln = (lm * geom).sum(1)
+        lt = np.linalg.norm(lm - ln[:, None] * geom, axis=1)
+        branch = np.where(ln <= 0.0, 0, np.where(lt >= mu * ln * (1 - 1e-9), 2, 1))
+        sets.append((c["pp_off"], c["pp_j"], c["bc_off"], c["bc_b"], branch))
+    return o.scoop_loss(1, scene.info["eps"]), sets
+
+
+def same_sets(a, b):
+    return all(all(np.array_equal(x, y) for x, y in zip(sa, sb)) for sa, sb in zip(a, b))
+
+
+def oracle_loss(scene, tw, mu, ref_sets=None):
+    """The oracle's loss; with ref_sets, also asserts that the contact and active sets
+    of every step are those of the unperturbed run (the precondition of a central
+    difference of a piecewise-smooth function)."""
+    L, sets = oracle_run(scene, tw, mu)
+    if ref_sets is not None:
+        assert same_sets(sets, ref_sets), "a finite-difference step changed a contact or active set"
+    return L
 
 
 def gpu_grad(torch, scene, checkpoint_every=4):
@@ -67,23 +96,26 @@ def test_adjoint_matches_oracle_gradient(torch, scene):
     L, g_tw, g_mu = gpu_grad(torch, scene)
     tw0 = scene.twist[1].astype(F32)
     mu0 = F32(scene.params.mu)
-    L_orc = oracle_loss(scene, tw0, float(mu0))
+    L_orc, ref = oracle_run(scene, tw0, float(mu0))
     assert abs(L - L_orc) < 1e-4 * L_orc
+    assert sum(int(s[0][-1]) for s in ref) > 1000 and sum(int((s[4] == 2).sum()) for s in ref) > 0
     want = np.zeros_like(g_tw)
     for k in range(T_STEPS):
         for c in range(6):
             def f(v, k=k, c=c):
                 t = tw0.copy()
                 t[k, c] = v
-                return oracle_loss(scene, t, float(mu0))
+                return oracle_loss(scene, t, float(mu0), ref)
             want[k, c] = fd(f, tw0[k, c], 1e-5 if c < 3 else 1e-4)
-    want_mu = fd(lambda v: oracle_loss(scene, tw0, float(v)), mu0, 1e-4)
+    want_mu = fd(lambda v: oracle_loss(scene, tw0, float(v), ref), mu0, 1e-4)
     assert np.abs(want).max() > 0
     cos = float((g_tw * want).sum() / (np.linalg.norm(g_tw) * np.linalg.norm(want)))
     rel = float(np.abs(g_tw - want).max() / np.abs(want).max())
-    assert cos > 0.999, (cos, rel)
-    assert rel < 1e-2, (cos, rel)
-    assert abs(g_mu - want_mu) <= 1e-2 * max(abs(want_mu), 1e-3 * np.abs(want).max()), (g_mu, want_mu)
+    # the GPU runs the forward and the adjoint in FP32: measured max rel 1.2e-3 (twists)
+    # at cos 0.9999986, and 0.9 % on dL/dmu, against the FP64 oracle's central differences
+    assert cos > 0.99999, (cos, rel, g_mu, want_mu)
+    assert rel < 2e-3, (cos, rel, g_mu, want_mu)
+    assert abs(g_mu - want_mu) <= 2e-2 * max(abs(want_mu), 1e-3 * np.abs(want).max()), (g_mu, want_mu, cos, rel)
 
 
 def test_adjoint_invariant_to_checkpoint_interval(torch, scene):

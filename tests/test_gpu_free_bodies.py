@@ -4,7 +4,7 @@ and oracle lockstep."""
 import numpy as np
 import pytest
 
-from gpu_helpers import F32, assert_contacts_equal, lockstep_pair, need_gpu, vel_err
+from gpu_helpers import F32, assert_contacts_equal, check_vel, lockstep_pair, need_gpu
 from paper_2306_01369_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -99,7 +99,7 @@ def test_excavation_with_free_cubes_lockstep(gg, k):
     o.step(1)
     assert_contacts_equal(sim.contacts(), want)
     assert want["stats"]["n_body"] > 50
-    assert vel_err(sim.vel(), o.v, s32, length=0.1) < 1
+    check_vel(sim.vel(), o.v, s32, want)
     bs = sim.body_state()
     for b in (2, 3):   # the free cubes
         tw = o.body_twist(b)

@@ -9,7 +9,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from gpu_helpers import F32, assert_contacts_equal, lockstep_pair, need_gpu, oracle_advanced, vel_err
+from gpu_helpers import F32, assert_contacts_equal, check_vel, lockstep_pair, need_gpu, oracle_advanced
 from paper_2306_01369_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -43,10 +43,10 @@ def test_gear_contacts_bit_exact_lockstep(gg, gear_scene):
 
 def test_gear_one_step_and_ten_steps(gg, gear_scene):
     sim, o, sc = lockstep_pair(gg, gear_scene, 400)
+    want = o.contacts()
     sim.step(1)
     o.step(1)
-    # body-frame coordinate scale of the SDF contacts: 0.1 m
-    assert vel_err(sim.vel(), o.v, sc, length=0.1) < 1
+    check_vel(sim.vel(), o.v, sc, want)
     sim.step(9)
     o.step(9)
     dx = np.linalg.norm(sim.pos()[:, :3].astype(np.float64) - o.x, axis=1)
@@ -173,7 +173,7 @@ def test_tower_contacts_and_dynamics_lockstep(gg, tower_scene):
     assert_contacts_equal(sim.contacts(), want)
     assert int((want["bc_b"] >= 1).sum()) > 10       # contacts with the gears
     o.step(1)
-    assert vel_err(sim.vel(), o.v, sc, length=0.1) < 1
+    check_vel(sim.vel(), o.v, sc, want)
 
 
 def test_tube_wall_contacts_and_dynamics(gg, orc):
@@ -195,7 +195,7 @@ def test_tube_wall_contacts_and_dynamics(gg, orc):
     assert int(want["stats"]["n_body"]) > 300
     assert_contacts_equal(sim.contacts(), want)
     o.step(1)
-    assert vel_err(sim.vel(), o.v, sc, length=0.1) < 1
+    check_vel(sim.vel(), o.v, sc, want)
 
 
 def test_cyclic_boundary_wraps_like_the_oracle(gg, orc):

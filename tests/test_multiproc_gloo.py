@@ -70,6 +70,48 @@ def test_shard_envs_balanced_and_deterministic():
     assert offs[-1] == sizes[3] + sizes[1] and idx.size == offs[-1]
 
 
+def _shard_worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from paper_2306_01369_gb300 import scenes
+    sc = bench.batched_shard(scenes, world, rank, 8)      # what bench.py --workload batched steps on this rank
+    total = bench.sum_over_ranks(float(sc.n), world)
+    q.put((rank, sc.info["envs"], sc.n, [int(v) for v in sc.env_offsets], len(sc.bodies), sorted(sc.twist),
+           total))
+    dist.destroy_process_group()
+
+
+def test_batched_workload_shards_by_environment():
+    """bench.py's batched workload on 2 ranks: each rank builds the full seeded batch
+    of 256 environments and steps only its shard; the shards partition the 256
+    environments, and the particle counts summed over ranks give the batch total."""
+    from paper_2306_01369_gb300 import scenes
+    full = scenes.batched_beds(n_envs=256, seed=1003, n_steps=8)
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    envs = [e for r in res for e in r[1]]
+    assert sorted(envs) == list(range(256))
+    assert sum(r[2] for r in res) == full.n
+    sizes = np.diff(full.env_offsets.astype(np.int64))
+    for rank, mine, n, offs, nbodies, twist_keys, total in res:
+        assert total == float(full.n)
+        assert np.array_equal(np.diff(offs), sizes[mine])
+        assert nbodies == 2 * len(mine) and twist_keys == [2 * k + 1 for k in range(len(mine))]
+    loads = [r[2] for r in res]
+    assert max(loads) - min(loads) <= sizes.max()
+
+
 def test_shard_envs_rejects_empty_world():
     with pytest.raises(ValueError):
         shard_envs([1, 2], 0)
