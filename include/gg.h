@@ -20,7 +20,9 @@
  *    ("id" order), which is also the library's storage order; the bucket sort
  *    produces a list of slots, not a reordered copy of the particles.
  *  - Host pointers are borrowed for the duration of the call only; the library
- *    copies what it needs.  Device pointers (flag *_on_device != 0) must be
+ *    copies what it needs.  Exception: pinned host buffers given to gg_set_particles
+ *    and gg_readback are read or written by work enqueued on the stream, so they must
+ *    stay valid (and, for inputs, unchanged) until that work has run.  Device pointers (flag *_on_device != 0) must be
  *    cudaMalloc'ed memory of the current device; they too are read only during the
  *    call (or, for async calls, by work enqueued on the given stream).
  *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
@@ -181,7 +183,8 @@ typedef enum {
   GG_FIELD_STATS = 12,         /* gg_stats */
   GG_FIELD_STATE = 13,         /* opaque checkpoint for gg_set_state (bit-exact resume) */
   GG_FIELD_POS_VEL = 14        /* float[n][4] as GG_FIELD_POS, then float[n][3] as GG_FIELD_VEL: both
-                                  in one copy and, to the host, one wait */
+                                  in one copy and, to the host, one wait (a pinned host buffer,
+                                  16-byte aligned, is written by one kernel over the host link) */
 } gg_field;
 
 typedef struct {
@@ -192,6 +195,9 @@ typedef struct {
   uint32_t max_body;       /* largest particle-body count of one particle, last step */
   uint32_t status_flags;   /* latched device flags: 1 pp overflow, 2 body overflow, 4 non-finite */
   float max_psi;           /* largest penetration depth at the last step */
+  uint32_t n_active;       /* particles with at least one contact at the last step (the others'
+                              velocity estimates stay their unconstrained velocity, and the
+                              sweeps leave them alone) */
 } gg_stats;
 
 GG_API uint32_t gg_abi_version(void);
@@ -247,7 +253,10 @@ GG_API gg_status gg_set_trajectory(gg_sim *sim, uint32_t env, uint32_t body, uin
                             const float *twist, int twist_on_device);
 
 /* Overwrite particle positions/radii (float[n][4]) and velocities (float[n][3]; NULL
- * keeps them), asynchronously on `stream`.  Masses are kept. */
+ * keeps them), asynchronously on `stream`.  Masses are kept.  Host buffers that are
+ * pinned (cudaHostAlloc, cudaHostRegister; positions 16-byte aligned) are read by one
+ * kernel over the host link; pageable ones are copied.  Either way the caller's buffers
+ * must stay unchanged until the work on `stream` has run. */
 GG_API gg_status gg_set_particles(gg_sim *sim, const float *pos_radius, const float *vel, int on_device,
                            void *stream);
 

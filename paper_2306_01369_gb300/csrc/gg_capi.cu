@@ -185,6 +185,18 @@ gg_status ensure_staging(gg_sim *s, size_t bytes) {
 
 bool finite_pos(float v) { return std::isfinite(v); }
 
+// Device address of a caller's pinned (page-locked, registered) host buffer, or null
+// for pageable memory: a kernel can then move particle state to or from it over the
+// host link directly, without a staging copy.
+void *pinned_device_ptr(const void *host) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 // One simulation state (what a step reads): particles, bodies, control word.
 size_t state_bytes(const gg_sim *s) {
   const size_t nbt = (size_t)s->n_envs * s->maxb;
@@ -947,6 +959,15 @@ gg_status gg_set_particles(gg_sim *s, const float *pos_radius, const float *vel,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (!s->n) return GG_OK;
+  if (!on_device) {  // pinned host buffers: one kernel reads them over the host link
+    const void *dp = pinned_device_ptr(pos_radius);
+    const void *dv = vel ? pinned_device_ptr(vel) : nullptr;
+    if (dp && (!vel || dv) && (reinterpret_cast<uintptr_t>(dp) & 15u) == 0) {
+      GG_CUDA(s, gg::enqueue_state_in(s->a.pos_id, s->a.vel_id, static_cast<const float *>(dp),
+                                      static_cast<const float *>(dv), s->n, st));
+      return GG_OK;
+    }
+  }
   GG_CUDA(s, cudaMemcpyAsync(s->a.pos_id, pos_radius, sizeof(float4) * s->n, kind, st));
   if (vel) {
     const float *src = vel;
@@ -1036,6 +1057,14 @@ gg_status gg_readback(gg_sim *s, gg_field f, void *dst, size_t bytes, int dst_on
     break;
   case GG_FIELD_POS_VEL:
     if (!n) break;
+    if (!dst_on_device) {  // a pinned host buffer: one kernel writes it over the host link
+      char *dd = static_cast<char *>(pinned_device_ptr(dst));
+      if (dd && (reinterpret_cast<uintptr_t>(dd) & 15u) == 0) {
+        GG_CUDA(s, gg::enqueue_state_out(s->a.pos_id, s->a.vel_id, reinterpret_cast<float *>(dd),
+                                         reinterpret_cast<float *>(dd + n * 16), s->n, st));
+        break;
+      }
+    }
     if ((rc = target(need, &t)) != GG_OK) return rc;
     GG_CUDA(s, cudaMemcpyAsync(t, s->a.pos_id, n * 16, cudaMemcpyDeviceToDevice, st));
     GG_CUDA(s, gg::enqueue_vel4_to_vel3(s->a.vel_id, reinterpret_cast<float *>(static_cast<char *>(t) + n * 16),
@@ -1105,6 +1134,7 @@ gg_status gg_readback(gg_sim *s, gg_field f, void *dst, size_t bytes, int dst_on
     out.max_pp = c.max_pp;
     out.max_body = c.max_body;
     out.status_flags = c.status;
+    out.n_active = c.n_active;
     uint32_t bits = c.max_psi_bits;
     std::memcpy(&out.max_psi, &bits, 4);
     std::memcpy(dst, &out, sizeof(out));

@@ -109,6 +109,7 @@ struct DevCtrl {
   uint32_t bar_abort;     // set when a barrier wait gave up (later barriers return at once)
   uint32_t bar_extra;     // phantom arrivals a barrier waits for (0; tests set it to force a timeout)
   uint32_t blocks_done;     // k_wrench_bodies: blocks finished this step (0 between steps)
+  uint32_t n_active;        // particles with at least one contact this step
 };
 
 // Index checks of the debug build (-DGG_DEBUG): GG_GUARD(ctrl, cond) is `cond`, and a

@@ -73,6 +73,11 @@ cudaError_t enqueue_pack3(float4 *dst, const float *src3, uint32_t n, cudaStream
 cudaError_t enqueue_export_contacts(const StepArgs &a, uint32_t *rows, float *geom, float *lam, float *bgeom,
                                     float *blam, cudaStream_t st);
 cudaError_t enqueue_vel3_to_vel4(float4 *vel_id, const float *vel3, uint32_t n, cudaStream_t st);
+// pos: float[n][4] (16-byte aligned), vel: float[n][3]; device-accessible host memory
+cudaError_t enqueue_state_out(const float4 *pos_id, const float4 *vel_id, float *pos, float *vel, uint32_t n,
+                              cudaStream_t st);
+cudaError_t enqueue_state_in(float4 *pos_id, float4 *vel_id, const float *pos, const float *vel, uint32_t n,
+                             cudaStream_t st);
 cudaError_t enqueue_vel4_to_vel3(const float4 *vel_id, float *vel3, uint32_t n, cudaStream_t st);
 cudaError_t enqueue_body_state(const DevBody *bodies, uint32_t nbt, float *out, cudaStream_t st);
 

@@ -100,7 +100,8 @@ def make_camera(cam) -> GGCamera:
 
 class GGStats(C.Structure):
     _fields_ = [("steps", C.c_uint64), ("n_pp", C.c_uint32), ("n_body", C.c_uint32), ("max_pp", C.c_uint32),
-                ("max_body", C.c_uint32), ("status_flags", C.c_uint32), ("max_psi", C.c_float)]
+                ("max_body", C.c_uint32), ("status_flags", C.c_uint32), ("max_psi", C.c_float),
+                ("n_active", C.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

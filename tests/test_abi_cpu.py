@@ -71,7 +71,7 @@ def test_struct_sizes_match_header():
     from paper_2306_01369_gb300 import gg
     assert ctypes.sizeof(gg.GGParams) == 4 * 26
     assert ctypes.sizeof(gg.GGBody) == 4 * (2 + 12 + 3 + 4 + 3 + 3 + 1 + 3)
-    assert ctypes.sizeof(gg.GGStats) == 8 + 4 * 6
+    assert ctypes.sizeof(gg.GGStats) == 8 + 4 * 8   # 7 four-byte fields, padded to 8
     assert ctypes.sizeof(gg.GGCamera) == 4 * 20
 
 
