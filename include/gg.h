@@ -109,7 +109,8 @@ typedef struct {
                                 registers, sets 11-13 find pairs over half the stencil and mirror
                                 them, sets 14-15 (sort, lists) run detection and every sweep in one
                                 cooperative launch, sets 16-18 (sort, lists, lists with the half
-                                stencil) reverse every other sweep).  Results do not depend on it. */
+                                stencil) reverse every other sweep and preload the first round's
+                                records).  Results do not depend on it. */
   uint32_t wrench_history;   /* per-step body wrenches kept for readback; 0 -> 1 */
   uint32_t max_free_bodies;  /* free rigid bodies over all environments (beyond the paper's
                                 kinematic bodies, Sec. V two-way coupling); 0 -> none */
@@ -388,6 +389,8 @@ GG_API uint32_t gg_tuning_selected(const gg_sim *sim);
                               bodies (with them the set runs the split launches) */
 #define GG_TUNE_SERP 32u   /* serpentine sweeps: every other sweep visits the particles in reverse,
                               starting on the data the previous stage left in L2 */
+#define GG_TUNE_PRELOAD 64u /* the sweep loads the records of the first two contact slots
+                               together with the counts */
 
 GG_API uint32_t gg_tuning_flags(uint32_t k);
 

@@ -28,14 +28,15 @@ namespace {
 
 // Launch-shape sets accepted by gg_params.tuning (index k-1).
 // (iters, per-launch sweep block, fused sweep block, fused grid, binning by lists, lean sweeps,
-//  half-stencil pair search, detection and sweeps in one cooperative launch, serpentine sweeps)
+//  half-stencil pair search, detection and sweeps in one cooperative launch, serpentine sweeps,
+//  preloaded first sweep round)
 const gg::LaunchShape kShapes[] = {{0, 256, 0, 0, 0, 0, 0},    {0, 128, 0, 0, 0, 0, 0}, {0, 512, 0, 0, 0, 0, 0},
                                    {0, 64, 0, 0, 0, 0, 0},     {0, 256, 1024, 0, 0, 0, 0}, {0, 256, 512, 0, 0, 0, 0},
                                    {0, 256, 0, 0, 1, 0, 0},    {0, 128, 0, 0, 1, 0, 0}, {0, 256, 0, 0, 1, 1, 0},
                                    {0, 256, 0, 0, 0, 1, 0},    {0, 256, 0, 0, 1, 0, 1}, {0, 256, 0, 0, 1, 1, 1},
                                    {0, 256, 0, 0, 0, 0, 1},    {0, 256, 0, 0, 0, 0, 0, 1}, {0, 256, 0, 0, 1, 0, 0, 1},
-                                   {0, 128, 0, 0, 0, 0, 0, 0, 1}, {0, 128, 0, 0, 1, 0, 0, 0, 1},
-                                   {0, 128, 0, 0, 1, 0, 1, 0, 1}};
+                                   {0, 128, 0, 0, 0, 0, 0, 0, 1, 1}, {0, 128, 0, 0, 1, 0, 0, 0, 1, 1},
+                                   {0, 128, 0, 0, 1, 0, 1, 0, 1, 1}};
 constexpr uint32_t kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 // n_h factors the autotuner tries when gg_params.hash_tune is set (the paper's 2n first)
@@ -486,7 +487,8 @@ uint32_t gg_tuning_flags(uint32_t k) {
   if (k < 1 || k > kNumShapes) return 0;
   const gg::LaunchShape &ls = kShapes[k - 1];
   return (ls.lists ? GG_TUNE_LISTS : 0u) | (ls.fused_block ? GG_TUNE_FUSED : 0u) | (ls.lean ? GG_TUNE_LEAN : 0u) |
-         (ls.half ? GG_TUNE_HALF : 0u) | (ls.detect ? GG_TUNE_DETECT : 0u) | (ls.serp ? GG_TUNE_SERP : 0u);
+         (ls.half ? GG_TUNE_HALF : 0u) | (ls.detect ? GG_TUNE_DETECT : 0u) | (ls.serp ? GG_TUNE_SERP : 0u) |
+         (ls.pre ? GG_TUNE_PRELOAD : 0u);
 }
 
 uint32_t gg_kernels_per_step(const gg_sim *sim) { return sim ? gg::kernels_per_step(sim->a, sim->ls) : 0; }
@@ -1046,6 +1048,7 @@ gg_status gg_readback(gg_sim *s, gg_field f, void *dst, size_t bytes, int dst_on
   };
   gg_status rc = GG_OK;
   void *t = nullptr;
+  bool ctrl_done = false;  // the control word already came back with the data (pinned path)
   switch (f) {
   case GG_FIELD_POS:
     if (n) GG_CUDA(s, cudaMemcpyAsync(dst, s->a.pos_id, need, d2x, st));
@@ -1060,8 +1063,14 @@ gg_status gg_readback(gg_sim *s, gg_field f, void *dst, size_t bytes, int dst_on
     if (!dst_on_device) {  // a pinned host buffer: one kernel writes it over the host link
       char *dd = static_cast<char *>(pinned_device_ptr(dst));
       if (dd && (reinterpret_cast<uintptr_t>(dd) & 15u) == 0) {
+        if (!s->ctrl_host) GG_CUDA(s, cudaHostAlloc(reinterpret_cast<void **>(&s->ctrl_host), sizeof(DevCtrl), 0));
+        DevCtrl *cd = static_cast<DevCtrl *>(pinned_device_ptr(s->ctrl_host));
         GG_CUDA(s, gg::enqueue_state_out(s->a.pos_id, s->a.vel_id, reinterpret_cast<float *>(dd),
-                                         reinterpret_cast<float *>(dd + n * 16), s->n, st));
+                                         reinterpret_cast<float *>(dd + n * 16), s->n, s->a.ctrl, cd, st));
+        if (cd) {
+          GG_CUDA(s, cudaStreamSynchronize(st));
+          ctrl_done = true;
+        }
         break;
       }
     }
@@ -1159,7 +1168,10 @@ gg_status gg_readback(gg_sim *s, gg_field f, void *dst, size_t bytes, int dst_on
   }
   if (dst_on_device) return GG_OK;
   DevCtrl c;
-  if ((rc = read_ctrl(s, &c, st)) != GG_OK) return rc;
+  if (ctrl_done)
+    c = *s->ctrl_host;
+  else if ((rc = read_ctrl(s, &c, st)) != GG_OK)
+    return rc;
   return status_from_flags(s, c.status);
 }
 

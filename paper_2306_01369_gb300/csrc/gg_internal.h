@@ -38,6 +38,7 @@ struct LaunchShape {
   uint32_t half;        // pair search over half the stencil in two passes instead of k_contacts
   uint32_t detect;      // detection and all sweeps in one cooperative launch (fused_grid blocks)
   uint32_t serp;        // serpentine sweeps: every other per-launch sweep runs its blocks in reverse
+  uint32_t pre;         // per-launch sweeps load the first round's records with the counts
 };
 int fused_pja_blocks_per_sm(int block);
 int detect_sweeps_blocks_per_sm(bool lists, uint32_t K);
@@ -73,9 +74,10 @@ cudaError_t enqueue_pack3(float4 *dst, const float *src3, uint32_t n, cudaStream
 cudaError_t enqueue_export_contacts(const StepArgs &a, uint32_t *rows, float *geom, float *lam, float *bgeom,
                                     float *blam, cudaStream_t st);
 cudaError_t enqueue_vel3_to_vel4(float4 *vel_id, const float *vel3, uint32_t n, cudaStream_t st);
-// pos: float[n][4] (16-byte aligned), vel: float[n][3]; device-accessible host memory
+// pos: float[n][4] (16-byte aligned), vel: float[n][3]; device-accessible host memory;
+// ctrl_out (optional, device-accessible host memory): receives a copy of *ctrl
 cudaError_t enqueue_state_out(const float4 *pos_id, const float4 *vel_id, float *pos, float *vel, uint32_t n,
-                              cudaStream_t st);
+                              const DevCtrl *ctrl, DevCtrl *ctrl_out, cudaStream_t st);
 cudaError_t enqueue_state_in(float4 *pos_id, float4 *vel_id, const float *pos, const float *vel, uint32_t n,
                              cudaStream_t st);
 cudaError_t enqueue_vel4_to_vel3(const float4 *vel_id, float *vel3, uint32_t n, cudaStream_t st);

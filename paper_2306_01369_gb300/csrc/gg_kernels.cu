@@ -833,6 +833,8 @@ __device__ __forceinline__ void pja_particle(const StepArgs &a, uint32_t i, int 
   // sweep) and costs where most spheres have no contact (the collapsing column: their
   // unused records are 64 bytes of extra reads each, 3.2 -> 3.6 us), so the serpentine
   // launch shapes, which the autotuner picks for the former, use it.
+  // (Loading only the partner ids of slots 0 and 1 early was measured too: slower on
+  // every workload, 64 registers with spills.)
   const bool two = PRE && a.K > 1;
   uint32_t pj0 = 0u, pj1 = 0u;
   float4 pn0 = make_float4(0.f, 0.f, 0.f, 0.f), pn1 = pn0;
@@ -968,6 +970,7 @@ __global__ void __maxnreg__(40) k_pja_lean(StepArgs a, int s, int it, int rev) {
   const Tape none{};
   if (i < a.n) pja_particle<false, false>(a, i, s, none, it);
 }
+
 
 // Grid-wide barrier of a cooperative launch (all blocks resident).  The wait is
 // bounded: past `limit` SM cycles it latches kFlagTimeout and sets bar_abort, after
@@ -1222,7 +1225,10 @@ __device__ __forceinline__ void integrate_particle(const StepArgs &a, int s, uin
 //      each body's contact forces and torques over them in a fixed order
 // ---------------------------------------------------------------------------
 
-constexpr int kIntegrateThreads = kWrenchChunk;  // one particle of the chunk per thread
+// One particle of the chunk per thread.  (Two per thread in 512-thread blocks, so that
+// a 262,144-sphere step's 256 chunks fit one wave of two blocks per SM, measured
+// slower: 16.0 against 14.3 us for the stage on the column.)
+constexpr int kIntegrateThreads = kWrenchChunk;
 
 __global__ void __launch_bounds__(kIntegrateThreads) k_integrate_wrench(StepArgs a, int s, int rev) {
   pdl_enter();
@@ -1610,7 +1616,7 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
         GG_LAUNCH(k_pja<true>, dim3(grid_for(a.n, ls.pja_block)), ls.pja_block, 0, a, (int)(it & 1), *tp, (int)it, 0);
       else if (ls.lean)
         GG_LAUNCH(k_pja_lean, dim3(grid_for(a.n, ls.pja_block)), ls.pja_block, 0, a, (int)(it & 1), (int)it, rev);
-      else if (ls.serp)  // serpentine sweeps come with the preloaded first round (see pja_particle)
+      else if (ls.pre)  // the first round's records preloaded (see pja_particle)
         GG_LAUNCH((k_pja<false, true>), dim3(grid_for(a.n, ls.pja_block)), ls.pja_block, 0, a, (int)(it & 1), none,
                   (int)it, rev);
       else
@@ -1676,8 +1682,10 @@ cudaError_t enqueue_export_contacts(const StepArgs &a, uint32_t *rows, float *ge
 // Particle state to and from a caller's pinned host buffers, read or written by the
 // kernel itself over the host link (no staging copy): pos float[n][4], vel float[n][3]
 // (either may be null).
-__global__ void k_state_out(const float4 *pos_id, const float4 *vel_id, float4 *pos, float *vel, uint32_t n) {
+__global__ void k_state_out(const float4 *pos_id, const float4 *vel_id, float4 *pos, float *vel, uint32_t n,
+                            const DevCtrl *ctrl, DevCtrl *ctrl_out) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ctrl_out && i == 0) *ctrl_out = *ctrl;  // the status word rides along (no copy of its own)
   if (i >= n) return;
   if (pos) pos[i] = pos_id[i];
   if (vel) {
@@ -1699,8 +1707,10 @@ __global__ void k_state_in(float4 *pos_id, float4 *vel_id, const float4 *pos, co
 }
 
 cudaError_t enqueue_state_out(const float4 *pos_id, const float4 *vel_id, float *pos, float *vel, uint32_t n,
-                              cudaStream_t st) {
-  if (n) k_state_out<<<grid_for(n, 256), 256, 0, st>>>(pos_id, vel_id, reinterpret_cast<float4 *>(pos), vel, n);
+                              const DevCtrl *ctrl, DevCtrl *ctrl_out, cudaStream_t st) {
+  if (n || ctrl_out)
+    k_state_out<<<grid_for(n, 256), 256, 0, st>>>(pos_id, vel_id, reinterpret_cast<float4 *>(pos), vel, n, ctrl,
+                                                 ctrl_out);
   return cudaGetLastError();
 }
 

@@ -63,7 +63,8 @@ def test_tuning_sets_cover_every_variant():
         assert {v} in sets and {v, "lists"} in sets
     assert {"fused"} in sets
     assert {"detect"} in sets and {"detect", "lists"} in sets
-    assert {"serp"} in sets and {"serp", "lists"} in sets and {"serp", "lists", "half"} in sets
+    assert {"serp", "preload"} in sets and {"serp", "lists", "preload"} in sets
+    assert {"serp", "lists", "half", "preload"} in sets
 
 
 def test_struct_sizes_match_header():
