@@ -329,28 +329,43 @@ __device__ __forceinline__ void contact_records(const StepArgs &a, uint32_t i, f
                                                 const uint32_t *fid, uint32_t S, uint32_t K, uint32_t npp, bool ovf,
                                                 uint32_t &nbc, float &psi_max) {
     const size_t n = a.n;
-    for (uint32_t c = 0; c < npp; ++c) {
-      const uint32_t j = fid[c * S];
-      float d2;
-      float3 d;
-      const float4 pj = a.pos_id[j];
-      sphere_hit(pi, pj, &d2, &d);
-      const float dist = __fsqrt_rn(d2);
-      float3 nn;
-      if (dist > 0.f) {
-        const float id = __frcp_rn(dist);
-        nn = make_float3(d.x * id, d.y * id, d.z * id);
-      } else {
-        nn = make_float3(0.f, 0.f, i > j ? 1.f : -1.f);
+    // the partners' positions are gathered four at a time, all four loads in flight
+    // before any record of the group is computed and stored
+    constexpr uint32_t kGroup = 4;
+    for (uint32_t c0 = 0; c0 < npp; c0 += kGroup) {
+      uint32_t jg[kGroup];
+      float4 pg[kGroup];
+#pragma unroll
+      for (uint32_t q = 0; q < kGroup; ++q) {
+        jg[q] = c0 + q < npp ? fid[(c0 + q) * S] : i;
+        pg[q] = a.pos_id[jg[q]];
       }
-      const float psi = __fsub_rn(__fadd_rn(pi.w, pj.w), dist);
-      psi_max = fmaxf(psi_max, psi);
-      const size_t o = (size_t)c * n + i;
-      a.cj[o] = j;
-      a.cn[o] = make_float4(nn.x, nn.y, nn.z, psi);
-      a.clam[o] = 0.f;
-      a.clam[o + (size_t)K * n] = 0.f;
-      a.clam[o + 2 * (size_t)K * n] = 0.f;
+#pragma unroll
+      for (uint32_t q = 0; q < kGroup; ++q) {
+        const uint32_t c = c0 + q;
+        if (c >= npp) break;
+        const uint32_t j = jg[q];
+        float d2;
+        float3 d;
+        const float4 pj = pg[q];
+        sphere_hit(pi, pj, &d2, &d);
+        const float dist = __fsqrt_rn(d2);
+        float3 nn;
+        if (dist > 0.f) {
+          const float id = __frcp_rn(dist);
+          nn = make_float3(d.x * id, d.y * id, d.z * id);
+        } else {
+          nn = make_float3(0.f, 0.f, i > j ? 1.f : -1.f);
+        }
+        const float psi = __fsub_rn(__fadd_rn(pi.w, pj.w), dist);
+        psi_max = fmaxf(psi_max, psi);
+        const size_t o = (size_t)c * n + i;
+        a.cj[o] = j;
+        a.cn[o] = make_float4(nn.x, nn.y, nn.z, psi);
+        a.clam[o] = 0.f;
+        a.clam[o + (size_t)K * n] = 0.f;
+        a.clam[o + 2 * (size_t)K * n] = 0.f;
+      }
     }
     // particle-body contacts, bodies in ascending index
     const float3 xi = make_float3(pi.x, pi.y, pi.z);
@@ -589,7 +604,7 @@ __device__ __forceinline__ void detect_particle(const StepArgs &a, uint32_t i, u
 }
 
 template <bool LISTS>
-__global__ void __launch_bounds__(kContactsBlock) k_contacts(StepArgs a) {
+__global__ void __launch_bounds__(kContactsBlock, 8) k_contacts(StepArgs a) {
   pdl_enter();
   extern __shared__ uint32_t s_fid[];
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -756,7 +771,7 @@ __global__ void __launch_bounds__(kContactsBlock, 9) k_pairs_half(StepArgs a) {
 
 // Pass 2: the partner list of particle i from its scratch entries (sorted, duplicates
 // dropped, the K smallest ids kept as in k_contacts), then the same records.
-__global__ void __launch_bounds__(kContactsBlock) k_pairs_finish(StepArgs a) {
+__global__ void __launch_bounds__(kContactsBlock, 8) k_pairs_finish(StepArgs a) {
   pdl_enter();
   extern __shared__ uint32_t s_fid[];
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1239,12 +1254,27 @@ __global__ void __launch_bounds__(kIntegrateThreads) k_integrate_wrench(StepArgs
   const DevEnv &E = a.envs[e];
   const uint32_t s0 = E.off + (c - E.chunk0) * kWrenchChunk;
   const uint32_t s1 = min(s0 + kWrenchChunk, E.off + E.n);
-  for (uint32_t i = s0 + threadIdx.x; i < s1; i += kIntegrateThreads) integrate_particle(a, s, i);
+  // one particle per thread (the chunk is the block)
+  const uint32_t i = s0 + threadIdx.x;
+  const bool own = i < s1;
+  const uint32_t nbc = own ? (a.ccount[i] >> 8) & 0xffu : 0u;
+  if (own) integrate_particle(a, s, i);
   // linked-list binning: the step's lists have been walked, so empty every bucket for
-  // the next step's pushes here instead of in a launch of its own (created empty)
-  if (a.lists)
-    for (uint32_t b = blockIdx.x * kIntegrateThreads + threadIdx.x; b < a.nh_total; b += gridDim.x * kIntegrateThreads)
-      a.head[b] = kListEnd;
+  // the next step's pushes here instead of in a launch of its own (created empty); the
+  // table is padded to a multiple of kScanTile buckets, so it is cleared four at a time
+  if (a.lists) {
+    uint4 *h4 = reinterpret_cast<uint4 *>(a.head);
+    const uint4 empty = make_uint4(kListEnd, kListEnd, kListEnd, kListEnd);
+    for (uint32_t b = blockIdx.x * kIntegrateThreads + threadIdx.x; b < a.nh_pad / 4u; b += gridDim.x * kIntegrateThreads)
+      h4[b] = empty;
+  }
+  // no body contact in the chunk (most chunks): every partial of the environment's
+  // bodies is zero, written at once (the partials of slot c are contiguous)
+  if (!__syncthreads_or(nbc != 0u)) {
+    for (uint32_t t = threadIdx.x; t < 6u * E.nbodies; t += kIntegrateThreads)
+      a.wpart[(size_t)c * a.maxb * 6 + t] = 0.f;
+    return;
+  }
   const size_t n = a.n, KbN = (size_t)a.Kb * n;
   const float inv_dt = 1.0f / a.dt;
   for (uint32_t lb = 0; lb < E.nbodies; ++lb) {
@@ -1252,22 +1282,19 @@ __global__ void __launch_bounds__(kIntegrateThreads) k_integrate_wrench(StepArgs
     const DevBody &B = a.bodies[gb];
     float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int hit = 0;
-    for (uint32_t i = s0 + threadIdx.x; i < s1; i += kIntegrateThreads) {
-      const uint32_t nbc = (a.ccount[i] >> 8) & 0xffu;
-      for (uint32_t k = 0; k < nbc; ++k) {
-        const size_t o = (size_t)k * n + i;
-        if (a.bj[o] != gb) continue;
-        hit = 1;
-        const float fx = -a.blam[o] * inv_dt, fy = -a.blam[o + KbN] * inv_dt, fz = -a.blam[o + 2 * KbN] * inv_dt;
-        const float4 xc = a.bxc[o];
-        const float rx = xc.x - B.p[0], ry = xc.y - B.p[1], rz = xc.z - B.p[2];
-        v[0] += fx;
-        v[1] += fy;
-        v[2] += fz;
-        v[3] += ry * fz - rz * fy;
-        v[4] += rz * fx - rx * fz;
-        v[5] += rx * fy - ry * fx;
-      }
+    for (uint32_t k = 0; k < nbc; ++k) {
+      const size_t o = (size_t)k * n + i;
+      if (a.bj[o] != gb) continue;
+      hit = 1;
+      const float fx = -a.blam[o] * inv_dt, fy = -a.blam[o + KbN] * inv_dt, fz = -a.blam[o + 2 * KbN] * inv_dt;
+      const float4 xc = a.bxc[o];
+      const float rx = xc.x - B.p[0], ry = xc.y - B.p[1], rz = xc.z - B.p[2];
+      v[0] += fx;
+      v[1] += fy;
+      v[2] += fz;
+      v[3] += ry * fz - rz * fy;
+      v[4] += rz * fx - rx * fz;
+      v[5] += rx * fy - ry * fx;
     }
     if (!__syncthreads_or(hit)) {  // no contact with this body in the chunk: zero partial
       if (threadIdx.x < 6) a.wpart[((size_t)c * a.maxb + lb) * 6 + threadIdx.x] = 0.f;
