@@ -241,7 +241,10 @@ def stage_kernels(flags):
     `flags` runs."""
     if "detect" in flags:                 # one launch holds the contact stage and the sweeps
         return "k_detect_sweeps", "k_detect_sweeps"
-    sweep = "k_pja_fused" if "fused" in flags else ("k_pja_lean" if "lean" in flags else "k_pja")
+    if "oneloop" in flags:                # every iteration walks the cells again
+        sweep = "k_oneloop"
+    else:
+        sweep = "k_pja_fused" if "fused" in flags else ("k_pja_lean" if "lean" in flags else "k_pja")
     contacts = "k_pairs_half+k_pairs_finish" if "half" in flags else "k_contacts"
     return sweep, contacts
 
@@ -580,6 +583,28 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
                                           "speedup_vs_2n": {k: row["nh2n"] / v for k, v in row.items()}}
         out["hashtable_sizes"] = {"workload": "columns of 1,024-65,536 spheres (same recipe), steps 1000-1200, "
                                                "fixed launch shapes (sets 1 and 7)", "configs": curve}
+        # the loop-structure experiment (Sec. II-D, Fig. warp-divergence-performance):
+        # TwoLoopsSplit (detection, then one launch per sweep), TwoLoopsFused (both loops
+        # in one cooperative launch) and OneLoop (every iteration walks the cells again),
+        # binning by lists, on columns of 1k-262k spheres 1,000 steps into the collapse
+        n_sets = gg.load().gg_tuning_count()
+        by_flags = {frozenset(gg.tuning_flags(k)): k for k in range(n_sets, 0, -1)}
+        forms = (("TwoLoopsSplit", by_flags[frozenset({"lists"})]),
+                 ("TwoLoopsFused", by_flags[frozenset({"lists", "detect"})]),
+                 ("OneLoop", by_flags[frozenset({"lists", "oneloop"})]))
+        loops = {}
+        for nc in (1024, 4096, 16384, 65536, 262144):
+            colc = scenes.column_collapse(n=nc)
+            row = {}
+            for name, tuning in forms:
+                sim = gg.Sim.from_scene(colc, tuning=tuning)
+                sim.step(1000, stream=stream)
+                row[name] = _timed_steps(sim, 100, stream, torch) / 100
+                sim.close()
+            loops[f"n{nc}"] = {"ms_per_step": row, "split_speedup": {k: v / row["TwoLoopsSplit"] for k, v in row.items()}}
+        out["loop_structure"] = {"workload": "columns of 1,024-262,144 spheres (same recipe), steps 1000-1100, "
+                                             "lists binning, n_h = 2n; split_speedup = form's time / split time",
+                                 "sets": {name: k for name, k in forms}, "configs": loops}
     # excavation: 1,048,576 spheres, scoop, two free cubes, I = 30
     if time.perf_counter() - t_start < seconds_cap:
         ex = scenes.excavation(n=1048576, n_steps=steps_exc + 20)

@@ -110,7 +110,9 @@ typedef struct {
                                 them, sets 14-15 (sort, lists) run detection and every sweep in one
                                 cooperative launch, sets 16-18 (sort, lists, lists with the half
                                 stencil) reverse every other sweep and preload the first round's
-                                records).  Results do not depend on it. */
+                                records, sets 19-20 (sort, lists) run the paper's OneLoop: every
+                                iteration walks the cells again and computes each response as it
+                                finds the contact).  Results do not depend on it. */
   uint32_t wrench_history;   /* per-step body wrenches kept for readback; 0 -> 1 */
   uint32_t max_free_bodies;  /* free rigid bodies over all environments (beyond the paper's
                                 kinematic bodies, Sec. V two-way coupling); 0 -> none */
@@ -391,6 +393,8 @@ GG_API uint32_t gg_tuning_selected(const gg_sim *sim);
                               starting on the data the previous stage left in L2 */
 #define GG_TUNE_PRELOAD 64u /* the sweep loads the records of the first two contact slots
                                together with the counts */
+#define GG_TUNE_ONELOOP 128u /* OneLoop (Sec. II-D): each iteration re-walks the neighbour cells
+                                and computes the responses there, not from stored records */
 
 GG_API uint32_t gg_tuning_flags(uint32_t k);
 

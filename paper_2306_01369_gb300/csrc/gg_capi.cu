@@ -29,14 +29,15 @@ namespace {
 // Launch-shape sets accepted by gg_params.tuning (index k-1).
 // (iters, per-launch sweep block, fused sweep block, fused grid, binning by lists, lean sweeps,
 //  half-stencil pair search, detection and sweeps in one cooperative launch, serpentine sweeps,
-//  preloaded first sweep round)
+//  preloaded first sweep round, OneLoop)
 const gg::LaunchShape kShapes[] = {{0, 256, 0, 0, 0, 0, 0},    {0, 128, 0, 0, 0, 0, 0}, {0, 512, 0, 0, 0, 0, 0},
                                    {0, 64, 0, 0, 0, 0, 0},     {0, 256, 1024, 0, 0, 0, 0}, {0, 256, 512, 0, 0, 0, 0},
                                    {0, 256, 0, 0, 1, 0, 0},    {0, 128, 0, 0, 1, 0, 0}, {0, 256, 0, 0, 1, 1, 0},
                                    {0, 256, 0, 0, 0, 1, 0},    {0, 256, 0, 0, 1, 0, 1}, {0, 256, 0, 0, 1, 1, 1},
                                    {0, 256, 0, 0, 0, 0, 1},    {0, 256, 0, 0, 0, 0, 0, 1}, {0, 256, 0, 0, 1, 0, 0, 1},
                                    {0, 128, 0, 0, 0, 0, 0, 0, 1, 1}, {0, 128, 0, 0, 1, 0, 0, 0, 1, 1},
-                                   {0, 128, 0, 0, 1, 0, 1, 0, 1, 1}};
+                                   {0, 128, 0, 0, 1, 0, 1, 0, 1, 1}, {0, 128, 0, 0, 0, 0, 0, 0, 0, 0, 1},
+                                   {0, 128, 0, 0, 1, 0, 0, 0, 0, 0, 1}};
 constexpr uint32_t kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 // n_h factors the autotuner tries when gg_params.hash_tune is set (the paper's 2n first)
@@ -488,7 +489,7 @@ uint32_t gg_tuning_flags(uint32_t k) {
   const gg::LaunchShape &ls = kShapes[k - 1];
   return (ls.lists ? GG_TUNE_LISTS : 0u) | (ls.fused_block ? GG_TUNE_FUSED : 0u) | (ls.lean ? GG_TUNE_LEAN : 0u) |
          (ls.half ? GG_TUNE_HALF : 0u) | (ls.detect ? GG_TUNE_DETECT : 0u) | (ls.serp ? GG_TUNE_SERP : 0u) |
-         (ls.pre ? GG_TUNE_PRELOAD : 0u);
+         (ls.pre ? GG_TUNE_PRELOAD : 0u) | (ls.one ? GG_TUNE_ONELOOP : 0u);
 }
 
 uint32_t gg_kernels_per_step(const gg_sim *sim) { return sim ? gg::kernels_per_step(sim->a, sim->ls) : 0; }

@@ -39,6 +39,7 @@ struct LaunchShape {
   uint32_t detect;      // detection and all sweeps in one cooperative launch (fused_grid blocks)
   uint32_t serp;        // serpentine sweeps: every other per-launch sweep runs its blocks in reverse
   uint32_t pre;         // per-launch sweeps load the first round's records with the counts
+  uint32_t one;         // OneLoop: every iteration re-walks the cells and computes the responses
 };
 int fused_pja_blocks_per_sm(int block);
 int detect_sweeps_blocks_per_sm(bool lists, uint32_t K);

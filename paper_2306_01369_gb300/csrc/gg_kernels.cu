@@ -323,6 +323,48 @@ __device__ __forceinline__ uint2 bounded_range(const StepArgs &a, uint2 rg) {
 constexpr int kWalkGroup = 3;       // buckets of a row (dx = -1, 0, 1), walked together
 constexpr int kContactsBlock = 128;  // threads per block of k_contacts
 
+// Contact normal (from j towards i) and penetration psi = r_i + r_j - |x_i - x_j| of a
+// pair that passed the hit test; coincident centres get +-z by id order.  Every
+// product is rounded on its own (no contraction), so the result is the same wherever
+// the helper is inlined.
+__device__ __forceinline__ float4 pair_geometry(const float4 &pi, const float4 &pj, uint32_t i, uint32_t j) {
+  float d2;
+  float3 d;
+  sphere_hit(pi, pj, &d2, &d);
+  const float dist = __fsqrt_rn(d2);
+  float3 nn;
+  if (dist > 0.f) {
+    const float id = __frcp_rn(dist);
+    nn = make_float3(__fmul_rn(d.x, id), __fmul_rn(d.y, id), __fmul_rn(d.z, id));
+  } else {
+    nn = make_float3(0.f, 0.f, i > j ? 1.f : -1.f);
+  }
+  return make_float4(nn.x, nn.y, nn.z, __fsub_rn(__fadd_rn(pi.w, pj.w), dist));
+}
+
+// Particle-body contact test (Sec. II-C, Eq. 7): culled by the body's bounding sphere
+// (with a margin far above rounding), then the SDF at the centre in the body frame;
+// true when f <= r_i (y, f and the SDF branch returned for body_geometry).
+__device__ __forceinline__ bool body_touch(const DevBody &B, const float3 &xi, float ri, float3 *y, float *f,
+                                           int *br) {
+  if (B.bound_r > 0.f) {
+    const float dx = xi.x - B.p[0], dy = xi.y - B.p[1], dz = xi.z - B.p[2];
+    const float rb = B.bound_r + ri;
+    if (dx * dx + dy * dy + dz * dz > 1.0001f * rb * rb) return false;
+  }
+  *y = world_to_body(B, xi);
+  *f = body_sdf(B, *y, br);
+  return *f <= ri;
+}
+
+// World normal and psi = r_i - f of a touching body, and the contact point x_i - f n.
+__device__ __forceinline__ void body_geometry(const DevBody &B, const float3 &xi, float ri, const float3 &y, float f,
+                                              int br, float4 *bn, float4 *bxc) {
+  const float3 nn = rot_apply(B.R, body_grad(B, y, br));
+  *bn = make_float4(nn.x, nn.y, nn.z, ri - f);
+  *bxc = make_float4(xi.x - f * nn.x, xi.y - f * nn.y, xi.z - f * nn.z, 0.f);
+}
+
 // Contact records of particle i from its partner list (ascending ids, shared memory,
 // stride S), then its body contacts in ascending body index; counts and U^0.
 __device__ __forceinline__ void contact_records(const StepArgs &a, uint32_t i, float4 pi, uint32_t e, const DevEnv &E,
@@ -345,23 +387,11 @@ __device__ __forceinline__ void contact_records(const StepArgs &a, uint32_t i, f
         const uint32_t c = c0 + q;
         if (c >= npp) break;
         const uint32_t j = jg[q];
-        float d2;
-        float3 d;
-        const float4 pj = pg[q];
-        sphere_hit(pi, pj, &d2, &d);
-        const float dist = __fsqrt_rn(d2);
-        float3 nn;
-        if (dist > 0.f) {
-          const float id = __frcp_rn(dist);
-          nn = make_float3(d.x * id, d.y * id, d.z * id);
-        } else {
-          nn = make_float3(0.f, 0.f, i > j ? 1.f : -1.f);
-        }
-        const float psi = __fsub_rn(__fadd_rn(pi.w, pj.w), dist);
-        psi_max = fmaxf(psi_max, psi);
+        const float4 g = pair_geometry(pi, pg[q], i, j);
+        psi_max = fmaxf(psi_max, g.w);
         const size_t o = (size_t)c * n + i;
         a.cj[o] = j;
-        a.cn[o] = make_float4(nn.x, nn.y, nn.z, psi);
+        a.cn[o] = g;
         a.clam[o] = 0.f;
         a.clam[o + (size_t)K * n] = 0.f;
         a.clam[o + 2 * (size_t)K * n] = 0.f;
@@ -372,23 +402,17 @@ __device__ __forceinline__ void contact_records(const StepArgs &a, uint32_t i, f
     for (uint32_t b = 0; b < E.nbodies; ++b) {
       const uint32_t gb = e * a.maxb + b;
       const DevBody &B = a.bodies[gb];
-      if (B.bound_r > 0.f) {  // outside the bounding sphere (with a margin far above rounding): no contact
-        const float dx = xi.x - B.p[0], dy = xi.y - B.p[1], dz = xi.z - B.p[2];
-        const float rb = B.bound_r + pi.w;
-        if (dx * dx + dy * dy + dz * dz > 1.0001f * rb * rb) continue;
-      }
-      const float3 y = world_to_body(B, xi);
+      float3 y;
+      float f;
       int br;
-      const float f = body_sdf(B, y, &br);
-      if (!(f <= pi.w)) continue;
+      if (!body_touch(B, xi, pi.w, &y, &f, &br)) continue;
       if (nbc == a.Kb) {
         flag(a.ctrl, kFlagBodyOverflow);
         continue;
       }
-      const float3 g = body_grad(B, y, br);
-      const float3 nn = rot_apply(B.R, g);
-      const float psi = pi.w - f;
-      psi_max = fmaxf(psi_max, psi);
+      float4 bn, bxc;
+      body_geometry(B, xi, pi.w, y, f, br, &bn, &bxc);
+      psi_max = fmaxf(psi_max, bn.w);
       const size_t o = (size_t)nbc * n + i;
       if (B.is_free) {
         atomicAdd(&a.ncb[gb], 1u);
@@ -399,8 +423,8 @@ __device__ __forceinline__ void contact_records(const StepArgs &a, uint32_t i, f
           flag(a.ctrl, kFlagBodyOverflow);
       }
       a.bj[o] = gb;
-      a.bn[o] = make_float4(nn.x, nn.y, nn.z, psi);
-      a.bxc[o] = make_float4(xi.x - f * nn.x, xi.y - f * nn.y, xi.z - f * nn.z, 0.f);
+      a.bn[o] = bn;
+      a.bxc[o] = bxc;
       a.blam[o] = 0.f;
       a.blam[o + (size_t)a.Kb * n] = 0.f;
       a.blam[o + 2 * (size_t)a.Kb * n] = 0.f;
@@ -439,18 +463,14 @@ __device__ __forceinline__ void contact_stats(const StepArgs &a, uint32_t npp, u
 // in shared memory, slot p of thread t at [p * blockDim.x + t] (conflict-free): an
 // array indexed at run time in registers would go to local memory, which at full
 // occupancy does not fit in L1.  Dynamic shared memory: K * blockDim.x words.
-// Detection of particle i (Sec. II-B 27-cell query, Sec. II-C SDF tests): its partner
-// list in the thread's shared-memory column fid (stride S), then its contact records.
+// The partner list of particle i (Sec. II-B 27-cell query): ascending ids in the
+// thread's shared-memory column fid (stride S), the K smallest kept (ovf set if more).
 template <bool LISTS>
-__device__ __forceinline__ void detect_particle(const StepArgs &a, uint32_t i, uint32_t *fid, uint32_t S,
-                                                uint32_t &npp, uint32_t &nbc, float &psi_max) {
+__device__ __forceinline__ void walk_partners(const StepArgs &a, uint32_t i, const float4 &pi, const DevEnv &E,
+                                              uint32_t *fid, uint32_t S, uint32_t &npp, bool &ovf) {
   {
-    const float4 pi = a.pos_id[i];
-    const uint32_t e = a.env_of[i];
-    const DevEnv E = a.envs[e];
     const int32_t k0 = cell_of(pi.x, E.inv_cell), k1 = cell_of(pi.y, E.inv_cell), k2 = cell_of(pi.z, E.inv_cell);
     const uint32_t K = a.K;
-    bool ovf = false;
     // Eq. 6 terms of the three cells along each axis, combined 27 ways below
     uint32_t hx[3], hy[3], hz[3];
 #pragma unroll
@@ -599,8 +619,20 @@ __device__ __forceinline__ void detect_particle(const StepArgs &a, uint32_t i, u
       }
     }
     }
-    contact_records(a, i, pi, e, E, fid, S, K, npp, ovf, nbc, psi_max);
   }
+}
+
+// Detection of particle i (Sec. II-B 27-cell query, Sec. II-C SDF tests): its partner
+// list, then its contact records.
+template <bool LISTS>
+__device__ __forceinline__ void detect_particle(const StepArgs &a, uint32_t i, uint32_t *fid, uint32_t S,
+                                                uint32_t &npp, uint32_t &nbc, float &psi_max) {
+  const float4 pi = a.pos_id[i];
+  const uint32_t e = a.env_of[i];
+  const DevEnv E = a.envs[e];
+  bool ovf = false;
+  walk_partners<LISTS>(a, i, pi, E, fid, S, npp, ovf);
+  contact_records(a, i, pi, e, E, fid, S, a.K, npp, ovf, nbc, psi_max);
 }
 
 template <bool LISTS>
@@ -986,6 +1018,80 @@ __global__ void __maxnreg__(40) k_pja_lean(StepArgs a, int s, int it, int rev) {
   if (i < a.n) pja_particle<false, false>(a, i, s, none, it);
 }
 
+
+// OneLoop, the third form of the paper's loop-structure ablation (Sec. II-D, Fig.
+// warp-divergence-performance): every impulse iteration walks the neighbour cells
+// again and computes each contact's response as it finds it, instead of reading the
+// records that detection stored once per step.  The detection launch still runs
+// first, for the contact counts behind the mass-splitting weights, U^0 and the zeroed
+// impulses.  The walk yields the same ascending partner list, the geometry comes from
+// the same helpers (pair_geometry, body_touch, body_geometry) and the impulses keep
+// their ELL slots, so the iterates are bit-identical to the split form (tested).  Not
+// with free bodies (their updates run between sweeps) nor taped steps.
+template <bool LISTS>
+__global__ void __launch_bounds__(kContactsBlock) k_oneloop(StepArgs a, int s) {
+  pdl_enter();
+  extern __shared__ uint32_t s_fid[];
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const float4 pi = a.pos_id[i];
+  const uint32_t e = a.env_of[i];
+  const DevEnv E = a.envs[e];
+  uint32_t *fid = s_fid + threadIdx.x;
+  const uint32_t S = blockDim.x;
+  uint32_t npp = 0;
+  bool ovf = false;
+  walk_partners<LISTS>(a, i, pi, E, fid, S, npp, ovf);
+  const float4 *__restrict__ Uin = a.U[s];
+  float *__restrict__ clam = a.clam;
+  const size_t n = a.n, KN = (size_t)a.K * n, KbN = (size_t)a.Kb * n;
+  const float4 ui = Uin[i];
+  const float4 base = base_velocity(a, a.vel_id[i]);
+  const float pw = a.lit ? 0.f : 1.f;
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  for (uint32_t c = 0; c < npp; ++c) {
+    const uint32_t j = fid[c * S];
+    const float4 g = pair_geometry(pi, a.pos_id[j], i, j);
+    const float4 uj = Uin[j];
+    const size_t o = (size_t)c * n + i;
+    const float3 l = pja_project(make_float3(clam[o], clam[o + KN], clam[o + 2 * KN]),
+                                 make_float3(ui.x - uj.x, ui.y - uj.y, ui.z - uj.z), make_float3(g.x, g.y, g.z),
+                                 a.ab * g.w, 1.0f / (ui.w + pw * uj.w), a.mu);
+    clam[o] = l.x;
+    clam[o + KN] = l.y;
+    clam[o + 2 * KN] = l.z;
+    sx += l.x;
+    sy += l.y;
+    sz += l.z;
+  }
+  const float3 xi = make_float3(pi.x, pi.y, pi.z);
+  uint32_t nbc = 0;
+  for (uint32_t b = 0; b < E.nbodies && nbc < a.Kb; ++b) {
+    const DevBody &B = a.bodies[e * a.maxb + b];
+    float3 y;
+    float f;
+    int br;
+    if (!body_touch(B, xi, pi.w, &y, &f, &br)) continue;
+    float4 bn, bxc;
+    body_geometry(B, xi, pi.w, y, f, br, &bn, &bxc);
+    const size_t o = (size_t)nbc * n + i;
+    const float rx = bxc.x - B.p[0], ry = bxc.y - B.p[1], rz = bxc.z - B.p[2];
+    const float ubx = B.v[0] + (B.w[1] * rz - B.w[2] * ry);
+    const float uby = B.v[1] + (B.w[2] * rx - B.w[0] * rz);
+    const float ubz = B.v[2] + (B.w[0] * ry - B.w[1] * rx);
+    const float3 l = pja_project(make_float3(a.blam[o], a.blam[o + KbN], a.blam[o + 2 * KbN]),
+                                 make_float3(ui.x - ubx, ui.y - uby, ui.z - ubz), make_float3(bn.x, bn.y, bn.z),
+                                 a.ab * bn.w, 1.0f / (ui.w + 0.f), a.mu);
+    a.blam[o] = l.x;
+    a.blam[o + KbN] = l.y;
+    a.blam[o + 2 * KbN] = l.z;
+    sx += l.x;
+    sy += l.y;
+    sz += l.z;
+    ++nbc;
+  }
+  a.U[s ^ 1][i] = make_float4(base.x + base.w * sx, base.y + base.w * sy, base.z + base.w * sz, ui.w);
+}
 
 // Grid-wide barrier of a cooperative launch (all blocks resident).  The wait is
 // bounded: past `limit` SM cycles it latches kFlagTimeout and sets bar_abort, after
@@ -1635,6 +1741,13 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
     cfg.numAttrs = 1;
     if ((e = cudaLaunchKernelEx(&cfg, k_pja_fused, a, ls.iters)) != cudaSuccess) return e;
     after_kernel = true;
+  } else if (ls.one && !tp && !a.F && a.n) {
+    const size_t smem = (size_t)a.K * kContactsBlock * sizeof(uint32_t);
+    for (uint32_t it = 0; it < ls.iters; ++it)
+      if (a.lists)
+        GG_LAUNCH(k_oneloop<true>, dim3(grid_for(a.n, kContactsBlock)), kContactsBlock, smem, a, (int)(it & 1));
+      else
+        GG_LAUNCH(k_oneloop<false>, dim3(grid_for(a.n, kContactsBlock)), kContactsBlock, smem, a, (int)(it & 1));
   } else
   for (uint32_t it = 0; it < ls.iters; ++it) {
     const int rev = (ls.serp && !tp && it % 2 == 0) ? 1 : 0;  // serpentine: reverse sweeps 0, 2, 4, ...

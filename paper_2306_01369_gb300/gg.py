@@ -125,7 +125,7 @@ def load():
     return _lib
 
 
-TUNE_BITS = {"lists": 1, "fused": 2, "lean": 4, "half": 8, "detect": 16, "serp": 32, "preload": 64}   # GG_TUNE_* of gg.h
+TUNE_BITS = {"lists": 1, "fused": 2, "lean": 4, "half": 8, "detect": 16, "serp": 32, "preload": 64, "oneloop": 128}   # GG_TUNE_* of gg.h
 
 
 def tuning_flags(k):

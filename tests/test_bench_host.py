@@ -11,6 +11,7 @@ def test_stage_kernels_follow_the_tuning_flags():
     assert bench.stage_kernels({"lean"})[0] == "k_pja_lean"
     assert bench.stage_kernels({"fused"})[0] == "k_pja_fused"
     assert bench.stage_kernels({"detect", "lists"}) == ("k_detect_sweeps", "k_detect_sweeps")
+    assert bench.stage_kernels({"oneloop", "lists"}) == ("k_oneloop", "k_contacts")
     assert bench.profile_traffic("k_pja", "column_pile", "x") is None     # no profile kept for it
 
 
