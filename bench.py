@@ -601,9 +601,9 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
                 sim.step(1000, stream=stream)
                 row[name] = _timed_steps(sim, 100, stream, torch) / 100
                 sim.close()
-            loops[f"n{nc}"] = {"ms_per_step": row, "split_speedup": {k: v / row["TwoLoopsSplit"] for k, v in row.items()}}
+            loops[f"n{nc}"] = {"ms_per_step": row, "time_vs_split": {k: v / row["TwoLoopsSplit"] for k, v in row.items()}}
         out["loop_structure"] = {"workload": "columns of 1,024-262,144 spheres (same recipe), steps 1000-1100, "
-                                             "lists binning, n_h = 2n; split_speedup = form's time / split time",
+                                             "lists binning, n_h = 2n; time_vs_split = the form's step time / the split form's",
                                  "sets": {name: k for name, k in forms}, "configs": loops}
     # excavation: 1,048,576 spheres, scoop, two free cubes, I = 30
     if time.perf_counter() - t_start < seconds_cap:

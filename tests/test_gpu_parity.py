@@ -516,7 +516,7 @@ def _lists_differ(og, jg, oo, jo):
 
 def _column_check(gg, orc, column_800, tuning, hash_factor):
     """One step: bit-exact keys, sort order and contacts, per-particle velocities and
-    positions.  Ten steps (the benchmark spec: within 1e-3 r_i): the two runs then take their
+    positions.  Ten steps (the bar: within 1e-3 r_i): the two runs then take their
     contact decisions from their own states, FP32 and FP64, which differ by ~1e-5 r
     after a few steps, so a pair whose gap is within that distance of zero can be in
     contact on one side only; such a pair's impulse sends both of its spheres (and
