@@ -350,7 +350,12 @@ GG_API uint32_t gg_kernels_per_step(const gg_sim *sim);
  * differentiation).  Single environment, kinematic bodies only.
  *
  * gg_tape_reserve: allocate checkpoint and tape memory for n_steps taped steps with a
- *   full-state checkpoint every `checkpoint_every` steps (recompute in between).
+ *   full-state checkpoint every `checkpoint_every` steps (recompute in between).  The
+ *   reverse pass recomputes a segment once, keeping every step's contact arrays and
+ *   iterates, so the tape memory is min(checkpoint_every, n_steps) step tapes of
+ *   about n ((I + 1) (16 + 12 K + 12 Kb) + 20 K + 36 Kb + 4) bytes each (K, Kb: the
+ *   contact capacities, I: the sweeps per step); GG_ERR_OOM if it does not fit
+ *   (a smaller checkpoint_every needs less).
  * gg_step_taped: enqueue n_steps (<= reserved) forward steps saving the checkpoints;
  *   the tool's twist for those steps must come from gg_set_trajectory.
  * gg_backward: gradients of L given dL/dx_N (float[n][3]), dL/dv_N (float[n][3]; NULL

@@ -89,12 +89,15 @@ struct gg_sim {
   float *render_out = nullptr;     // ... device image for host destinations, ...
   float4 *render_rays = nullptr;   // ... and the depth camera's per-pixel rays
   size_t render_px = 0;
-  // differentiation: checkpoints, per-step tape, adjoint buffers
+  // differentiation: checkpoints, the tapes of one segment, adjoint buffers
   struct {
-    uint32_t n_steps = 0, K = 0, taped = 0, tool = 0xffffffffu;
+    uint32_t n_steps = 0, K = 0, slots = 0, taped = 0, tool = 0xffffffffu;
     size_t state_bytes = 0;
     char *ckpt = nullptr, *seg = nullptr, *fin = nullptr;
-    gg::Tape tp{};
+    gg::Tape tp{};  // slot 0's tape; slot k's starts k tapes further
+    // each step of a segment keeps its own contact arrays (slot k at k times the size)
+    uint32_t *ccount = nullptr, *cj = nullptr, *bj = nullptr;
+    float4 *cn = nullptr, *bn = nullptr, *bxc = nullptr;
     gg::AdjArgs d{};
     std::vector<void *> allocs;
   } ad;
@@ -448,6 +451,29 @@ gg_status capture(gg_sim *s) {
   s->graph[t] = g;
   GG_CUDA(s, cudaGraphInstantiate(&s->exec[t], g, 0));
   return GG_OK;
+}
+
+// The step arguments of segment slot k: the simulation's, with that slot's contact arrays.
+gg::StepArgs slot_args(const gg_sim *s, uint32_t k) {
+  gg::StepArgs a = s->a;
+  const size_t n = s->n, KN = (size_t)s->K * n, KbN = (size_t)s->Kb * n;
+  a.ccount = s->ad.ccount + k * n;
+  a.cj = s->ad.cj + k * KN;
+  a.cn = s->ad.cn + k * KN;
+  a.bj = s->ad.bj + k * KbN;
+  a.bn = s->ad.bn + k * KbN;
+  a.bxc = s->ad.bxc + k * KbN;
+  return a;
+}
+
+// The tape of segment slot k.
+gg::Tape slot_tape(const gg_sim *s, uint32_t k) {
+  gg::Tape t = s->ad.tp;
+  const size_t n = s->n, I = s->ls.iters, KN = (size_t)s->K * n, KbN = (size_t)s->Kb * n;
+  t.Uh += k * (I + 1) * n;
+  t.lamh += k * (I + 1) * 3 * KN;
+  t.blamh += k * (I + 1) * 3 * KbN;
+  return t;
 }
 
 }  // namespace
@@ -1226,12 +1252,16 @@ gg_status gg_tape_reserve(gg_sim *s, uint32_t n_steps, uint32_t K) {
   const uint32_t nblk = gg::adjoint_blocks(s->n);
   s->ad.state_bytes = (state_bytes(s) + 255) / 256 * 256;
   const size_t nck = (n_steps + K - 1) / K;
+  const size_t slots = std::min(K, n_steps);  // steps of a segment, each with its own tape
   gg::Tape &tp = s->ad.tp;
   gg::AdjArgs &d = s->ad.d;
   gg_status rc;
   if ((rc = ad_alloc(s, &s->ad.ckpt, nck * s->ad.state_bytes)) || (rc = ad_alloc(s, &s->ad.seg, (size_t)K * s->ad.state_bytes)) ||
-      (rc = ad_alloc(s, &s->ad.fin, s->ad.state_bytes)) || (rc = ad_alloc(s, &tp.Uh, (I + 1) * n)) ||
-      (rc = ad_alloc(s, &tp.lamh, (I + 1) * 3 * KN)) || (rc = ad_alloc(s, &tp.blamh, (I + 1) * 3 * KbN)) ||
+      (rc = ad_alloc(s, &s->ad.fin, s->ad.state_bytes)) || (rc = ad_alloc(s, &tp.Uh, slots * (I + 1) * n)) ||
+      (rc = ad_alloc(s, &tp.lamh, slots * (I + 1) * 3 * KN)) || (rc = ad_alloc(s, &tp.blamh, slots * (I + 1) * 3 * KbN)) ||
+      (rc = ad_alloc(s, &s->ad.ccount, slots * n)) || (rc = ad_alloc(s, &s->ad.cj, slots * KN)) ||
+      (rc = ad_alloc(s, &s->ad.cn, slots * KN)) || (rc = ad_alloc(s, &s->ad.bj, slots * KbN)) ||
+      (rc = ad_alloc(s, &s->ad.bn, slots * KbN)) || (rc = ad_alloc(s, &s->ad.bxc, slots * KbN)) ||
       (rc = ad_alloc(s, &d.twin, KN)) || (rc = ad_alloc(s, &d.Ubar[0], n)) || (rc = ad_alloc(s, &d.Ubar[1], n)) ||
       (rc = ad_alloc(s, &d.ubar[0], 3 * KN)) || (rc = ad_alloc(s, &d.ubar[1], 3 * KN)) || (rc = ad_alloc(s, &d.Lbar, 3 * KN)) || (rc = ad_alloc(s, &d.bLbar, 3 * KbN)) ||
       (rc = ad_alloc(s, &d.psibar, KN)) || (rc = ad_alloc(s, &d.nbar, 3 * KN)) || (rc = ad_alloc(s, &d.bpsibar, KbN)) ||
@@ -1247,8 +1277,10 @@ gg_status gg_tape_reserve(gg_sim *s, uint32_t n_steps, uint32_t K) {
   d.tool = 0xffffffffu;
   s->ad.n_steps = n_steps;
   s->ad.K = K;
+  s->ad.slots = (uint32_t)slots;
   return GG_OK;
 }
+
 
 gg_status gg_step_taped(gg_sim *s, uint32_t tool_body, uint32_t n_steps, void *stream) {
   if (!s) return GG_ERR_INVALID_ARG;
@@ -1318,36 +1350,47 @@ gg_status gg_backward(gg_sim *s, const float *dL_dpos, const float *dL_dvel, con
   GG_CUDA(s, cudaMemcpyAsync(d.pose_bar, pose6, sizeof(pose6), cudaMemcpyHostToDevice, st));
   GG_CUDA(s, cudaMemsetAsync(d.mubar, 0, sizeof(double), st));
   GG_CUDA(s, cudaStreamSynchronize(st));  // pose6 lives on this stack frame
-  if (!s->exec[s->timing]) {
-    gg_status rc = capture(s);
-    if (rc != GG_OK) return rc;
-  }
-  // one step of the reverse pass (the taped forward of the step, then its adjoint) as
-  // a graph: the work does not depend on the step index (the adjoint reads it from the
-  // step counter restored with the state), so it is captured once per call
-  cudaGraphExec_t bexec = nullptr;
+  // Each checkpoint segment is recomputed with taped full steps, every step keeping its
+  // contact arrays and its sweeps' iterates in a slot of its own, and then reversed from
+  // its last step: the body frames of the step restored, then its adjoint.  One graph
+  // per slot and direction (the slot's arrays are baked in; the adjoint reads the step
+  // index from the step counter restored with the state), captured once per call.
+  const uint32_t slots = s->ad.slots;
+  std::vector<cudaGraphExec_t> fwd(slots, nullptr), adj(slots, nullptr);
+  struct ExecGuard {  // the graphs are destroyed on every return below, after their launches
+    std::vector<cudaGraphExec_t> *v[2];
+    cudaStream_t st;
+    ~ExecGuard() {
+      cudaStreamSynchronize(st);
+      for (auto *x : v)
+        for (cudaGraphExec_t g : *x)
+          if (g) cudaGraphExecDestroy(g);
+    }
+  } guard{{&fwd, &adj}, st};
   {
     const gg::DevCtrl *ctrl0 = reinterpret_cast<const gg::DevCtrl *>(
         s->ad.ckpt + (size_t)n * 32 + (size_t)s->n_envs * s->maxb * sizeof(DevBody));
-    GG_CUDA(s, cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e1 = gg::enqueue_step(s->a, s->ls, s->cap, nullptr, &s->ad.tp);
-    if (e1 == cudaSuccess) e1 = gg::enqueue_adjoint_step(s->a, d, ctrl0, N, s->cap);
-    cudaGraph_t g = nullptr;
-    const cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
-    if (e1 == cudaSuccess && e2 == cudaSuccess) e1 = cudaGraphInstantiate(&bexec, g, 0);
-    if (g) cudaGraphDestroy(g);
-    if (e1 != cudaSuccess || e2 != cudaSuccess) return cuda_fail(s, e1 != cudaSuccess ? e1 : e2, "capturing the reverse step");
-  }
-  struct ExecGuard {  // the graph is destroyed on every return below, after its launches
-    cudaGraphExec_t *x;
-    cudaStream_t st;
-    ~ExecGuard() {
-      if (*x) {
-        cudaStreamSynchronize(st);
-        cudaGraphExecDestroy(*x);
+    for (uint32_t k = 0; k < 2 * slots; ++k) {
+      const uint32_t slot = k % slots;
+      const gg::StepArgs ak = slot_args(s, slot);
+      gg::AdjArgs dk = d;
+      dk.tp = slot_tape(s, slot);
+      GG_CUDA(s, cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e1;
+      if (k < slots) {
+        e1 = gg::enqueue_step(ak, s->ls, s->cap, nullptr, &dk.tp, true);
+      } else {
+        e1 = gg::enqueue_prep_bodies(ak, s->cap);
+        if (e1 == cudaSuccess) e1 = gg::enqueue_adjoint_step(ak, dk, ctrl0, N, s->cap);
       }
+      cudaGraph_t g = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
+      if (e1 == cudaSuccess && e2 == cudaSuccess) e1 = cudaGraphInstantiate(k < slots ? &fwd[slot] : &adj[slot], g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e1 != cudaSuccess || e2 != cudaSuccess)
+        return cuda_fail(s, e1 != cudaSuccess ? e1 : e2, "capturing the reverse pass");
     }
-  } guard{&bexec, st};
+  }
   // An error inside the segment loop would leave the simulation at an intermediate
   // checkpoint: put the end state of the taped run back on every return before the
   // loop completes (destroyed before `guard`, so the copy is queued before its wait).
@@ -1364,13 +1407,13 @@ gg_status gg_backward(gg_sim *s, const float *dL_dpos, const float *dL_dvel, con
     const uint32_t k0 = (uint32_t)seg * K, k1 = std::min(k0 + K, N);
     gg_status rc = restore_state(s, s->ad.ckpt + (size_t)seg * s->ad.state_bytes, st);
     if (rc != GG_OK) return rc;
-    for (uint32_t k = k0; k < k1; ++k) {  // recompute the segment's step-start states
+    for (uint32_t k = k0; k < k1; ++k) {  // taped recompute, each step's start state kept
       if ((rc = save_state(s, s->ad.seg + (size_t)(k - k0) * s->ad.state_bytes, st)) != GG_OK) return rc;
-      if (k + 1 < k1) GG_CUDA(s, cudaGraphLaunch(s->exec[s->timing], st));
+      GG_CUDA(s, cudaGraphLaunch(fwd[k - k0], st));
     }
-    for (int k = (int)k1 - 1; k >= (int)k0; --k) {  // reverse the steps: taped forward + adjoint
+    for (int k = (int)k1 - 1; k >= (int)k0; --k) {  // the steps' adjoints, last first
       if ((rc = restore_state(s, s->ad.seg + (size_t)(k - k0) * s->ad.state_bytes, st)) != GG_OK) return rc;
-      GG_CUDA(s, cudaGraphLaunch(bexec, st));
+      GG_CUDA(s, cudaGraphLaunch(adj[k - k0], st));
     }
   }
 

@@ -45,10 +45,13 @@ int fused_pja_blocks_per_sm(int block);
 int detect_sweeps_blocks_per_sm(bool lists, uint32_t K);
 
 // ev (optional): 5 events recorded at the stage boundaries of the step.
-// tape (optional): keep every sweep's iterates and stop after the sweeps (no
-// integration, wrench or pose update): the first half of a step for the adjoint.
+// tape (optional): keep every sweep's iterates; unless `whole`, stop after the sweeps
+// (no integration, wrench or pose update).  With `whole` the taped step is a full step.
 cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st, cudaEvent_t *ev = nullptr,
-                         const Tape *tape = nullptr);
+                         const Tape *tape = nullptr, bool whole = false);
+// the body frames and velocities of the step in the device step counter (as the step's
+// binning kernel sets them), for an adjoint run on a restored state
+cudaError_t enqueue_prep_bodies(const StepArgs &a, cudaStream_t st);
 uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls);
 // the counting sort of the keys of the last binning (for the sort-order readbacks when
 // the step bins by linked lists)

@@ -101,6 +101,13 @@ __device__ void prep_body(const StepArgs &a, uint32_t gb) {
   }
 }
 
+// The body frames and velocities of the step in the device step counter (prep_body)
+// alone: the reverse pass runs it on the state restored for a step, before its adjoint.
+__global__ void k_prep_bodies(StepArgs a) {
+  const uint32_t gb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gb < a.n_envs * a.maxb) prep_body(a, gb);
+}
+
 // Histogram of the stored keys (the sort-order readbacks of a step that binned by lists).
 __global__ void k_hist_keys(StepArgs a) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1648,7 +1655,8 @@ uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls) {
   return k;
 }
 
-cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st, cudaEvent_t *ev, const Tape *tp) {
+cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t st, cudaEvent_t *ev, const Tape *tp,
+                         bool whole) {
   cudaError_t e;
   const uint32_t nbt = a.n_envs * a.maxb;
   const uint32_t nk = a.n > nbt ? a.n : nbt;
@@ -1765,14 +1773,14 @@ cudaError_t enqueue_step(const StepArgs &a, const LaunchShape &ls, cudaStream_t 
     }
     if (a.F) GG_LAUNCH(k_free_update, dim3(a.F), 256, 0, a);
   }
-  if (tp) {  // the taped step ends here; empty the lists it filled
+  if (tp && !whole) {  // the taped step ends here; empty the lists it filled
     if (a.lists) GG_LAUNCH(k_list_clear, dim3(std::min<uint32_t>(grid_for(a.nh_total, 256), 4096u)), 256, 0, a);
     return cudaGetLastError();
   }
   GG_MARK(3);
   if (a.n_chunks)
     GG_LAUNCH(k_integrate_wrench, dim3(a.n_chunks), kIntegrateThreads, 0, a, (int)(ls.iters & 1),
-              (int)(ls.serp && ls.iters % 2 == 0));
+              (int)(ls.serp && !tp && ls.iters % 2 == 0));
   GG_LAUNCH(k_wrench_bodies, dim3(nbt), kWrenchBodyThreads, 0, a);
   GG_MARK(4);
 #undef GG_LAUNCH
@@ -1811,6 +1819,12 @@ int detect_sweeps_blocks_per_sm(bool lists, uint32_t K) {
     return 0;
   }
   return per;
+}
+
+cudaError_t enqueue_prep_bodies(const StepArgs &a, cudaStream_t st) {
+  const uint32_t nbt = a.n_envs * a.maxb;
+  if (nbt) k_prep_bodies<<<grid_for(nbt, 128), 128, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t enqueue_export_contacts(const StepArgs &a, uint32_t *rows, float *geom, float *lam, float *bgeom,
