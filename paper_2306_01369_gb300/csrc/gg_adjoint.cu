@@ -16,6 +16,8 @@
 //   k_adj_tool      fixed-order sums, tool pose chain (p, R) -> twist gradient
 // No floating-point atomics: every sum is per particle in contact order, per block
 // in a fixed tree, then over blocks in index order.
+#include <algorithm>
+
 #include "gg_device.cuh"
 #include "gg_internal.h"
 
@@ -507,7 +509,27 @@ __global__ void __launch_bounds__(kToolThreads) k_adj_tool(StepArgs a, AdjArgs d
 
 inline unsigned blocks(uint32_t n) { return n ? (n + kAdjThreads - 1) / kAdjThreads : 1; }
 
+// Up to four word regions copied in one launch (grid-stride over their concatenation).
+__global__ void k_copy_regions(CopyRegions c) {
+  size_t total = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) total += c.words[r];
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    size_t w = t;
+    int r = 0;
+    while (r < 3 && w >= c.words[r]) w -= c.words[r++];
+    c.dst[r][w] = c.src[r][w];
+  }
+}
+
 }  // namespace
+
+cudaError_t enqueue_copy_regions(const CopyRegions &c, cudaStream_t st) {
+  size_t total = 0;
+  for (int r = 0; r < 4; ++r) total += c.words[r];
+  if (total) k_copy_regions<<<(unsigned)std::min<size_t>((total + 255) / 256, 1024), 256, 0, st>>>(c);
+  return cudaGetLastError();
+}
 
 uint32_t adjoint_blocks(uint32_t n) { return blocks(n); }
 

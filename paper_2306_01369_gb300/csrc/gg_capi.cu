@@ -466,6 +466,26 @@ gg::StepArgs slot_args(const gg_sim *s, uint32_t k) {
   return a;
 }
 
+// The state regions (the layout save_state writes) between the simulation and `buf`,
+// as one copy launch: saving (to buf) or restoring (from buf).
+gg::CopyRegions state_regions(gg_sim *s, char *buf, bool save) {
+  static_assert(sizeof(DevBody) % 4 == 0 && sizeof(DevCtrl) % 4 == 0, "state regions are copied as words");
+  const size_t n = s->n, nbt = (size_t)s->n_envs * s->maxb;
+  uint32_t *live[4] = {reinterpret_cast<uint32_t *>(s->a.pos_id), reinterpret_cast<uint32_t *>(s->a.vel_id),
+                       reinterpret_cast<uint32_t *>(s->a.bodies), reinterpret_cast<uint32_t *>(s->a.ctrl)};
+  uint32_t *saved[4] = {reinterpret_cast<uint32_t *>(buf), reinterpret_cast<uint32_t *>(buf + n * 16),
+                        reinterpret_cast<uint32_t *>(buf + n * 32),
+                        reinterpret_cast<uint32_t *>(buf + n * 32 + nbt * sizeof(DevBody))};
+  const size_t words[4] = {4 * n, 4 * n, nbt * sizeof(DevBody) / 4, sizeof(DevCtrl) / 4};
+  gg::CopyRegions c{};
+  for (int r = 0; r < 4; ++r) {
+    c.dst[r] = save ? saved[r] : live[r];
+    c.src[r] = save ? live[r] : saved[r];
+    c.words[r] = words[r];
+  }
+  return c;
+}
+
 // The tape of segment slot k.
 gg::Tape slot_tape(const gg_sim *s, uint32_t k) {
   gg::Tape t = s->ad.tp;
@@ -1354,7 +1374,8 @@ gg_status gg_backward(gg_sim *s, const float *dL_dpos, const float *dL_dvel, con
   // contact arrays and its sweeps' iterates in a slot of its own, and then reversed from
   // its last step: the body frames of the step restored, then its adjoint.  One graph
   // per slot and direction (the slot's arrays are baked in; the adjoint reads the step
-  // index from the step counter restored with the state), captured once per call.
+  // index from the step counter restored with the state), captured when first needed,
+  // so that the host captures the next graph while the device runs the previous one.
   const uint32_t slots = s->ad.slots;
   std::vector<cudaGraphExec_t> fwd(slots, nullptr), adj(slots, nullptr);
   struct ExecGuard {  // the graphs are destroyed on every return below, after their launches
@@ -1367,30 +1388,35 @@ gg_status gg_backward(gg_sim *s, const float *dL_dpos, const float *dL_dvel, con
           if (g) cudaGraphExecDestroy(g);
     }
   } guard{{&fwd, &adj}, st};
-  {
-    const gg::DevCtrl *ctrl0 = reinterpret_cast<const gg::DevCtrl *>(
-        s->ad.ckpt + (size_t)n * 32 + (size_t)s->n_envs * s->maxb * sizeof(DevBody));
-    for (uint32_t k = 0; k < 2 * slots; ++k) {
-      const uint32_t slot = k % slots;
+  const gg::DevCtrl *ctrl0 = reinterpret_cast<const gg::DevCtrl *>(
+      s->ad.ckpt + (size_t)n * 32 + (size_t)s->n_envs * s->maxb * sizeof(DevBody));
+  auto launch_slot = [&](bool reverse, uint32_t slot) -> gg_status {
+    cudaGraphExec_t &x = reverse ? adj[slot] : fwd[slot];
+    if (!x) {
       const gg::StepArgs ak = slot_args(s, slot);
       gg::AdjArgs dk = d;
       dk.tp = slot_tape(s, slot);
+      // the forward graph first saves the step's start state into the slot, the reverse
+      // graph first restores it
+      const gg::CopyRegions cr = state_regions(s, s->ad.seg + (size_t)slot * s->ad.state_bytes, !reverse);
       GG_CUDA(s, cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e1;
-      if (k < slots) {
+      cudaError_t e1 = gg::enqueue_copy_regions(cr, s->cap);
+      if (e1 == cudaSuccess && !reverse) {
         e1 = gg::enqueue_step(ak, s->ls, s->cap, nullptr, &dk.tp, true);
-      } else {
+      } else if (e1 == cudaSuccess) {
         e1 = gg::enqueue_prep_bodies(ak, s->cap);
         if (e1 == cudaSuccess) e1 = gg::enqueue_adjoint_step(ak, dk, ctrl0, N, s->cap);
       }
       cudaGraph_t g = nullptr;
       const cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
-      if (e1 == cudaSuccess && e2 == cudaSuccess) e1 = cudaGraphInstantiate(k < slots ? &fwd[slot] : &adj[slot], g, 0);
+      if (e1 == cudaSuccess && e2 == cudaSuccess) e1 = cudaGraphInstantiate(&x, g, 0);
       if (g) cudaGraphDestroy(g);
       if (e1 != cudaSuccess || e2 != cudaSuccess)
         return cuda_fail(s, e1 != cudaSuccess ? e1 : e2, "capturing the reverse pass");
     }
-  }
+    GG_CUDA(s, cudaGraphLaunch(x, st));
+    return GG_OK;
+  };
   // An error inside the segment loop would leave the simulation at an intermediate
   // checkpoint: put the end state of the taped run back on every return before the
   // loop completes (destroyed before `guard`, so the copy is queued before its wait).
@@ -1407,14 +1433,10 @@ gg_status gg_backward(gg_sim *s, const float *dL_dpos, const float *dL_dvel, con
     const uint32_t k0 = (uint32_t)seg * K, k1 = std::min(k0 + K, N);
     gg_status rc = restore_state(s, s->ad.ckpt + (size_t)seg * s->ad.state_bytes, st);
     if (rc != GG_OK) return rc;
-    for (uint32_t k = k0; k < k1; ++k) {  // taped recompute, each step's start state kept
-      if ((rc = save_state(s, s->ad.seg + (size_t)(k - k0) * s->ad.state_bytes, st)) != GG_OK) return rc;
-      GG_CUDA(s, cudaGraphLaunch(fwd[k - k0], st));
-    }
-    for (int k = (int)k1 - 1; k >= (int)k0; --k) {  // the steps' adjoints, last first
-      if ((rc = restore_state(s, s->ad.seg + (size_t)(k - k0) * s->ad.state_bytes, st)) != GG_OK) return rc;
-      GG_CUDA(s, cudaGraphLaunch(adj[k - k0], st));
-    }
+    for (uint32_t k = k0; k < k1; ++k)  // taped recompute, each step's start state kept
+      if ((rc = launch_slot(false, k - k0)) != GG_OK) return rc;
+    for (int k = (int)k1 - 1; k >= (int)k0; --k)  // the steps' adjoints, last first
+      if ((rc = launch_slot(true, (uint32_t)(k - k0))) != GG_OK) return rc;
   }
 
   fin_guard.done = true;

@@ -63,6 +63,13 @@ cudaError_t enqueue_sort_from_keys(const StepArgs &a, cudaStream_t st);
 cudaError_t enqueue_adjoint_step(const StepArgs &a, const AdjArgs &d, const DevCtrl *ctrl0, uint32_t n_taped,
                                  cudaStream_t st);
 uint32_t adjoint_blocks(uint32_t n);
+// up to four regions of 32-bit words (unused ones with zero words), copied in one launch
+struct CopyRegions {
+  uint32_t *dst[4];
+  const uint32_t *src[4];
+  size_t words[4];
+};
+cudaError_t enqueue_copy_regions(const CopyRegions &c, cudaStream_t st);
 // Depth observation (gg_render): everything the kernels need, precomputed on the host.
 struct RenderArgs {
   uint32_t kind, W, H;
