@@ -748,3 +748,25 @@ def test_crowded_bucket_is_reported_quickly(gg):
     ok = gg.Sim(pr2, vel2, S.sphere_mass(pr2[:, 3]), S.Params(dt=1e-4, max_contacts=32))
     ok.step(2)
     ok.sync()
+
+
+@pytest.mark.parametrize("n", [1, 3, 4, 5, 4097])
+def test_pinned_transfers_ragged_and_misaligned(gg, torch, n):
+    """set_particles from pinned host buffers (velocities 16-byte aligned or not) and the
+    POS_VEL readback into a pinned buffer move every value bit for bit, whatever n mod 4."""
+    pr0, vel = S.random_cloud(n, seed=31 + n, box=0.5, vel_scale=0.2)
+    pr = pr0.copy()
+    pr[:, :3] += np.float32(0.01)
+    p = S.Params(dt=1e-4, gravity=(0, 0, 0))
+    for shift in (0, 1):   # velocity buffer at a 16-byte boundary, and 4 bytes past one
+        sim = gg.Sim(pr0, np.zeros_like(vel), S.sphere_mass(pr0[:, 3]), p)
+        pos_h = torch.from_numpy(pr.copy()).pin_memory()
+        vbuf = torch.zeros(3 * n + 4, dtype=torch.float32).pin_memory()
+        vbuf[shift:shift + 3 * n] = torch.from_numpy(vel.reshape(-1))
+        sim.set_particles(pos_h, vbuf[shift:shift + 3 * n].view(n, 3))
+        assert np.array_equal(sim.pos(), pr) and np.array_equal(sim.vel(), vel)
+        out = torch.full((7 * n,), -1.0, dtype=torch.float32).pin_memory()
+        sim.read("POS_VEL", out=out)
+        o = out.numpy()
+        assert np.array_equal(o[:4 * n].reshape(n, 4), pr) and np.array_equal(o[4 * n:].reshape(n, 3), vel)
+        sim.close()
