@@ -534,7 +534,7 @@ cudaError_t enqueue_copy_regions(const CopyRegions &c, cudaStream_t st) {
 uint32_t adjoint_blocks(uint32_t n) { return blocks(n); }
 
 // The step's adjoint kernels, chained with programmatic dependent launch (every one
-// begins with pdl_enter); the first follows the taped forward's last sweep.
+// begins with pdl_enter); the first follows the body-frame kernel of the step.
 cudaError_t enqueue_adjoint_step(const StepArgs &a, const AdjArgs &d, const DevCtrl *ctrl0, uint32_t n_taped,
                                  cudaStream_t st) {
   const dim3 g(blocks(a.n));

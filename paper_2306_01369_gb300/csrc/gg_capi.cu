@@ -1301,7 +1301,6 @@ gg_status gg_tape_reserve(gg_sim *s, uint32_t n_steps, uint32_t K) {
   return GG_OK;
 }
 
-
 gg_status gg_step_taped(gg_sim *s, uint32_t tool_body, uint32_t n_steps, void *stream) {
   if (!s) return GG_ERR_INVALID_ARG;
   if (!s->ad.ckpt || n_steps == 0 || n_steps > s->ad.n_steps)

@@ -56,10 +56,10 @@ uint32_t kernels_per_step(const StepArgs &a, const LaunchShape &ls);
 // the counting sort of the keys of the last binning (for the sort-order readbacks when
 // the step bins by linked lists)
 cudaError_t enqueue_sort_from_keys(const StepArgs &a, cudaStream_t st);
-// reverse of one taped step (after enqueue_step with a tape, which stops after the sweeps)
-// The adjoint of one step (after that step's taped forward); the step index is the
-// device step counter less ctrl0->step (the counter saved with the taped run's first
-// checkpoint), so the enqueued work does not depend on it.
+// The adjoint of one step, on that step's start state with its body frames set
+// (enqueue_prep_bodies) and with the contact arrays and tape its taped forward left;
+// the step index is the device step counter less ctrl0->step (the counter saved with
+// the taped run's first checkpoint), so the enqueued work does not depend on it.
 cudaError_t enqueue_adjoint_step(const StepArgs &a, const AdjArgs &d, const DevCtrl *ctrl0, uint32_t n_taped,
                                  cudaStream_t st);
 uint32_t adjoint_blocks(uint32_t n);
