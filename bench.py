@@ -793,10 +793,8 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     barrier(world)
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        sim.set_particles(pos_h, vel_h, stream=stream)
-        sim.step(1, stream=stream)
-        sim.read("POS_VEL", out=state_h, stream=stream)
+    for _ in range(e2e_steps):   # gg_step_io: the state in, one step, the new state out, waited for
+        sim.step_io(pos_h, vel_h, state_h, stream=stream)
     torch.cuda.synchronize(dev)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e_val = sum_over_ranks(float(sc.n * e2e_steps), world, dev) / e2e_s

@@ -271,6 +271,19 @@ GG_API gg_status gg_step(gg_sim *sim, uint32_t n_steps, void *stream);
 /* Wait for `stream` and report the latched device status (GG_OK or the first error). */
 GG_API gg_status gg_sync(gg_sim *sim, void *stream);
 
+/*
+ * One turn of a host-driven loop: the particle state from host buffers (pos_radius
+ * float[n][4], vel float[n][3] or NULL to keep the velocities), one time step, and the
+ * new state into out (float[7 n]: positions float[n][4], then velocities float[n][3],
+ * the GG_FIELD_POS_VEL layout), waited for.  The same work and results, bit for bit, as
+ * gg_set_particles + gg_step(1) + gg_readback(GG_FIELD_POS_VEL).  When all three host
+ * buffers are pinned (positions and out 16-byte aligned) and stage timing is off, the
+ * transfers and the step are one graph (kept while the buffers' device addresses and
+ * the launch shape stay the same); otherwise the three calls run.  Host buffers only
+ * (device tensors: the three calls).  Returns the step's status like gg_readback.
+ */
+GG_API gg_status gg_step_io(gg_sim *sim, const float *pos_radius, const float *vel, float *out, void *stream);
+
 /* Size in bytes of a readback field. */
 GG_API size_t gg_field_bytes(const gg_sim *sim, gg_field field);
 

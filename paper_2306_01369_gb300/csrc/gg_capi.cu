@@ -80,6 +80,10 @@ struct gg_sim {
   // the step graph, captured lazily: [0] plain, [1] with the stage-timing events
   cudaGraph_t graph[2] = {};
   cudaGraphExec_t exec[2] = {};
+  // gg_step_io: pinned inputs -> one step -> pinned outputs as one graph, for the
+  // device addresses of the last buffers it was given
+  cudaGraphExec_t io_exec = nullptr;
+  const void *io_ptr[3] = {};
   uint64_t steps = 0;
   void *staging = nullptr;
   size_t staging_bytes = 0;
@@ -172,6 +176,9 @@ void free_graph(gg_sim *s) {
     s->exec[t] = nullptr;
     s->graph[t] = nullptr;
   }
+  if (s->io_exec) cudaGraphExecDestroy(s->io_exec);
+  s->io_exec = nullptr;
+  for (const void *&p : s->io_ptr) p = nullptr;
 }
 
 gg_status ensure_staging(gg_sim *s, size_t bytes) {
@@ -1043,6 +1050,51 @@ gg_status gg_step(gg_sim *s, uint32_t n_steps, void *stream) {
   for (uint32_t k = 0; k < n_steps; ++k) GG_CUDA(s, cudaGraphLaunch(s->exec[s->timing], st));
   s->steps += n_steps;
   return GG_OK;
+}
+
+gg_status gg_step_io(gg_sim *s, const float *pos_radius, const float *vel, float *out, void *stream) {
+  if (!s || !pos_radius || !out) return s ? fail(s, GG_ERR_INVALID_ARG, "gg_step_io: null buffer") : GG_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const void *dp = pinned_device_ptr(pos_radius);
+  const void *dv = vel ? pinned_device_ptr(vel) : nullptr;
+  void *dout = pinned_device_ptr(out);
+  const bool one_graph = s->n && !s->timing && dp && (!vel || dv) && dout &&
+                         (reinterpret_cast<uintptr_t>(dp) & 15u) == 0 && (reinterpret_cast<uintptr_t>(dout) & 15u) == 0;
+  gg_status rc;
+  if (!one_graph) {
+    if ((rc = gg_set_particles(s, pos_radius, vel, 0, stream)) != GG_OK) return rc;
+    if ((rc = gg_step(s, 1, stream)) != GG_OK) return rc;
+    return gg_readback(s, GG_FIELD_POS_VEL, out, gg_field_bytes(s, GG_FIELD_POS_VEL), 0, stream);
+  }
+  if (!s->tuned && (rc = autotune(s, st)) != GG_OK) return rc;  // (may drop the graphs)
+  if (!s->ctrl_host) GG_CUDA(s, cudaHostAlloc(reinterpret_cast<void **>(&s->ctrl_host), sizeof(DevCtrl), 0));
+  DevCtrl *cd = static_cast<DevCtrl *>(pinned_device_ptr(s->ctrl_host));
+  if (!cd) return fail(s, GG_ERR_INTERNAL, "gg_step_io: status mirror not mapped");
+  if (!s->io_exec || s->io_ptr[0] != dp || s->io_ptr[1] != dv || s->io_ptr[2] != dout) {
+    if (s->io_exec) cudaGraphExecDestroy(s->io_exec);
+    s->io_exec = nullptr;
+    const size_t n = s->n;
+    GG_CUDA(s, cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = gg::enqueue_state_in(s->a.pos_id, s->a.vel_id, static_cast<const float *>(dp),
+                                          static_cast<const float *>(dv), s->n, s->cap);
+    if (e1 == cudaSuccess) e1 = gg::enqueue_step(s->a, s->ls, s->cap, nullptr);
+    if (e1 == cudaSuccess)
+      e1 = gg::enqueue_state_out(s->a.pos_id, s->a.vel_id, static_cast<float *>(dout),
+                                 reinterpret_cast<float *>(static_cast<char *>(dout) + n * 16), s->n, s->a.ctrl, cd,
+                                 s->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
+    if (e1 == cudaSuccess && e2 == cudaSuccess) e1 = cudaGraphInstantiate(&s->io_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return cuda_fail(s, e1 != cudaSuccess ? e1 : e2, "gg_step_io capture");
+    s->io_ptr[0] = dp;
+    s->io_ptr[1] = dv;
+    s->io_ptr[2] = dout;
+  }
+  GG_CUDA(s, cudaGraphLaunch(s->io_exec, st));
+  s->steps += 1;
+  GG_CUDA(s, cudaStreamSynchronize(st));
+  return status_from_flags(s, s->ctrl_host->status);
 }
 
 gg_status gg_sync(gg_sim *s, void *stream) {

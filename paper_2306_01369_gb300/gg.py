@@ -40,6 +40,7 @@ SIGNATURES = {
     "gg_set_particles": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "gg_step": (C.c_int, [_P, C.c_uint32, _P]),
     "gg_sync": (C.c_int, [_P, _P]),
+    "gg_step_io": (C.c_int, [_P, _P, _P, _P, _P]),
     "gg_field_bytes": (C.c_size_t, [_P, C.c_int]),
     "gg_readback": (C.c_int, [_P, C.c_int, _P, C.c_size_t, C.c_int, _P]),
     "gg_set_state": (C.c_int, [_P, _P, C.c_size_t, C.c_int, _P]),
@@ -281,6 +282,16 @@ class Sim:
         tw = twist if _is_torch(twist) else np.ascontiguousarray(twist, np.float32)
         p, dev = _ptr(tw)
         self._check(self._L.gg_set_trajectory(self.h, env, body, int(tw.shape[0]), p, dev), "gg_set_trajectory")
+
+    def step_io(self, pos_r, vel, out, stream=None):
+        """gg_step_io: state in from host buffers, one step, the new state (POS_VEL
+        layout, float[7 n]) into `out`, waited for."""
+        pp, d0 = _ptr(pos_r)
+        vp, d1 = _ptr(vel)
+        op, d2 = _ptr(out)
+        assert not (d0 or d1 or d2), "gg_step_io takes host buffers"
+        self._check(self._L.gg_step_io(self.h, pp, vp, op, _stream(stream)), "gg_step_io")
+        return out
 
     def set_particles(self, pos_r, vel=None, stream=None):
         pp, dev = _ptr(pos_r)

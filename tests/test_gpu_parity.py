@@ -770,3 +770,36 @@ def test_pinned_transfers_ragged_and_misaligned(gg, torch, n):
         o = out.numpy()
         assert np.array_equal(o[:4 * n].reshape(n, 4), pr) and np.array_equal(o[4 * n:].reshape(n, 3), vel)
         sim.close()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_step_io_equals_the_three_calls(gg, torch, pinned):
+    """gg_step_io (one graph for pinned buffers, the three calls otherwise) moves the same
+    state and steps to the same result, bit for bit, as set_particles + step + POS_VEL."""
+    sc = squeezed_box(3001)
+    a, b = gg.Sim.from_scene(sc, tuning=11), gg.Sim.from_scene(sc, tuning=11)
+    a.step(3)
+    b.step(3)
+    p0, v0 = a.pos_vel()
+
+    def buf(x):
+        t = torch.from_numpy(np.ascontiguousarray(x, dtype=F32))
+        return t.pin_memory() if pinned else t
+
+    pos_h, vel_h = buf(p0), buf(v0)
+    out = buf(np.zeros(7 * sc.n, F32))
+    for _ in range(4):                       # the same buffers: the graph is reused
+        a.step_io(pos_h, vel_h, out)
+        pos_h.copy_(out[:4 * sc.n].view(sc.n, 4))
+        vel_h.copy_(out[4 * sc.n:].view(sc.n, 3))
+    for _ in range(4):
+        b.set_particles(p0, v0)
+        b.step(1)
+        p0, v0 = b.pos_vel()
+    o = out.numpy()
+    assert np.array_equal(o[:4 * sc.n].reshape(-1, 4), p0) and np.array_equal(o[4 * sc.n:].reshape(-1, 3), v0)
+    assert a.stats()["steps"] == b.stats()["steps"]
+    other = buf(np.zeros(7 * sc.n, F32))     # new output buffer: the graph is captured again
+    a.step_io(pos_h, vel_h, other)
+    b.step(1)
+    assert np.array_equal(other.numpy()[:4 * sc.n].reshape(-1, 4), b.pos())
