@@ -782,8 +782,8 @@ def test_step_io_equals_the_three_calls(gg, torch, pinned):
     b.step(3)
     p0, v0 = a.pos_vel()
 
-    def buf(x):
-        t = torch.from_numpy(np.ascontiguousarray(x, dtype=F32))
+    def buf(x):   # a copy (the loops below write into these buffers)
+        t = torch.from_numpy(np.array(x, dtype=F32, copy=True))
         return t.pin_memory() if pinned else t
 
     pos_h, vel_h = buf(p0), buf(v0)
