@@ -374,9 +374,9 @@ __device__ __forceinline__ void body_geometry(const DevBody &B, const float3 &xi
 
 // Contact records of particle i from its partner list (ascending ids, shared memory,
 // stride S), then its body contacts in ascending body index; counts and U^0.
-__device__ __forceinline__ void contact_records(const StepArgs &a, uint32_t i, float4 pi, uint32_t e, const DevEnv &E,
-                                                const uint32_t *fid, uint32_t S, uint32_t K, uint32_t npp, bool ovf,
-                                                uint32_t &nbc, float &psi_max) {
+__device__ __forceinline__ void contact_records(const StepArgs &a, uint32_t i, float4 pi, float4 vi, uint32_t e,
+                                                const DevEnv &E, const uint32_t *fid, uint32_t S, uint32_t K,
+                                                uint32_t npp, bool ovf, uint32_t &nbc, float &psi_max) {
     const size_t n = a.n;
     // the partners' positions are gathered four at a time, all four loads in flight
     // before any record of the group is computed and stored
@@ -439,7 +439,7 @@ __device__ __forceinline__ void contact_records(const StepArgs &a, uint32_t i, f
     }
     if (ovf) flag(a.ctrl, kFlagPPOverflow);
     a.ccount[i] = npp | (nbc << 8);
-    const float4 sb = base_velocity(a, a.vel_id[i]);
+    const float4 sb = base_velocity(a, vi);
     a.U[0][i] = make_float4(sb.x, sb.y, sb.z, (float)(a.lit ? 1u : npp + nbc) * sb.w);
   }
 
@@ -639,7 +639,7 @@ __device__ __forceinline__ void detect_particle(const StepArgs &a, uint32_t i, u
   const DevEnv E = a.envs[e];
   bool ovf = false;
   walk_partners<LISTS>(a, i, pi, E, fid, S, npp, ovf);
-  contact_records(a, i, pi, e, E, fid, S, a.K, npp, ovf, nbc, psi_max);
+  contact_records(a, i, pi, a.vel_id[i], e, E, fid, S, a.K, npp, ovf, nbc, psi_max);
 }
 
 template <bool LISTS>
@@ -662,11 +662,38 @@ __global__ void __launch_bounds__(kContactsBlock, 8) k_contacts(StepArgs a) {
 // hit test is symmetric in FP32, so each pair is found once, or twice when two of the
 // walked cells share a bucket.  Pass 2 sorts and deduplicates the entries and writes
 // the same records as k_contacts.
-__device__ __forceinline__ void record_pair(const StepArgs &a, uint32_t i, uint32_t j, uint32_t &nf) {
-  if (nf < a.K) a.pscr[(size_t)nf * a.n + i] = j;
-  ++nf;
+// The partner half of a hit needs the slot an atomic returns.  The first kDeferPairs
+// hits of a thread keep their partner in shared memory (slot q of thread t at
+// [q][t]) and take their atomics together after the walk (mirror_deferred), so the
+// walk does not wait for an atomic at every hit; later hits take theirs at once.  The
+// partner rows are sorted by pass 2, so the order in which the atomics land changes
+// nothing.
+constexpr uint32_t kDeferPairs = 4;
+
+__device__ __forceinline__ void mirror_pair(const StepArgs &a, uint32_t i, uint32_t j) {
   const uint32_t aj = atomicAdd(&a.pcnt[j], 1u) & 0xffffu;
   if (aj < a.K) a.pscr[(size_t)(a.K + aj) * a.n + j] = i;
+}
+
+__device__ __forceinline__ void record_pair(const StepArgs &a, uint32_t i, uint32_t j, uint32_t &nf, uint32_t *jd) {
+  if (nf < a.K) a.pscr[(size_t)nf * a.n + i] = j;
+  if (nf < kDeferPairs)
+    jd[nf * kContactsBlock] = j;
+  else
+    mirror_pair(a, i, j);
+  ++nf;
+}
+
+// The deferred hits' atomics, all issued before any of their slots is used.
+__device__ __forceinline__ void mirror_deferred(const StepArgs &a, uint32_t i, uint32_t nf, const uint32_t *jd) {
+  uint32_t j[kDeferPairs], aj[kDeferPairs];
+#pragma unroll
+  for (uint32_t q = 0; q < kDeferPairs; ++q) j[q] = q < nf ? jd[q * kContactsBlock] : 0u;
+#pragma unroll
+  for (uint32_t q = 0; q < kDeferPairs; ++q) aj[q] = q < nf ? atomicAdd(&a.pcnt[j[q]], 1u) & 0xffffu : a.K;
+#pragma unroll
+  for (uint32_t q = 0; q < kDeferPairs; ++q)
+    if (aj[q] < a.K) a.pscr[(size_t)(a.K + aj[q]) * a.n + j[q]] = i;
 }
 
 template <bool LISTS>
@@ -679,6 +706,8 @@ __global__ void __launch_bounds__(kContactsBlock, 9) k_pairs_half(StepArgs a) {
   const DevEnv E = a.envs[e];
   const int32_t k0 = cell_of(pi.x, E.inv_cell), k1 = cell_of(pi.y, E.inv_cell), k2 = cell_of(pi.z, E.inv_cell);
   uint32_t nf = 0;  // partners found by i
+  __shared__ uint32_t s_jd[kDeferPairs * kContactsBlock];  // the first kDeferPairs of them
+  uint32_t *jd = s_jd + threadIdx.x;
     // Eq. 6 terms of the three cells along each axis, combined 27 ways below
     uint32_t hx[3], hy[3], hz[3];
 #pragma unroll
@@ -717,7 +746,7 @@ __global__ void __launch_bounds__(kContactsBlock, 9) k_pairs_half(StepArgs a) {
   // (1, 1) with qx = 1 (the own cell) and 2
 #pragma unroll 1
   for (int row = 0; row < 5; ++row) {
-    const int qz = row < 4 ? (row < 3 ? 2 : 1) : 1;
+    const int qz = row < 3 ? 2 : 1;
     const int qy = row < 3 ? row : (row == 3 ? 2 : 1);
     const uint32_t mask = row == 4 ? 6u : 7u;
     const uint32_t hyz = pick3(hy, qy) ^ pick3(hz, qz);
@@ -759,7 +788,7 @@ __global__ void __launch_bounds__(kContactsBlock, 9) k_pairs_half(StepArgs a) {
           float d2;
           float3 d;
           const bool own = row == 4 && q == 1;
-          if ((own ? j > i : j != i) && sphere_hit(pi, pc[q], &d2, &d)) record_pair(a, i, j, nf);
+          if ((own ? j > i : j != i) && sphere_hit(pi, pc[q], &d2, &d)) record_pair(a, i, j, nf, jd);
           jn[q] = nx[q];
         }
       }
@@ -800,16 +829,24 @@ __global__ void __launch_bounds__(kContactsBlock, 9) k_pairs_half(StepArgs a) {
           r0[q] += (live >> q) & 1u;
           if (!((hit >> q) & 1u)) continue;
           const bool own = row == 4 && q == 1;
-          if (own ? jc[q] > i : jc[q] != i) record_pair(a, i, jc[q], nf);
+          if (own ? jc[q] > i : jc[q] != i) record_pair(a, i, jc[q], nf, jd);
         }
       }
     }
   }
+  mirror_deferred(a, i, nf, jd);
   if (nf) atomicAdd(&a.pcnt[i], min(nf, a.K + 1u) << 16);
 }
 
 // Pass 2: the partner list of particle i from its scratch entries (sorted, duplicates
 // dropped, the K smallest ids kept as in k_contacts), then the same records.
+// Loads are issued in batches, each batch before any of its values is used: the counts
+// with the particle's position, velocity and environment; then the first kFinishPre
+// entries of both scratch halves together (only entries below the counts are read).
+// The entries are inserted in the order they are stored (finder half, then partner
+// half), so the lists do not depend on the batching.
+constexpr uint32_t kFinishPre = 4;
+
 __global__ void __launch_bounds__(kContactsBlock, 8) k_pairs_finish(StepArgs a) {
   pdl_enter();
   extern __shared__ uint32_t s_fid[];
@@ -817,25 +854,40 @@ __global__ void __launch_bounds__(kContactsBlock, 8) k_pairs_finish(StepArgs a) 
   uint32_t npp = 0, nbc = 0;
   float psi_max = 0.f;
   if (i < a.n) {
+    const size_t n = a.n;
+    const uint32_t K = a.K;
+    const uint32_t cnt = a.pcnt[i];
     const float4 pi = a.pos_id[i];
+    const float4 vi = a.vel_id[i];
     const uint32_t e = a.env_of[i];
+    const uint32_t nfw = cnt >> 16, nbw = cnt & 0xffffu;
+    bool ovf = nfw > K || nbw > K;  // entries were lost: the list may be incomplete
+    const uint32_t mf = min(nfw, K), mb = min(nbw, K);
+    uint32_t jf[kFinishPre], jb[kFinishPre];
+#pragma unroll
+    for (uint32_t p = 0; p < kFinishPre; ++p) {
+      jf[p] = p < mf ? a.pscr[(size_t)p * n + i] : 0u;
+      jb[p] = p < mb ? a.pscr[(size_t)(K + p) * n + i] : 0u;
+    }
     const DevEnv E = a.envs[e];
     uint32_t *fid = s_fid + threadIdx.x;
     const uint32_t S = blockDim.x;
-    const uint32_t K = a.K;
-    const uint32_t cnt = a.pcnt[i];
-    const uint32_t nfw = cnt >> 16, nbw = cnt & 0xffffu;
-    bool ovf = nfw > K || nbw > K;  // entries were lost: the list may be incomplete
-    for (uint32_t p = 0; p < min(nfw, K); ++p) {
-      const uint32_t j = a.pscr[(size_t)p * a.n + i];
+#pragma unroll
+    for (uint32_t p = 0; p < kFinishPre; ++p)
+      if (p < mf && GG_GUARD(a.ctrl, jf[p] < a.n && jf[p] != i)) insert_partner(fid, S, K, jf[p], npp, ovf);
+    for (uint32_t p = kFinishPre; p < mf; ++p) {
+      const uint32_t j = a.pscr[(size_t)p * n + i];
       if (GG_GUARD(a.ctrl, j < a.n && j != i)) insert_partner(fid, S, K, j, npp, ovf);
     }
-    for (uint32_t p = 0; p < min(nbw, K); ++p) {
-      const uint32_t j = a.pscr[(size_t)(K + p) * a.n + i];
+#pragma unroll
+    for (uint32_t p = 0; p < kFinishPre; ++p)
+      if (p < mb && GG_GUARD(a.ctrl, jb[p] < a.n && jb[p] != i)) insert_partner(fid, S, K, jb[p], npp, ovf);
+    for (uint32_t p = kFinishPre; p < mb; ++p) {
+      const uint32_t j = a.pscr[(size_t)(K + p) * n + i];
       if (GG_GUARD(a.ctrl, j < a.n && j != i)) insert_partner(fid, S, K, j, npp, ovf);
     }
     a.pcnt[i] = 0;  // ready for the next step
-    contact_records(a, i, pi, e, E, fid, S, K, npp, ovf, nbc, psi_max);
+    contact_records(a, i, pi, vi, e, E, fid, S, K, npp, ovf, nbc, psi_max);
   }
   contact_stats(a, npp, nbc, psi_max);
 }

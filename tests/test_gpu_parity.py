@@ -103,6 +103,27 @@ def test_contacts_bit_exact_random_cloud_tiny_table(gg, orc):
     assert_contacts_equal(sim.contacts(), want)
 
 
+def test_half_stencil_sets_on_a_dense_cloud(gg, orc):
+    """The two-pass pair search on a cloud where many spheres have more than eight
+    partners, so both halves of a sphere's scratch hold more entries than the first
+    pass keeps in shared memory and the second pass loads in its first batch: every
+    half-stencil launch shape, both table sizes, the oracle's lists."""
+    pr, vel = S.random_cloud(1500, seed=22, box=0.035, overlap=1.0)
+    p = S.Params(dt=1e-4, gravity=(0, 0, 0), mu=0.5, pja_iters=5, max_contacts=32)
+    want = orc.contacts(pr[:, :3], pr[:, 3], [], p)
+    deg = np.diff(want["pp_off"].astype(np.int64))
+    assert 12 <= want["stats"]["max_pp"] <= 32 and (deg > 8).sum() > 100
+    sets = [k for k in range(1, gg.load().gg_tuning_count() + 1) if "half" in gg.tuning_flags(k)]
+    assert sets
+    for tuning in sets:
+        for hf in (2, 8):
+            sim = gg.Sim(pr, vel, S.sphere_mass(pr[:, 3]), p, tuning=tuning, hash_factor=hf)
+            sim.step(1)
+            sim.sync()
+            assert_contacts_equal(sim.contacts(), want)
+            sim.close()
+
+
 # --------------------------------------------------------------------------- #
 # dynamics
 # --------------------------------------------------------------------------- #
