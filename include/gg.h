@@ -113,7 +113,8 @@ typedef struct {
                                 records, sets 19-20 (sort, lists) run the paper's OneLoop: every
                                 iteration walks the cells again and computes each response as it
                                 finds the contact, set 21 is set 11 with 128-thread sweep
-                                blocks).  Results do not depend on it. */
+                                blocks, set 22 is set 18 with the 40-register sweep and no
+                                preloaded round).  Results do not depend on it. */
   uint32_t wrench_history;   /* per-step body wrenches kept for readback; 0 -> 1 */
   uint32_t max_free_bodies;  /* free rigid bodies over all environments (beyond the paper's
                                 kinematic bodies, Sec. V two-way coupling); 0 -> none */

@@ -37,7 +37,8 @@ const gg::LaunchShape kShapes[] = {{0, 256, 0, 0, 0, 0, 0},    {0, 128, 0, 0, 0,
                                    {0, 256, 0, 0, 0, 0, 1},    {0, 256, 0, 0, 0, 0, 0, 1}, {0, 256, 0, 0, 1, 0, 0, 1},
                                    {0, 128, 0, 0, 0, 0, 0, 0, 1, 1}, {0, 128, 0, 0, 1, 0, 0, 0, 1, 1},
                                    {0, 128, 0, 0, 1, 0, 1, 0, 1, 1}, {0, 128, 0, 0, 0, 0, 0, 0, 0, 0, 1},
-                                   {0, 128, 0, 0, 1, 0, 0, 0, 0, 0, 1}, {0, 128, 0, 0, 1, 0, 1}};
+                                   {0, 128, 0, 0, 1, 0, 0, 0, 0, 0, 1}, {0, 128, 0, 0, 1, 0, 1},
+                                   {0, 128, 0, 0, 1, 1, 1, 0, 1, 0}};
 constexpr uint32_t kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 // n_h factors the autotuner tries when gg_params.hash_tune is set (the paper's 2n first)

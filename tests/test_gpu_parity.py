@@ -602,7 +602,7 @@ def test_column_collapse_full_size_parity(gg, orc, column_800):
     _column_check(gg, orc, column_800, 0, 2)
 
 
-@pytest.mark.parametrize("tuning", list(range(1, 22)))
+@pytest.mark.parametrize("tuning", list(range(1, 23)))
 def test_column_collapse_full_size_every_launch_shape_at_8n(gg, orc, column_800, tuning):
     """The same at n_h = 8n under every launch-shape set, the benchmark's configuration
     among them (the autotuner picks one of these sets and a table of 2n, 4n or 8n)."""
