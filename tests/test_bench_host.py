@@ -12,6 +12,7 @@ def test_stage_kernels_follow_the_tuning_flags():
     assert bench.stage_kernels({"fused"})[0] == "k_pja_fused"
     assert bench.stage_kernels({"detect", "lists"}) == ("k_detect_sweeps", "k_detect_sweeps")
     assert bench.stage_kernels({"oneloop", "lists"}) == ("k_oneloop", "k_contacts")
+    assert bench.stage_kernels({"lists", "lean", "half", "serp"}) == ("k_pja_lean", "k_pairs_half+k_pairs_finish")
     assert bench.profile_traffic("k_pja", "column_pile", "x") is None     # no profile kept for it
 
 
@@ -34,3 +35,26 @@ def test_algorithmic_bytes():
 def test_hash_option():
     assert bench.hash_kw(argparse.Namespace(hash_factor=0)) == {"hash_tune": 1}
     assert bench.hash_kw(argparse.Namespace(hash_factor=2)) == {"hash_factor": 2}
+
+
+def test_committed_profiles_are_readable_and_name_their_command():
+    """Every kernel summary under profiles/ gives the command that made it (with the
+    clocks left alone) and, where it carries DRAM traffic, the kernel digest it was
+    taken on; bench.py reads the traffic back for its own kernel and workload names."""
+    import glob
+    import os
+    files = sorted(glob.glob(os.path.join(bench.ROOT, "profiles", "*.txt")))
+    assert files
+    for path in files:
+        text = open(path).read()
+        assert ("command" in text and "--clock-control none" in text) or "same report" in text, path
+        kv = dict(line.split(":", 1) for line in text.splitlines() if ":" in line and not line.startswith("#"))
+        if "dram_bytes_per_launch" in kv:
+            assert float(kv["dram_bytes_per_launch"]) > 0 and len(kv["kernel_digest"].strip()) == 16, path
+            stem, workload = os.path.basename(path)[:-4], None
+            for w, name in bench.PROFILE_WORKLOAD.items():
+                if stem.endswith("_" + name):
+                    workload, kernel = w, stem[: -len(name) - 1]
+            assert workload is not None, path
+            assert bench.profile_traffic(kernel, workload, kv["kernel_digest"].strip()) == \
+                float(kv["dram_bytes_per_launch"])
