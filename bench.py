@@ -390,6 +390,44 @@ def _timed_steps(sim, steps, stream, torch):
     return e0.elapsed_time(e1)
 
 
+def steady_backward(gg, torch, dev, stream, s32, ds, p, v, pose, mu, mass, grad_twist, fwd_ms, scoop_mass):
+    """The differentiable rollout and its reverse pass on one simulation that is kept (a
+    training loop's steady state): from the second pass on, the taped forward and the
+    backward reuse the tape, the checkpoints and the per-slot graphs.  Seeds: the
+    gradient of the same loss at the autograd rollout's final state."""
+    import dataclasses
+    pd, posed = p.detach().requires_grad_(), pose.detach().requires_grad_()
+    g_pos, g_pose = torch.autograd.grad(scoop_mass(pd, mass, posed, ds.bodies[1].shape12(), ds.info["eps"]),
+                                        (pd, posed))
+    g_vel = torch.zeros_like(v)          # the loss does not read the velocities
+    keep = gg.Sim(s32.pos_r, s32.vel, s32.mass, dataclasses.replace(s32.params, mu=float(mu.detach())))
+    try:
+        keep.set_bodies(s32.bodies)
+        for b, twb in s32.twist.items():
+            keep.set_trajectory(b, twb)
+        keep.tape_reserve(200, 20)
+        st0 = keep.state()
+        steady = []
+        for _ in range(3):
+            keep.set_state(st0)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            keep.step_taped(1, 200, stream=stream)
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            dtw, dmu = keep.backward(g_pos, g_vel, g_pose, stream=stream)
+            torch.cuda.synchronize(dev)
+            t2 = time.perf_counter()
+            steady.append((1e3 * (t1 - t0), 1e3 * (t2 - t1)))
+    finally:
+        keep.close()
+    return {"steady_taped_forward_ms": steady[-1][0], "steady_backward_ms": steady[-1][1],
+            "steady_bwd_over_fwd": steady[-1][1] / fwd_ms,
+            "steady_grad_equals_autograd": bool(torch.equal(dtw.reshape(grad_twist.shape), grad_twist)),
+            "steady_note": "third taped forward + backward on one kept simulation, set back to the start "
+                           f"state each time; the first pass measured {steady[0][0]:.1f} + {steady[0][1]:.1f} ms"}
+
+
 def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.0, settle_steps=1500,
            settle_steps_exc=3000):
     """The other figures of the headline metric, one GPU: batched env-steps/s against
@@ -521,7 +559,17 @@ def extras(torch, dev, stream, steps_batched=50, steps_exc=100, seconds_cap=180.
         out["differentiable"] = {"workload": "32,768 spheres + scoop, 200 steps, I=20, checkpoint every 20",
                                  "forward_ms": fwd_ms, "taped_forward_ms": 1e3 * (t1 - t0),
                                  "backward_ms": 1e3 * (t2 - t1), "bwd_over_fwd": 1e3 * (t2 - t1) / fwd_ms,
-                                 "grad_norm_twist": float(tw.grad.norm()), "dL_dmu": float(mu.grad)}
+                                 "grad_norm_twist": float(tw.grad.norm()), "dL_dmu": float(mu.grad),
+                                 "autograd_note": "each rollout creates, autotunes and tapes a new simulation; "
+                                                  "its backward captures every per-slot graph and frees the tape"}
+        # the same rollout and reverse pass on one simulation that is kept (a training
+        # loop's steady state): from the second pass on, the taped forward and the
+        # backward reuse the tape, the checkpoints and the per-slot graphs
+        try:
+            out["differentiable"].update(steady_backward(gg, torch, dev, stream, s32, ds, p, v, pose, mu, mass,
+                                                         tw.grad, fwd_ms, scoop_mass))
+        except gg.GGError as e:      # reported in the line; the other figures still run
+            out["differentiable"]["steady_error"] = str(e)
     # the gear tower (Sec. III, Fig. helical-gear-benchmark): 65,536 spheres in a tube
     # with a cyclic vertical boundary, n helical gears (GRID bodies sharing one baked
     # grid) on its axis; throughput against the number of gears (the paper's claim:
