@@ -93,8 +93,9 @@ def vel_tol(scene, v_orc, contacts, x=None, per_contact=False):
     floor of the Baumgarte bias of the contacts it has.  psi evaluated in FP32 carries up
     to ~8 eps32 L of rounding, L = the size of the coordinates it is computed from:
     2 r_max for a particle pair (|x_i - x_j| <= r_i + r_j), the body-frame coordinate
-    scale for an SDF contact (particles with a body contact, and their direct partners);
-    the bias alpha psi / dt turns that into (alpha / dt) 8 eps32 L of velocity.
+    scale for an SDF contact (particles with a body contact, and their direct partners;
+    further away, scaled by the mass-splitting share of every contact on the way); the
+    bias alpha psi / dt turns that into (alpha / dt) 8 eps32 L of velocity.
     `contacts`: the oracle's contact lists of the step's start state; x: its positions.
     per_contact: the floor once per contact of the particle (weightings that hand a
     particle each contact's whole correction, Alg. 1 as printed)."""
@@ -118,6 +119,19 @@ def vel_tol(scene, v_orc, contacts, x=None, per_contact=False):
     if has.any():
         owner = np.repeat(np.arange(n), np.diff(po))
         np.maximum.at(L, owner, Lb[pj])
+        # beyond the first hop the hand-off is the mass-splitting share of the contact,
+        # w_ij / m_i = 1 / (n_i + n_j m_i / m_j): a scale reaches a particle h hops away
+        # multiplied by the shares along the way (at most pja_iters hops, one per sweep)
+        cnt = np.diff(po) + np.diff(off.astype(np.int64))
+        m = np.asarray(scene.mass, np.float64)
+        share = 1.0 / (cnt[owner] + cnt[pj] * m[owner] / m[pj])
+        for _ in range(p.pja_iters - 1):
+            reach = np.zeros(n)
+            np.maximum.at(reach, owner, share * L[pj])
+            grown = np.maximum(L, reach)
+            if np.array_equal(grown, L):
+                break
+            L = grown
     floor = (p.alpha / p.dt) * 8.0 * EPS32 * L
     if per_contact:
         cnt = np.diff(contacts["pp_off"].astype(np.int64)) + np.diff(off.astype(np.int64))

@@ -90,3 +90,40 @@ def test_batched_env_contacts_match_oracle_lockstep(gg, k):
         check_vel(v[o0:o1], o.v, es, want)
     if k:
         assert n_pp > 1000
+
+
+def test_batched_full_recipe_sixteen_envs_lockstep(gg):
+    """Sixteen environments at the batched workload's own sizes (8k-64k spheres each,
+    525,557 in all) under the launch shapes and table size its benchmark runs (set 22,
+    n_h = 8n): from each environment's oracle state after 40 steps, every environment's
+    contact lists bit for bit and its one-step velocities per particle."""
+    from gpu_helpers import fp32_scene, oracle_advanced
+    import oracle
+    sc = S.batched_beds(n_envs=16, seed=1003, n_steps=80)
+    envs = [fp32_scene(es, oracle_advanced(es, 40, 16)) for es in (env_scene(sc, e)[0] for e in range(16))]
+    pos = np.concatenate([es.pos_r for es in envs])
+    vel = np.concatenate([es.vel for es in envs])
+    mass = np.concatenate([es.mass for es in envs])
+    bat = gg.Sim(pos, vel, mass, sc.params, env_offsets=sc.env_offsets, tuning=22, hash_factor=8)
+    for e, es in enumerate(envs):
+        bat.set_bodies(es.bodies, e)
+        for b, tw in es.twist.items():
+            bat.set_trajectory(b, tw, e)
+    bat.step(1)
+    got = bat.contacts()
+    v = bat.vel()
+    bat.close()
+    n_pp = 0
+    for e, es in enumerate(envs):
+        o0, o1 = int(sc.env_offsets[e]), int(sc.env_offsets[e + 1])
+        o = oracle.Sim(es.pos_r, es.vel, es.mass, es.bodies, es.params, twist=es.twist, n_threads=16)
+        want = o.contacts()
+        n_pp += want["stats"]["n_pp"]
+        sub = {"pp_off": got["pp_off"][o0:o1 + 1] - got["pp_off"][o0],
+               "pp_j": got["pp_j"][got["pp_off"][o0]:got["pp_off"][o1]] - o0,
+               "bc_off": got["bc_off"][o0:o1 + 1] - got["bc_off"][o0],
+               "bc_b": got["bc_b"][got["bc_off"][o0]:got["bc_off"][o1]]}
+        assert_contacts_equal(sub, want)
+        o.step(1)
+        check_vel(v[o0:o1], o.v, es, want)
+    assert sc.n > 500000 and n_pp > 200000
