@@ -64,7 +64,7 @@ def test_tuning_sets_cover_every_variant():
     assert {"fused"} in sets
     assert {"detect"} in sets and {"detect", "lists"} in sets
     assert {"serp", "preload"} in sets and {"serp", "lists", "preload"} in sets
-    assert {"serp", "lists", "half", "preload"} in sets
+    assert {"serp", "lists", "half", "preload"} in sets and {"serp", "lists", "half", "lean"} in sets
     assert {"oneloop"} in sets and {"oneloop", "lists"} in sets
 
 
