@@ -26,19 +26,38 @@ using gg::StepArgs;
 
 namespace {
 
+// One launch-shape set: threads per block of the per-launch sweep, the GG_TUNE_* bits of
+// its variants (GG_TUNE_FUSED aside: a set is fused when it names a fused block size),
+// and the block size of the cooperative all-sweeps launch.  The iteration count and the
+// cooperative grid are filled in at creation.
+constexpr gg::LaunchShape shape(int pja_block, uint32_t bits, int fused_block = 0) {
+  gg::LaunchShape s{};
+  s.pja_block = pja_block;
+  s.fused_block = fused_block;
+  s.lists = (bits & GG_TUNE_LISTS) ? 1u : 0u;
+  s.lean = (bits & GG_TUNE_LEAN) ? 1u : 0u;
+  s.half = (bits & GG_TUNE_HALF) ? 1u : 0u;
+  s.detect = (bits & GG_TUNE_DETECT) ? 1u : 0u;
+  s.serp = (bits & GG_TUNE_SERP) ? 1u : 0u;
+  s.pre = (bits & GG_TUNE_PRELOAD) ? 1u : 0u;
+  s.one = (bits & GG_TUNE_ONELOOP) ? 1u : 0u;
+  return s;
+}
+
 // Launch-shape sets accepted by gg_params.tuning (index k-1).
-// (iters, per-launch sweep block, fused sweep block, fused grid, binning by lists, lean sweeps,
-//  half-stencil pair search, detection and sweeps in one cooperative launch, serpentine sweeps,
-//  preloaded first sweep round, OneLoop)
-const gg::LaunchShape kShapes[] = {{0, 256, 0, 0, 0, 0, 0},    {0, 128, 0, 0, 0, 0, 0}, {0, 512, 0, 0, 0, 0, 0},
-                                   {0, 64, 0, 0, 0, 0, 0},     {0, 256, 1024, 0, 0, 0, 0}, {0, 256, 512, 0, 0, 0, 0},
-                                   {0, 256, 0, 0, 1, 0, 0},    {0, 128, 0, 0, 1, 0, 0}, {0, 256, 0, 0, 1, 1, 0},
-                                   {0, 256, 0, 0, 0, 1, 0},    {0, 256, 0, 0, 1, 0, 1}, {0, 256, 0, 0, 1, 1, 1},
-                                   {0, 256, 0, 0, 0, 0, 1},    {0, 256, 0, 0, 0, 0, 0, 1}, {0, 256, 0, 0, 1, 0, 0, 1},
-                                   {0, 128, 0, 0, 0, 0, 0, 0, 1, 1}, {0, 128, 0, 0, 1, 0, 0, 0, 1, 1},
-                                   {0, 128, 0, 0, 1, 0, 1, 0, 1, 1}, {0, 128, 0, 0, 0, 0, 0, 0, 0, 0, 1},
-                                   {0, 128, 0, 0, 1, 0, 0, 0, 0, 0, 1}, {0, 128, 0, 0, 1, 0, 1},
-                                   {0, 128, 0, 0, 1, 1, 1, 0, 1, 0}};
+constexpr uint32_t kL = GG_TUNE_LISTS, kLean = GG_TUNE_LEAN, kHalf = GG_TUNE_HALF, kDet = GG_TUNE_DETECT,
+                   kSerp = GG_TUNE_SERP, kPre = GG_TUNE_PRELOAD, kOne = GG_TUNE_ONELOOP;
+const gg::LaunchShape kShapes[] = {
+    shape(256, 0),  shape(128, 0), shape(512, 0), shape(64, 0),       // 1-4: sort, per-launch sweeps
+    shape(256, 0, 1024), shape(256, 0, 512),                           // 5-6: all sweeps in one launch
+    shape(256, kL), shape(128, kL),                                    // 7-8: lists
+    shape(256, kL | kLean), shape(256, kLean),                         // 9-10: 40-register sweeps
+    shape(256, kL | kHalf), shape(256, kL | kLean | kHalf), shape(256, kHalf),  // 11-13: half stencil
+    shape(256, kDet), shape(256, kL | kDet),                           // 14-15: TwoLoopsFused
+    shape(128, kSerp | kPre), shape(128, kL | kSerp | kPre), shape(128, kL | kHalf | kSerp | kPre),  // 16-18
+    shape(128, kOne), shape(128, kL | kOne),                           // 19-20: OneLoop
+    shape(128, kL | kHalf),                                            // 21
+    shape(128, kL | kLean | kHalf | kSerp)};                           // 22
 constexpr uint32_t kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 // n_h factors the autotuner tries when gg_params.hash_tune is set (the paper's 2n first)
@@ -897,7 +916,7 @@ gg_status gg_set_trajectory(gg_sim *s, uint32_t env, uint32_t body, uint32_t n_s
     GG_CUDA(s, cudaMemcpy(t, twist, sizeof(float) * 6 * n_steps,
                           twist_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
   }
-  DevCtrl c;
+  DevCtrl c{};
   GG_CUDA(s, cudaMemcpy(&c, s->a.ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost));
   DevBody *db = s->a.bodies + gb;
   const float *tp = t;
@@ -1100,7 +1119,7 @@ gg_status gg_step_io(gg_sim *s, const float *pos_radius, const float *vel, float
 
 gg_status gg_sync(gg_sim *s, void *stream) {
   if (!s) return GG_ERR_INVALID_ARG;
-  DevCtrl c;
+  DevCtrl c{};
   gg_status rc = read_ctrl(s, &c, static_cast<cudaStream_t>(stream));
   if (rc != GG_OK) return rc;
   return status_from_flags(s, c.status);
@@ -1234,7 +1253,7 @@ gg_status gg_readback(gg_sim *s, gg_field f, void *dst, size_t bytes, int dst_on
   }
   case GG_FIELD_STATS: {
     if (dst_on_device) return fail(s, GG_ERR_UNSUPPORTED, "GG_FIELD_STATS is host-only");
-    DevCtrl c;
+    DevCtrl c{};
     if ((rc = read_ctrl(s, &c, st)) != GG_OK) return rc;
     gg_stats out{};
     out.steps = s->steps;
@@ -1267,7 +1286,7 @@ gg_status gg_readback(gg_sim *s, gg_field f, void *dst, size_t bytes, int dst_on
     return fail(s, GG_ERR_INVALID_ARG, "unknown field");
   }
   if (dst_on_device) return GG_OK;
-  DevCtrl c;
+  DevCtrl c{};
   if (ctrl_done)
     c = *s->ctrl_host;
   else if ((rc = read_ctrl(s, &c, st)) != GG_OK)
@@ -1303,7 +1322,7 @@ gg_status gg_set_state(gg_sim *s, const void *state, size_t bytes, int on_device
     for (int k = 0; k < 3; ++k) bd[b].own_w[k] = q[10 + k];
   }
   GG_CUDA(s, cudaMemcpy(s->a.bodies, bd.data(), sizeof(DevBody) * nbt, cudaMemcpyHostToDevice));
-  DevCtrl c;
+  DevCtrl c{};
   GG_CUDA(s, cudaMemcpy(&c, s->a.ctrl, sizeof(c), cudaMemcpyDeviceToHost));
   c.step = (uint32_t)hd.steps;
   GG_CUDA(s, cudaMemcpy(s->a.ctrl, &c, sizeof(c), cudaMemcpyHostToDevice));
@@ -1500,7 +1519,7 @@ gg_status gg_backward(gg_sim *s, const float *dL_dpos, const float *dL_dvel, con
   GG_CUDA(s, cudaStreamSynchronize(st));
   const float muf = (float)mu;
   GG_CUDA(s, cudaMemcpy(dL_dmu, &muf, sizeof(float), on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
-  DevCtrl c;
+  DevCtrl c{};
   rc = read_ctrl(s, &c, st);
   if (rc != GG_OK) return rc;
   return status_from_flags(s, c.status);
