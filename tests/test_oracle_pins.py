@@ -301,6 +301,24 @@ def test_resting_sphere_baumgarte_decay(orc):
             assert np.allclose(s.wrench[0, [0, 1]], 0.0, atol=1e-18)
 
 
+def test_resting_sphere_torque_about_the_body_origin(orc):
+    """The wrench's torque is taken about the body's position, with the lever arm from
+    there to the contact point x - f n (Sec. III-C force readback; readings g18, g19):
+    a sphere resting at (dx, dy) on a plane through the origin presses on it with
+    F = (0, 0, -m g) at (dx, dy, 0), so tau = (dx, dy, 0) x F = (-m g dy, m g dx, 0).
+    A lever arm taken the other way round, or the product in the other order, flips
+    both signs."""
+    r = F32(0.005)
+    dx, dy = F32(0.03), F32(-0.02)
+    pr = np.array([[dx, dy, r, r]], F32)
+    p = S.Params(dt=1e-4, mu=0.5, alpha=0.2, pja_iters=20)
+    s = orc.Sim(pr, np.zeros((1, 3), F32), np.array([0.01], F32), [S.Body(kind=S.PLANE)], p)
+    s.step(3)
+    mg = float(F32(0.01)) * float(F32(9.81))
+    want = np.array([0.0, 0.0, -mg, -mg * float(dy), mg * float(dx), 0.0])
+    assert np.allclose(s.wrench[0], want, rtol=0, atol=1e-12 * mg)
+
+
 @pytest.mark.parametrize("dtheta_deg", [-2.0, 2.0])
 def test_block_on_incline_threshold(orc, dtheta_deg):
     """Sliding threshold tan(theta) = mu and a = g (sin theta - mu cos theta) above it."""
