@@ -319,6 +319,26 @@ def test_resting_sphere_torque_about_the_body_origin(orc):
     assert np.allclose(s.wrench[0], want, rtol=0, atol=1e-12 * mg)
 
 
+def test_sphere_sticks_to_a_moving_plate(orc):
+    """A kinematic body's surface velocity at a contact is v_b + w_b x (x_c - p_b)
+    (reading g18, world-frame twist): a sphere resting at (dx, dy) on a plate through
+    the origin that translates at v_b and spins at w_b about z is carried, after one
+    step, at exactly that velocity, as long as friction can hold it (|v_s| < mu g dt:
+    the first iteration removes the relative velocity, the cone keeps the impulse).
+    A lever arm or a cross product the other way round, or a dropped v_b, fails it."""
+    r = F32(0.005)
+    dx, dy = F32(0.03), F32(-0.02)
+    vb, wz = F32(1e-4), F32(0.005)
+    pr = np.array([[dx, dy, r, r]], F32)
+    p = S.Params(dt=1e-4, mu=0.5, alpha=0.2, pja_iters=20)
+    plate = S.Body(kind=S.PLANE, lin_vel=(float(vb), 0.0, 0.0), ang_vel=(0.0, 0.0, float(wz)))
+    s = orc.Sim(pr, np.zeros((1, 3), F32), np.array([0.01], F32), [plate], p)
+    s.step(1)
+    want = np.array([float(vb) - float(wz) * float(dy), float(wz) * float(dx), 0.0])
+    assert np.linalg.norm(want) < 0.5 * float(F32(9.81)) * float(F32(1e-4))   # inside the cone
+    assert np.allclose(s.v[0], want, rtol=0, atol=1e-15)
+
+
 @pytest.mark.parametrize("dtheta_deg", [-2.0, 2.0])
 def test_block_on_incline_threshold(orc, dtheta_deg):
     """Sliding threshold tan(theta) = mu and a = g (sin theta - mu cos theta) above it."""
