@@ -424,6 +424,26 @@ def test_kinematic_body_pose_closed_form(orc):
     assert np.allclose(pose[3:], [math.cos(ang / 2), 0, 0, math.sin(ang / 2)], atol=1e-14)
 
 
+def test_kinematic_body_follows_its_twist_table_row_by_row(orc):
+    """Reading g17: step k of a driven body uses row k of its per-step world twist table
+    (its own twist once the table ends).  Rows that grow with k make the pose after n
+    steps the sum of the first n rows times dt; a table read one row early or late
+    moves the body by a different amount."""
+    n, dt = 12, float(F32(1e-4))
+    k = np.arange(n + 4, dtype=np.float64)
+    tab = np.zeros((n + 4, 6), np.float32)
+    tab[:, 0] = (1e-3 * (k + 1)).astype(np.float32)       # x velocity of row k
+    tab[:, 5] = (0.5 * (k + 1)).astype(np.float32)        # rotation rate about z
+    body = S.Body(kind=S.BOX, shape=(0.01, 0.01, 0.01), pos=(0.0, 0.0, 1.0))
+    s = orc.Sim(np.zeros((0, 4), F32), np.zeros((0, 3), F32), np.zeros(0, F32), [body], _params(), twist={0: tab})
+    s.step(n)
+    pose = s.body_pose(0)
+    x = dt * float(tab[:n, 0].astype(np.float64).sum())
+    ang = dt * float(tab[:n, 5].astype(np.float64).sum())
+    assert abs(pose[0] - x) < 1e-14 and abs(pose[2] - 1.0) < 1e-14
+    assert np.allclose(pose[3:], [math.cos(ang / 2), 0, 0, math.sin(ang / 2)], atol=1e-14)
+
+
 def _quat_mul(a, b):
     """Hamilton product a (x) b of (w, x, y, z) quaternions."""
     aw, ax, ay, az = a
