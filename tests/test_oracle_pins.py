@@ -489,6 +489,47 @@ def test_kinematic_pose_world_frame_twist_from_tilted_start(orc, omega):
     assert abs(abs(float(np.dot(qk, s.body_pose(0)[3:]))) - 1.0) < 1e-12
 
 
+@pytest.mark.parametrize("iters,want_a,want_b", [(1, -0.5, -1.0), (2, -5.0 / 12.0, -5.0 / 6.0)])
+def test_stacked_spheres_on_a_plane_mass_split_iterates(orc, iters, want_a, want_b):
+    """Mass splitting counts a body contact in n_i too (reading g3).  Sphere A rests on a
+    plane, sphere B on A (both touching exactly, at rest, gravity on; equal masses).
+    First sweep: the plane contact of A (n_A = 2) takes w = m / 2 of A's approach
+    g dt, the A-B pair sees no relative velocity: U_A = -g dt / 2, U_B = -g dt.  Second
+    sweep: the plane contact grows to 3/4 m g dt, the pair (w = 1 / (2/m + 1/m) = m/3)
+    closes the relative velocity g dt / 2 by a third of it: U_A = -5/12 g dt,
+    U_B = -5/6 g dt.  A body-contact weight without the count gives U_A = 0 after one
+    sweep."""
+    r = F32(2.0 ** -8)                                # exact: the contacts touch exactly
+    pr = np.array([[0.0, 0.0, r, r], [0.0, 0.0, 3 * r, r]], F32)
+    p = S.Params(dt=1e-4, gravity=(0.0, 0.0, -9.81), mu=0.5, alpha=0.2, pja_iters=iters)
+    s = orc.Sim(pr, np.zeros((2, 3), F32), np.array([0.01, 0.01], F32), [S.Body(kind=S.PLANE)], p)
+    s.step(1)
+    gdt = float(F32(9.81)) * float(F32(1e-4))
+    assert np.allclose(s.v[:, :2], 0.0, atol=1e-18)
+    assert abs(s.v[0, 2] - want_a * gdt) < 1e-15 and abs(s.v[1, 2] - want_b * gdt) < 1e-15
+
+
+def test_free_box_hit_from_both_sides_counts_its_contacts(orc):
+    """A free body's share of the mass splitting counts its contacts this step (reading
+    for free bodies: n_b (1/M + ...)).  Two equal spheres hit a free cube through its
+    centre from opposite sides (gravity off, one sweep, levers parallel to the normals):
+    w = 1 / (1/m + 2/M), each sphere keeps s (1 - w/m) = s/2 for M = 2m, and the cube,
+    pushed equally both ways, stays at rest.  Counting one contact gives s/3."""
+    h, r = 2.0 ** -5, F32(2.0 ** -8)
+    m, M = 0.01, 0.02
+    cube = S.Body(kind=S.BOX, shape=(h, h, h), pos=(0.0, 0.0, 0.0), is_free=1, mass=M,
+                  inertia=(M * (2 * h) ** 2 / 6,) * 3)
+    x0 = F32(h) + r
+    pr = np.array([[-x0, 0.0, 0.0, r], [x0, 0.0, 0.0, r]], F32)
+    sp = 0.2
+    vel = np.array([[sp, 0.0, 0.0], [-sp, 0.0, 0.0]], F32)
+    s = orc.Sim(pr, vel, np.array([m, m], F32), [cube], _params(pja_iters=1))
+    s.step(1)
+    sp32 = float(F32(sp))
+    assert np.allclose(s.v, [[sp32 / 2, 0, 0], [-sp32 / 2, 0, 0]], rtol=0, atol=1e-15)
+    assert np.allclose(s.body_twist(0), 0.0, atol=1e-15)
+
+
 def test_free_body_central_hit_inelastic(orc):
     """A sphere hitting a free box through its centre: both end with m v / (m + M)."""
     M = 2.0
