@@ -230,6 +230,11 @@ def test_scoop_and_container_sdf_values(orc):
     # 4 mm from the cavity's +y wall (at y = 0.044), 2 cm above its floor
     f, n = orc.sdf(scoop, np.array([0.0, 0.04, -0.01]))
     assert abs(f - 0.004) < 1e-7 and np.allclose(n, [0, -1, 0])
+    # 4 mm from the cavity's +x and -x walls (at x = +-0.054): normals into the cavity
+    f, n = orc.sdf(scoop, np.array([0.05, 0.0, -0.01]))
+    assert abs(f - 0.004) < 1e-7 and np.allclose(n, [-1, 0, 0])
+    f, n = orc.sdf(scoop, np.array([-0.05, 0.0, -0.01]))
+    assert abs(f - 0.004) < 1e-7 and np.allclose(n, [1, 0, 0])
     # outside next to a side wall
     f, n = orc.sdf(scoop, np.array([0.07, 0.0, 0.0]))
     assert abs(f - 0.01) < 1e-7 and np.allclose(n, [1, 0, 0])
@@ -251,6 +256,35 @@ def _two_spheres(orc, v0, v1, m0=1.0, m1=3.0, mu=0.5, iters=20):
     s = orc.Sim(pr, vel, np.array([m0, m1], F32), [], _params(mu=mu, pja_iters=iters, cell_size=1.6))
     s.step(1)
     return s
+
+
+def test_body_contact_point_lies_on_the_touched_face(orc):
+    """Reading g18: the contact point of a body contact is x - f n, the closest point of
+    the surface.  A sphere pressing 0.1 mm into the +x face of a box turned 30 degrees
+    about z: the face's outward normal is R e_x, psi = r - (n . (x - p) - h), and the
+    contact point is on the face plane, f = r - psi from the centre along -n."""
+    th = math.radians(30.0)
+    h = 0.05
+    box = S.Body(kind=S.BOX, shape=(h, h, h), pos=(0.1, 0.2, 0.3),
+                 quat=(math.cos(th / 2), 0.0, 0.0, math.sin(th / 2)))
+    n_w = np.array([math.cos(th), math.sin(th), 0.0])
+    t_w = np.array([-math.sin(th), math.cos(th), 0.0])
+    r = 0.01
+    centre = np.array(box.pos) + (h + r - 1e-4) * n_w + 0.013 * t_w + np.array([0.0, 0.0, -0.007])
+    pr = np.array([[*centre, r]], F32)
+    s = orc.Sim(pr, np.zeros((1, 3), F32), np.array([0.01], F32), [box], _params(cell_size=0.05))
+    c = s.contacts()
+    assert c["bc_off"][-1] == 1
+    g = c["bc_geom"][0]
+    x = pr[0, :3].astype(np.float64)
+    p = np.array([float(F32(v)) for v in box.pos])
+    qf = np.array([float(F32(v)) for v in box.quat])
+    n_f = _quat_matrix(qf)[:, 0]                                        # R e_x of the stored pose
+    f = float(n_f @ (x - p)) - float(F32(h))
+    assert np.allclose(g[:3], n_f, atol=1e-12)
+    assert abs(g[3] - (float(F32(r)) - f)) < 1e-12
+    assert np.allclose(g[4:7], x - f * n_f, atol=1e-12)
+    assert abs(float(n_f @ (g[4:7] - p)) - float(F32(h))) < 1e-12         # on the face plane
 
 
 def test_two_sphere_head_on_inelastic(orc):
