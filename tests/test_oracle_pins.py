@@ -219,6 +219,27 @@ def test_box_sdf_against_sampled_surface(orc):
         assert f2 > f
 
 
+def test_box_face_tie_takes_the_lower_axis(orc):
+    """Reading g14: inside a box, a point as far from an x face as from a y face takes
+    the x face (ties go to the lower axis); as far from y as from z, the y face."""
+    box = S.Body(kind=S.BOX, shape=(0.02, 0.02, 0.02))
+    f, n = orc.sdf(box, np.array([0.015, 0.015, 0.0]))
+    assert np.allclose(n, [1, 0, 0]) and abs(f + 0.005) < 1e-9
+    f, n = orc.sdf(box, np.array([0.0, -0.015, -0.015]))
+    assert np.allclose(n, [0, -1, 0]) and abs(f + 0.005) < 1e-9
+
+
+def test_container_floor_below_its_origin(orc):
+    """Reading g16: an open box's floor is at -h_z in its frame (walls at +-h_x, +-h_y):
+    with h_z = 0.05 a point 4 mm above the floor is 4 mm away, normal up."""
+    box = S.Body(kind=S.OPEN_BOX, shape=(0.1, 0.1, 0.05), pos=(0.0, 0.0, 0.5))
+    f, n = orc.sdf(box, np.array([0.0, 0.0, 0.5 - 0.05 + 0.004]))
+    assert abs(f - 0.004) < 1e-7 and np.allclose(n, [0, 0, 1])
+    pr = np.array([[0.0, 0.0, 0.5 - 0.05 + 0.0049, 0.005], [0.05, 0.0, 0.5 - 0.05 + 0.03, 0.005]], F32)
+    c = orc.contacts(pr[:, :3], pr[:, 3], [box], _params(cell_size=0.011))
+    assert list(np.diff(c["bc_off"].astype(np.int64))) == [1, 0]       # touching; 3 cm above: free
+
+
 def test_scoop_and_container_sdf_values(orc):
     scoop = S.scoop_body(1.0)
     # inside the 6 mm floor: 5 mm from the bottom face and from the cavity floor
@@ -813,6 +834,20 @@ def test_grid_sdf_error_within_trilinear_bound(orc):
     assert nerrs[1] < 0.15
 
 
+def test_grid_sdf_on_its_last_samples(orc):
+    """The last cell along an axis ends on the last sample: a point exactly on the top
+    corner of the sampled box, or on its upper faces, takes the last cell (i = n - 2,
+    t = 1) and returns the sample there."""
+    a, c = np.array([0.25, -0.5, 0.75]), 0.125
+    o, h, dims = (-0.5, -0.25, -0.125), 1.0 / 64, (65, 33, 17)
+    body = _grid_body(lambda y: y @ a + c, o, h, dims)
+    top = np.array([o[k] + h * (dims[k] - 1) for k in range(3)])
+    for y in (top, np.array([top[0], 0.0, 0.0]), np.array([0.0, top[1], 0.0]), np.array([0.0, 0.0, top[2]])):
+        f, n = orc.sdf(body, y)
+        assert abs(f - (y @ a + c)) < 1e-12, y
+        assert np.allclose(n, a / np.linalg.norm(a), atol=1e-12), y     # the last cell's own gradient
+
+
 def test_grid_outside_the_samples_is_not_in_contact(orc):
     body = _grid_body(lambda y: y[..., 2], (-0.09375, -0.09375, -0.09375), 1.0 / 32, (7, 7, 7))
     f, _ = orc.sdf(body, np.array([0.0, 0.0, 0.0]))
@@ -876,6 +911,20 @@ def test_tube_sdf_values(orc):
         rho = math.hypot(y[0], y[1])
         if rho > 0:
             assert np.allclose(n, [-y[0] / rho, -y[1] / rho, 0.0], atol=1e-12)
+
+
+def test_tube_contacts_only_at_the_wall(orc):
+    """The FP32 contact test of the tube wall (f = R - rho <= r): a sphere touching the
+    wall from inside has one body contact, normal towards the axis; spheres near the axis
+    or half a radius from the wall have none."""
+    R = 0.0625
+    tube = S.Body(kind=S.TUBE, shape=(R,))
+    r = 0.004
+    pr = np.array([[R - 0.9 * r, 0.0, 0.1, r], [0.0, 0.0, 0.2, r], [0.0, -(R - 1.5 * r), 0.3, r]], F32)
+    c = orc.contacts(pr[:, :3], pr[:, 3], [tube], _params(cell_size=0.009))
+    assert list(np.diff(c["bc_off"].astype(np.int64))) == [1, 0, 0]
+    assert np.allclose(c["bc_geom"][0, :3], [-1, 0, 0], atol=1e-12)
+    assert abs(c["bc_geom"][0, 3] - (float(F32(r)) - (R - float(F32(R - 0.9 * r))))) < 1e-12
 
 
 # --------------------------------------------------------------------------- #
