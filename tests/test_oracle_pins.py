@@ -143,6 +143,37 @@ def test_contacts_match_kdtree(orc):
     assert (got - border) == (want - border)
 
 
+def test_pair_test_sums_in_the_stated_order(orc):
+    """The FP32 sphere test is ((dx^2 + dy^2) + dz^2) <= (r_i + r_j)^2, one rounding
+    per operation, no fused multiply-add (Sec. II-C; reading g9 family).  Search pairs
+    within a few ulps of touching on which another summation order decides the other
+    way; the oracle must follow the stated order, which numpy's float32 arithmetic
+    evaluates here independently."""
+    rng = np.random.default_rng(4)
+    p = _params(cell_size=0.01)
+    found = 0
+    for _ in range(6000):
+        ri, rj = F32(rng.uniform(1e-3, 3e-3)), F32(rng.uniform(1e-3, 3e-3))
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        xi = rng.uniform(-0.5, 0.5, 3).astype(F32)
+        rs = float(ri) + float(rj)
+        for k in (-2, -1, 0, 1, 2):
+            xj = (xi.astype(np.float64) + rs * (1 + k * 6e-8) * u).astype(F32)
+            d = [F32(xi[a] - xj[a]) for a in range(3)]
+            sq = [F32(v * v) for v in d]
+            stated = F32(F32(sq[0] + sq[1]) + sq[2])
+            others = (F32(sq[0] + F32(sq[1] + sq[2])), F32(F32(sq[0] + sq[2]) + sq[1]))
+            r2 = F32(F32(ri + rj) * F32(ri + rj))
+            if all((o <= r2) == (stated <= r2) for o in others):
+                continue
+            found += 1
+            pr = np.array([[*xi, ri], [*xj, rj]], F32)
+            c = orc.contacts(pr[:, :3], pr[:, 3], [], p)
+            assert (c["pp_off"][-1] == 2) == bool(stated <= r2), (xi, xj, ri, rj)
+    assert found >= 10, "too few order-sensitive pairs; widen the search"
+
+
 def test_contact_geometry_antisymmetric(orc):
     pr, _ = S.random_cloud(400, seed=5, box=0.04, overlap=0.5)
     res = orc.contacts(pr[:, :3], pr[:, 3], [], _params())
