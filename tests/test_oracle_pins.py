@@ -985,6 +985,20 @@ def test_height_camera_single_sphere(orc):
     assert covered > 10
 
 
+def test_height_camera_pixel_pitch_per_axis(orc):
+    """Non-square pixels (0.002 m wide, 0.001 m tall): a sphere of 1.5 mm radius at
+    (0.0001, 0.0045) over a 16 x 16 map of a 0.032 x 0.016 rectangle (pixel centres
+    x = -0.015 + 0.002 u, y = -0.0075 + 0.001 v) covers the two columns u = 7, 8
+    (x = -0.001, 0.001: 1.1 and 0.9 mm away) and in them the rows whose centre is
+    within sqrt(r^2 - dx^2) (1.02 and 1.2 mm) of y = 0.0045: v = 11, 12, 13."""
+    cam = S.Camera(kind=S.HEIGHT_CAMERA, width=16, height=16, pos=(0.0, 0.0, 0.0), extent=(0.032, 0.016),
+                   empty=-1.0)
+    img = orc.render(cam, np.array([[0.0001, 0.0045, 0.02]]), np.array([0.0015]), [])
+    rows = sorted({v for v in range(16) for u in range(16) if img[v, u] != -1.0})
+    assert rows == [11, 12, 13]
+    assert all(sorted(u for u in range(16) if img[v, u] != -1.0) == [7, 8] for v in rows)
+
+
 def test_height_camera_takes_the_highest_surface(orc):
     cam = S.Camera(kind=S.HEIGHT_CAMERA, width=4, height=4, pos=(0.0, 0.0, 0.0), extent=(0.008, 0.008))
     x = np.array([[0.001, 0.001, 0.01], [0.001, 0.001, 0.013], [0.001, 0.001, 0.004]])
@@ -1026,6 +1040,23 @@ def test_depth_camera_sphere_and_plane(orc):
     assert hits >= 4
     far = S.Camera(kind=S.DEPTH_CAMERA, width=4, height=4, pos=(0.0, 0.0, 5.0), quat=down, fov_y=0.5, far=2.0)
     assert np.all(orc.render(far, np.zeros((0, 3)), np.zeros(0), [floor]) == 2.0)
+
+
+def test_depth_camera_axes_and_near_clip(orc):
+    """Reading g25: camera x right, y down, z forward.  With the camera frame equal to
+    the world's, a sphere at world +y (camera down) lands in the lower rows and one at
+    world +x in the right columns; a sphere whose near surface is closer than `near`
+    is not seen."""
+    cam = S.Camera(kind=S.DEPTH_CAMERA, width=20, height=20, fov_y=0.8, near=0.01, far=2.0)
+    f = 0.5 * 20 / math.tan(0.4)
+    img = orc.render(cam, np.array([[0.0, 0.15, 1.0]]), np.array([0.05]), [])
+    rows = {v for v in range(20) for u in range(20) if img[v, u] < 2.0}
+    assert rows and min(rows) >= 10 and abs(np.mean(sorted(rows)) - (10 + f * 0.15)) < 1.5
+    img = orc.render(cam, np.array([[0.15, 0.0, 1.0]]), np.array([0.05]), [])
+    cols = {u for v in range(20) for u in range(20) if img[v, u] < 2.0}
+    assert cols and min(cols) >= 10
+    img = orc.render(cam, np.array([[0.0, 0.0, 0.03]]), np.array([0.025]), [])
+    assert np.all(img == 2.0)                      # near surface 5 mm away: clipped
 
 
 def test_depth_camera_traces_a_box_and_a_grid_box_alike(orc):
