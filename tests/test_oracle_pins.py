@@ -631,11 +631,14 @@ def test_free_body_central_hit_inelastic(orc):
 
 
 def test_scoop_loss_limits(orc):
+    """Reading g18 (loss): sum_i m_i sigmoid(-f_B(y_i) / eps) over the cavity box B.
+    Deep inside the cavity a particle counts fully, far outside not at all, and on the
+    cavity's +x wall (f_B = 0) by half; the three masses tell the terms apart."""
     scoop = S.scoop_body(1.0, pos=(0.0, 0.0, 0.0))
-    pr = np.array([[0.0, 0.0, 0.01, 0.002], [0.5, 0.5, 0.5, 0.002]], F32)
-    s = orc.Sim(pr, np.zeros((2, 3), F32), np.array([1.0, 1.0], F32), [scoop], _params())
+    pr = np.array([[0.0, 0.0, 0.01, 0.002], [0.5, 0.5, 0.5, 0.002], [0.054, 0.0, 0.01, 0.002]], F32)
+    s = orc.Sim(pr, np.zeros((3, 3), F32), np.array([1.0, 2.0, 4.0], F32), [scoop], _params())
     L = s.scoop_loss(0, eps=1e-3)
-    assert abs(L - 1.0) < 1e-9      # first one deep inside the cavity counts fully, second not at all
+    assert abs(L - (1.0 + 0.5 * 4.0)) < 1e-5
 
 
 def test_mass_splitting_weight_three_in_a_row(orc):
@@ -682,6 +685,26 @@ def test_literal_alg1_weight_three_in_a_row(orc, iters):
     s = orc.Sim(pr, vel, np.full(3, 2.0, F32), [], _params(pja_iters=iters, pja_weight=1, cell_size=2.2))
     s.step(1)
     assert np.abs(s.v).max() < 1e-15
+
+
+@pytest.mark.parametrize("iters", [1, 2])
+def test_literal_alg1_weight_body_contact(orc, iters):
+    """Alg. 1 as printed with a body: the particle takes the whole correction of its
+    body contact too (w = m_i).  A sphere touching a plane (psi = 0) and touching a
+    second, equal sphere on top, at rest with gravity on: each sweep the bottom sphere
+    cancels its plane approach g dt in full and the pair sees no relative velocity in
+    the first sweep: after one sweep U_bottom = 0, U_top = -g dt.  In the second the
+    pair's approach g dt is corrected in full by each side (the bottom moves down by
+    g dt, the top up by g dt), and the plane contact keeps its impulse: U_bottom = -g dt,
+    U_top = 0."""
+    r = F32(2.0 ** -8)
+    pr = np.array([[0.0, 0.0, r, r], [0.0, 0.0, 3 * r, r]], F32)
+    p = S.Params(dt=1e-4, gravity=(0.0, 0.0, -9.81), mu=0.5, alpha=0.2, pja_iters=iters, pja_weight=1)
+    s = orc.Sim(pr, np.zeros((2, 3), F32), np.array([0.01, 0.01], F32), [S.Body(kind=S.PLANE)], p)
+    s.step(1)
+    gdt = float(F32(9.81)) * float(F32(1e-4))
+    want = (0.0, -gdt) if iters == 1 else (-gdt, 0.0)
+    assert abs(s.v[0, 2] - want[0]) < 1e-15 and abs(s.v[1, 2] - want[1]) < 1e-15
 
 
 def test_literal_alg1_weight_rejects_free_bodies(orc):
