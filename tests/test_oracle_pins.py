@@ -783,6 +783,43 @@ def test_free_box_rests_on_plane(orc):
     assert abs(s.wrench[0, 2] + float(F32(M)) * g) < 1e-9 * M * g
 
 
+def test_tilted_free_box_on_its_lowest_edge(orc):
+    """A free box turned 30 degrees about x stands on the plane with its two lowest
+    corners (those at -y, -z in its frame: world y = h (sin - cos), z = 0).  Those two
+    corners, and only they, are the corner contacts; after the solve their velocities
+    do not point into the plane (the contact condition), whatever the box does about
+    the edge."""
+    M, h, th = 0.5, 0.05, math.radians(30.0)
+    q = (math.cos(th / 2), math.sin(th / 2), 0.0, 0.0)
+    box = S.Body(kind=S.BOX, shape=(h, h, h), pos=(0.0, 0.0, h * (math.sin(th) + math.cos(th))), quat=q,
+                 is_free=1, mass=M, inertia=(M * (2 * h) ** 2 / 6,) * 3)
+    s = orc.Sim(np.zeros((0, 4), F32), np.zeros((0, 3), F32), np.zeros(0, F32), [S.Body(kind=S.PLANE), box],
+                S.Params(dt=1e-4, mu=0.5, alpha=0.2, pja_iters=200))
+    pose0 = s.body_pose(1)
+    s.step(1)
+    assert s.stats.n_corner == 2
+    R = _quat_matrix(pose0[3:])
+    tw = s.body_twist(1)
+    for sx in (-1.0, 1.0):
+        rc = R @ np.array([sx * h, -h, -h])
+        assert abs(pose0[2] + rc[2]) < 1e-6                    # on the plane
+        vc = tw[:3] + np.cross(tw[3:], rc)
+        assert vc[2] > -1e-9, vc                               # not moving into it
+
+
+def test_free_box_corners_ignore_other_free_boxes(orc):
+    """Reading for free bodies: box corners are tested as points against the bodies that
+    are not free; a free box's corner inside another free box makes no contact."""
+    M, h = 0.5, 0.05
+    inert = (M * (2 * h) ** 2 / 6,) * 3
+    a = S.Body(kind=S.BOX, shape=(h, h, h), pos=(0.0, 0.0, 0.0), is_free=1, mass=M, inertia=inert)
+    b = S.Body(kind=S.BOX, shape=(h, h, h), pos=(0.09, 0.09, 0.09), is_free=1, mass=M, inertia=inert)
+    s = orc.Sim(np.zeros((0, 4), F32), np.zeros((0, 3), F32), np.zeros(0, F32), [a, b], _params())
+    s.step(1)
+    assert s.stats.n_corner == 0
+    assert np.allclose(s.body_twist(0), 0.0) and np.allclose(s.body_twist(1), 0.0)
+
+
 def test_fast_remainder_identity():
     """The step kernels compute Eq. 6's `mod n_h` without a division (Lemire, Kaser &
     Kurz 2019): low = magic * x mod 2^64, result = high 64 bits of low * d, with
