@@ -98,3 +98,21 @@ def test_checked_build_exports_the_same_symbols():
         return {l.split()[-1] for l in out.splitlines() if " T " in l}
 
     assert exported(_build.build(debug=True)) == exported(_build.build()) == set(_declared())
+
+
+def test_no_device_fails_loudly(lib):
+    """Without a CUDA device the library reports it (GG_ERR_NO_DEVICE) instead of
+    computing anything on the host: creating a simulation raises, and the
+    allocation-free binning call returns the status without touching its buffers."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import numpy as np
+    from paper_2306_01369_gb300 import gg, scenes as S
+    pr = np.array([[0.0, 0.0, 0.0, 0.01], [0.05, 0.0, 0.0, 0.01]], np.float32)
+    with pytest.raises(gg.GGError) as e:
+        gg.Sim(pr, None, None, S.Params())
+    assert e.value.status == gg.ERR_NO_DEVICE
+    keys = (ctypes.c_uint32 * 2)()
+    assert lib.gg_bin_sort_noalloc(ctypes.c_void_p(pr.ctypes.data), 2, ctypes.c_float(0.02), 4, keys, keys, keys,
+                                   None) == gg.ERR_NO_DEVICE
