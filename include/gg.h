@@ -209,7 +209,8 @@ GG_API uint32_t gg_abi_version(void);
 GG_API const char *gg_status_string(gg_status s);
 
 /*
- * Create a single-environment simulation of n spheres.
+ * Create a single-environment simulation of n spheres (the problem of Sec. II: sphere
+ * positions and velocities, bodies added with gg_set_bodies).
  * pos_radius: float[n][4] (x, y, z, radius > 0); vel: float[n][3] (NULL -> 0);
  * mass: float[n] (> 0; NULL -> density 4/3 pi r^3).  All device memory the step
  * needs is allocated here, at capacity; gg_step allocates nothing.
@@ -229,8 +230,9 @@ GG_API gg_status gg_create_batch(const gg_params *params, uint32_t n_envs, const
                           const float *pos_radius, const float *vel, const float *mass,
                           int inputs_on_device, gg_sim **out);
 
-/* Replace the bodies of environment env (n_bodies <= max_bodies; host array).
- * Synchronous with respect to previously enqueued steps. */
+/* Replace the bodies of environment env (n_bodies <= max_bodies; host array): rigid
+ * bodies with a pose in SE(3), a twist in se(3) and a signed distance function (Sec. II,
+ * Sec. II-C).  Synchronous with respect to previously enqueued steps. */
 GG_API gg_status gg_set_bodies(gg_sim *sim, uint32_t env, uint32_t n_bodies, const gg_body *bodies);
 
 /*
@@ -250,7 +252,7 @@ GG_API gg_status gg_set_body_grid(gg_sim *sim, uint32_t env, uint32_t body, cons
 
 /*
  * Prescribe the twist of kinematic body `body` of environment env for the next
- * n_steps steps: twist = float[n_steps][6] (world-frame lin_vel, ang_vel), step k
+ * n_steps steps (the paper's bodies are driven by time, Sec. II): twist = float[n_steps][6] (world-frame lin_vel, ang_vel), step k
  * counted from the current step.  Past the table the body keeps its own twist.
  * Allocates device memory (outside gg_step).
  */
@@ -258,22 +260,28 @@ GG_API gg_status gg_set_trajectory(gg_sim *sim, uint32_t env, uint32_t body, uin
                             const float *twist, int twist_on_device);
 
 /* Overwrite particle positions/radii (float[n][4]) and velocities (float[n][3]; NULL
- * keeps them), asynchronously on `stream`.  Masses are kept.  Host buffers that are
+ * keeps them), asynchronously on `stream` (the state x, v of Sec. II).  Returns
+ * GG_ERR_INVALID_ARG for a null position buffer.  Masses are kept.  Host buffers that are
  * pinned (cudaHostAlloc, cudaHostRegister; positions 16-byte aligned) are read by one
  * kernel over the host link; pageable ones are copied.  Either way the caller's buffers
  * must stay unchanged until the work on `stream` has run. */
 GG_API gg_status gg_set_particles(gg_sim *sim, const float *pos_radius, const float *vel, int on_device,
                            void *stream);
 
-/* Enqueue n_steps time steps on `stream` (replays of one captured CUDA graph per
- * step).  Returns without waiting; see gg_sync for device-side errors. */
+/* Enqueue n_steps time steps on `stream`: each one binning (Eq. 6), contacts (Sec. II-B,
+ * II-C, Eq. 7), the projected-Jacobi sweeps (Alg. 1), the wrenches (Sec. III-C) and the
+ * integration (Eq. 4-5), replayed from one captured CUDA graph.  Returns without
+ * waiting; see gg_sync for device-side errors. */
 GG_API gg_status gg_step(gg_sim *sim, uint32_t n_steps, void *stream);
 
-/* Wait for `stream` and report the latched device status (GG_OK or the first error). */
+/* Wait for `stream` and report the latched device status (GG_OK or the first error).
+ * Library plumbing; the paper has no counterpart. */
 GG_API gg_status gg_sync(gg_sim *sim, void *stream);
 
 /*
- * One turn of a host-driven loop: the particle state from host buffers (pos_radius
+ * One turn of a host-driven loop (an environment that exchanges the state with its
+ * caller every step, as the paper's learning tasks do, Sec. III-A): the particle state
+ * from host buffers (pos_radius
  * float[n][4], vel float[n][3] or NULL to keep the velocities), one time step, and the
  * new state into out (float[7 n]: positions float[n][4], then velocities float[n][3],
  * the GG_FIELD_POS_VEL layout), waited for.  The same work and results, bit for bit, as
@@ -285,7 +293,7 @@ GG_API gg_status gg_sync(gg_sim *sim, void *stream);
  */
 GG_API gg_status gg_step_io(gg_sim *sim, const float *pos_radius, const float *vel, float *out, void *stream);
 
-/* Size in bytes of a readback field. */
+/* Size in bytes of a readback field (0 for a null simulation or an unknown field). */
 GG_API size_t gg_field_bytes(const gg_sim *sim, gg_field field);
 
 /*
@@ -428,8 +436,10 @@ GG_API uint32_t gg_tuning_flags(uint32_t k);
 GG_API gg_status gg_autotune(gg_sim *sim, void *stream);
 
 /* Last error message of this simulation (never NULL). */
-GG_API const char *gg_last_error(const gg_sim *sim);
+GG_API const char *gg_last_error(const gg_sim *sim);  /* plumbing; no counterpart in the paper */
 
+/* Free the simulation and all its device memory (NULL: no-op).  Plumbing; no
+ * counterpart in the paper. */
 GG_API void gg_destroy(gg_sim *sim);
 
 /*
