@@ -297,7 +297,9 @@ GG_API gg_status gg_step_io(gg_sim *sim, const float *pos_radius, const float *v
 GG_API size_t gg_field_bytes(const gg_sim *sim, gg_field field);
 
 /*
- * Copy `field` into dst (bytes must equal gg_field_bytes).  dst on the device:
+ * Copy `field` into dst (bytes must equal gg_field_bytes, else GG_ERR_INVALID_ARG):
+ * the state x, v (Sec. II), the body wrenches (Sec. III-C force readback), the binning
+ * of Eq. 6, the contacts and their impulses (Alg. 1).  dst on the device:
  * asynchronous on `stream`; on the host: waits for `stream`.  Returns the latched
  * device status when it waited (the copy is made either way).
  */
@@ -343,11 +345,12 @@ typedef struct {
 GG_API gg_status gg_render(gg_sim *sim, uint32_t env, const gg_camera *camera, float *out, int out_on_device,
                            void *stream);
 
-/* Restore a GG_FIELD_STATE checkpoint taken from a simulation with the same sizes. */
+/* Restore a GG_FIELD_STATE checkpoint taken from a simulation with the same sizes
+ * (GG_ERR_INVALID_ARG otherwise).  Checkpoint and resume: beyond the paper. */
 GG_API gg_status gg_set_state(gg_sim *sim, const void *state, size_t bytes, int on_device, void *stream);
 
 /*
- * Stage timing.  gg_enable_timing(sim, 1) records CUDA events inside every
+ * Stage timing (measurement; the paper has no counterpart).  gg_enable_timing(sim, 1) records CUDA events inside every
  * subsequent step: the library keeps a second step graph with the events (captured
  * at its first use; switching back and forth afterwards costs nothing), and
  * gg_enable_timing(sim, 0) returns to the plain one.  The events break the
@@ -361,7 +364,8 @@ GG_API gg_status gg_set_state(gg_sim *sim, const void *state, size_t bytes, int 
 GG_API gg_status gg_enable_timing(gg_sim *sim, int on);
 GG_API gg_status gg_stage_ms(gg_sim *sim, float *ms);
 
-/* Kernel launches one step enqueues (all of them this library's own kernels). */
+/* Kernel launches one step enqueues (all of them this library's own kernels; 0 for a
+ * null simulation).  Measurement; the paper has no counterpart. */
 GG_API uint32_t gg_kernels_per_step(const gg_sim *sim);
 
 /*
@@ -404,7 +408,8 @@ GG_API uint32_t gg_hash_size(const gg_sim *sim, uint32_t env);
  * on); 0 for a bad argument. */
 GG_API float gg_cell_size(const gg_sim *sim, uint32_t env);
 
-/* Number of fixed launch-shape sets accepted by gg_params.tuning, and the set chosen. */
+/* Number of fixed launch-shape sets accepted by gg_params.tuning, and the set chosen
+ * (the paper's loop-structure and binning choices, Sec. II-D, Alg. 2, among them). */
 GG_API uint32_t gg_tuning_count(void);
 GG_API uint32_t gg_tuning_selected(const gg_sim *sim);
 
