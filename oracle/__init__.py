@@ -69,9 +69,12 @@ _lib = None
 
 
 def lib():
+    """The oracle library: the one build() makes, or the build named by the environment
+    variable GG_ORACLE_LIB (tests/oracle_mutations.py points it at copies of the oracle
+    with one mistake planted, to check that the pins catch each)."""
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
+        L = C.CDLL(os.environ.get("GG_ORACLE_LIB") or build())
         P = C.POINTER
         L.orc_inv_cell.restype = C.c_float
         L.orc_inv_cell.argtypes = [C.c_float]

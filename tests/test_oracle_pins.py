@@ -631,14 +631,17 @@ def test_free_body_central_hit_inelastic(orc):
 
 
 def test_scoop_loss_limits(orc):
-    """Reading g18 (loss): sum_i m_i sigmoid(-f_B(y_i) / eps) over the cavity box B.
-    Deep inside the cavity a particle counts fully, far outside not at all, and on the
-    cavity's +x wall (f_B = 0) by half; the three masses tell the terms apart."""
+    """Reading g18 (loss): sum_i m_i sigmoid(-f_B(y_i) / eps) over the cavity box B
+    (half extents 0.054, 0.044, 0.04 about z = 0.01 in the tool frame).  Deep inside the
+    cavity a particle counts fully, far outside not at all, on the cavity's +x wall
+    (f_B = 0) by half, and 5 mm below the cavity's open top (f_B = -0.005) by
+    1 / (1 + e^-5); the four masses tell the terms apart."""
     scoop = S.scoop_body(1.0, pos=(0.0, 0.0, 0.0))
-    pr = np.array([[0.0, 0.0, 0.01, 0.002], [0.5, 0.5, 0.5, 0.002], [0.054, 0.0, 0.01, 0.002]], F32)
-    s = orc.Sim(pr, np.zeros((3, 3), F32), np.array([1.0, 2.0, 4.0], F32), [scoop], _params())
+    pr = np.array([[0.0, 0.0, 0.01, 0.002], [0.5, 0.5, 0.5, 0.002], [0.054, 0.0, 0.01, 0.002],
+                   [0.0, 0.0, 0.045, 0.002]], F32)
+    s = orc.Sim(pr, np.zeros((4, 3), F32), np.array([1.0, 2.0, 4.0, 8.0], F32), [scoop], _params())
     L = s.scoop_loss(0, eps=1e-3)
-    assert abs(L - (1.0 + 0.5 * 4.0)) < 1e-5
+    assert abs(L - (1.0 + 0.5 * 4.0 + 8.0 / (1.0 + math.exp(-5.0)))) < 1e-4
 
 
 def test_mass_splitting_weight_three_in_a_row(orc):
